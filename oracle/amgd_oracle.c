@@ -1,0 +1,301 @@
+/*
+ * amgd_oracle.c -- plain, slow, FP64 CPU oracle for the algebraic-distance
+ * strength-of-connection build of Brandt, Brannick, Kahl and Livshits,
+ * "An algebraic distances measure of AMG strength of connection".
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  The product path (the
+ * CUDA library and its Python binding) never calls it, links it or shares
+ * a line of code, a header or a constant table with it.
+ *
+ * What it computes, step by step (one row at a time, CSR order):
+ *   1. test vectors X0: Philox4x64-10 counter-based random numbers mapped
+ *      to uniform[-1,1)                         (§3: relax Ax=0 from random
+ *                                                 starting vectors)
+ *   2. nu relaxation sweeps on A x = 0: weighted Jacobi, or multicolor
+ *      Gauss-Seidel with snapshot semantics      (§3, §2: Gauss-Seidel)
+ *   3. the LS target y_i: plain x_i (Eq. (3.1)) or the residual-corrected
+ *      x_i - r_i / a_ii with r = A x (Eqs. (3.2), (4.1), (4.3))
+ *   4. per stored off-diagonal (i,j): the one-point LS fit p_ij and the
+ *      minimal functional LS_ij; algebraic distance r_ij = 1/LS_ij
+ *                                                 (§4.1, Eq. (4.3))
+ *   5. row-relative threshold r_ij > theta * max_k r_ik  (§4.2, Eq. (4.4))
+ *   6. the strength graph as CSR                  (§4.2)
+ *
+ * Rounding conventions (the paper fixes none): every multiply-accumulate of
+ * a row sum is one fused multiply-add (C99 fma, a single rounding), sums run
+ * in CSR order (row sums) or in test-vector order (LS sums), and the update
+ * x_i - c_i * s is one fused multiply-add with c_i = omega / a_ii.  All other
+ * operations are plain IEEE double operations; the file is compiled with
+ * -ffp-contract=off so the compiler adds no fusion of its own.
+ *
+ * Parity pins (see tests/): Philox against numpy's Philox4x64-10; sweeps
+ * against dense matrix powers and a triangular solve; LS against a library
+ * least-squares solve and brute-force minimisation; the 7-point stencil
+ * generator against the worked stencil S_A of §5.1.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* 1. Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:  */
+/*    as easy as 1, 2, 3", SC'11).  Multipliers and Weyl key increments are */
+/*    the ones published for the 4x64 variant.                              */
+/* ------------------------------------------------------------------------ */
+static void orc_mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t hi0, lo0, hi1, lo1;
+        orc_mulhilo64(M0, c0, &hi0, &lo0);
+        orc_mulhilo64(M1, c2, &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c1 ^ k0;
+        uint64_t n1 = lo1;
+        uint64_t n2 = hi0 ^ c3 ^ k1;
+        uint64_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/*
+ * Test vectors X0 (n x K, row-major): §3 starts each test vector from a
+ * random vector before relaxing A x = 0.  Element (i, kappa) takes word
+ * (kappa mod 4) of Philox4x64-10 at counter (i, kappa / 4, 0, 0) and key
+ * (seed, stream); the top 53 bits m give u = m * 2^-53 in [0,1) and
+ * x = 2u - 1 in [-1,1).  Both steps are exact in double precision.
+ * stream distinguishes the matrices of a batch (0 for a single matrix).
+ */
+void orc_tv_init(int64_t n, int32_t K, uint64_t seed, uint64_t stream, double *X)
+{
+    const uint64_t key[2] = {seed, stream};
+    for (int64_t i = 0; i < n; ++i) {
+        for (int32_t kappa = 0; kappa < K; ++kappa) {
+            uint64_t ctr[4] = {(uint64_t)i, (uint64_t)(kappa / 4), 0, 0};
+            uint64_t out[4];
+            orc_philox4x64_10(ctr, key, out);
+            uint64_t m = out[kappa % 4] >> 11;
+            double u = (double)m * 0x1.0p-53;
+            X[i * K + kappa] = 2.0 * u - 1.0;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Input checks.  A is the graph G=(V,E) of §4.1: (i,j) in E iff a_ij != 0, */
+/* stored as CSR with an explicit, nonzero diagonal in every row.           */
+/* Returns 0, or: 1 bad row_ptr, 2 column out of range, 3 duplicate (i,j),  */
+/* 4 missing or zero diagonal, 5 non-finite value.                          */
+/* ------------------------------------------------------------------------ */
+int orc_check_csr(int64_t n, const int64_t *rp, const int32_t *col, const double *val)
+{
+    if (n < 0) return 1;
+    if (rp[0] != 0) return 1;
+    for (int64_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return 1;
+    for (int64_t i = 0; i < n; ++i) {
+        int have_diag = 0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            if (col[p] < 0 || (int64_t)col[p] >= n) return 2;
+            if (!isfinite(val[p])) return 5;
+            for (int64_t q = rp[i]; q < p; ++q)
+                if (col[q] == col[p]) return 3;
+            if (col[p] == i) {
+                if (val[p] == 0.0) return 4;
+                have_diag = 1;
+            }
+        }
+        if (!have_diag) return 4;
+    }
+    return 0;
+}
+
+static double orc_diag(const int64_t *rp, const int32_t *col, const double *val, int64_t i)
+{
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+        if (col[p] == i) return val[p];
+    return NAN; /* unreachable for checked input */
+}
+
+/* ------------------------------------------------------------------------ */
+/* 2. Relaxation of the homogeneous system A x = 0 (§3: "relaxing the       */
+/*    homogeneous system Ax=0 with a different starting vector").           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One weighted-Jacobi sweep on all K vectors at once:
+ *   x_i <- x_i - (omega / a_ii) * sum_p a_{i,col_p} x_{col_p}
+ * using only the values from before the sweep.
+ */
+void orc_jacobi_sweep(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                      int32_t K, double omega, const double *X, double *Xn)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double c = omega / orc_diag(rp, col, val, i);
+        for (int32_t kappa = 0; kappa < K; ++kappa) {
+            double s = 0.0;
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+                s = fma(val[p], X[(int64_t)col[p] * K + kappa], s);
+            Xn[i * K + kappa] = fma(-c, s, X[i * K + kappa]);
+        }
+    }
+}
+
+/*
+ * One multicolor Gauss-Seidel sweep (§2 names Gauss-Seidel as the smoother
+ * and §5.2 relaxes the test vectors with it).  Colors are processed in
+ * increasing order.  A row of color c is updated from the new values of
+ * rows of smaller colors and the values from the start of the sweep of all
+ * other rows, itself included ("snapshot" semantics: for a proper coloring
+ * this is Gauss-Seidel in color order; when same-colored rows touch, they
+ * see each other's old values).  omega is the over-relaxation weight
+ * (1 = plain Gauss-Seidel).
+ */
+void orc_mcgs_sweep(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                    const int32_t *color, int32_t ncolors, int32_t K, double omega,
+                    const double *X, double *Xn)
+{
+    memcpy(Xn, X, (size_t)n * (size_t)K * sizeof(double));
+    for (int32_t c = 0; c < ncolors; ++c) {
+        for (int64_t i = 0; i < n; ++i) {
+            if (color[i] != c) continue;
+            double ci = omega / orc_diag(rp, col, val, i);
+            for (int32_t kappa = 0; kappa < K; ++kappa) {
+                double s = 0.0;
+                for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                    int64_t j = col[p];
+                    double xj = (color[j] < c) ? Xn[j * K + kappa] : X[j * K + kappa];
+                    s = fma(val[p], xj, s);
+                }
+                Xn[i * K + kappa] = fma(-ci, s, X[i * K + kappa]);
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* 3. LS target.                                                            */
+/*   mode 0 (residual-corrected, default): y_i = x_i - r_i / a_ii, r = A x  */
+/*          -- the target of Eqs. (3.2), (4.1) and (4.3); the Remark in     */
+/*          §3.1 identifies it with one local Jacobi step, and with         */
+/*          omega = 1 it equals one orc_jacobi_sweep bit for bit.           */
+/*   mode 1 (plain): y_i = x_i -- the target of Eq. (3.1).                  */
+/* ------------------------------------------------------------------------ */
+void orc_target(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                int32_t K, int32_t mode, const double *X, double *Y)
+{
+    if (mode == 1) {
+        memcpy(Y, X, (size_t)n * (size_t)K * sizeof(double));
+        return;
+    }
+    orc_jacobi_sweep(n, rp, col, val, K, 1.0, X, Y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 4. One-point least squares per stored off-diagonal (§4.1, Eq. (4.3)):    */
+/*   LS_ij(p) = sum_kappa w_kappa (y_i^k - p x_j^k)^2, p_ij its minimiser,  */
+/*   r_ij = 1 / LS_ij(p_ij).  With S_xx = sum w x_j^2 and S_yx = sum w y x_j */
+/*   the minimiser is p = S_yx / S_xx (S_xx = 0: every p is a minimiser;   */
+/*   p = 0 is taken, LS = sum w y^2).  LS is evaluated as the weighted sum */
+/*   of squared residuals at p (two passes over the K vectors).            */
+/*   Residual-corrected target with exactly one off-diagonal in row i:     */
+/*   y_i = -(a_ij / a_ii) x_j holds exactly, so p = -a_ij/a_ii and LS = 0  */
+/*   are returned rather than a rounding residue.                          */
+/*   Diagonal slots get a = 0, ls = NaN.  Outputs are aligned with A's CSR */
+/*   slots.                                                                */
+/* ------------------------------------------------------------------------ */
+void orc_edge_ls(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                 int32_t K, const double *w, int32_t mode, const double *X, const double *Y,
+                 double *a, double *ls)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t off = 0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+            if (col[p] != i) ++off;
+        double aii = orc_diag(rp, col, val, i);
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            int64_t j = col[p];
+            if (j == i) {
+                a[p] = 0.0;
+                ls[p] = NAN;
+                continue;
+            }
+            if (mode == 0 && off == 1) {
+                a[p] = -val[p] / aii;
+                ls[p] = 0.0;
+                continue;
+            }
+            const double *y = Y + i * K;
+            const double *x = X + j * K;
+            double sxx = 0.0, syx = 0.0;
+            for (int32_t kappa = 0; kappa < K; ++kappa) {
+                sxx += w[kappa] * x[kappa] * x[kappa];
+                syx += w[kappa] * y[kappa] * x[kappa];
+            }
+            double pij = (sxx == 0.0) ? 0.0 : syx / sxx;
+            double res = 0.0;
+            for (int32_t kappa = 0; kappa < K; ++kappa) {
+                double e = y[kappa] - pij * x[kappa];
+                res += w[kappa] * e * e;
+            }
+            a[p] = pij;
+            ls[p] = res;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* 5. Strength graph (§4.2, Eq. (4.4)): keep (i,j) iff                      */
+/*      r_ij > theta * max_k r_ik,  k over the off-diagonals of row i.      */
+/*   With r = 1/LS and m_i = min_k LS_ik this is LS_ij = 0 (r = +inf is     */
+/*   always kept) or theta * LS_ij < m_i; evaluated in LS form so that no   */
+/*   division by zero occurs.  The comparison is strict.                    */
+/*   count[i] = number of kept slots of row i.                              */
+/* ------------------------------------------------------------------------ */
+void orc_threshold(int64_t n, const int64_t *rp, const int32_t *col, const double *ls,
+                   double theta, uint8_t *flag, int64_t *count)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double m = INFINITY;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+            if (col[p] != i && ls[p] < m) m = ls[p];
+        int64_t cnt = 0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            int strong = 0;
+            if (col[p] != i)
+                strong = (ls[p] == 0.0) || (theta * ls[p] < m);
+            flag[p] = (uint8_t)strong;
+            cnt += strong;
+        }
+        count[i] = cnt;
+    }
+}
+
+/* 6. The strength graph M^1 as CSR: kept slots, rows in order, CSR order  */
+/*    within a row.  Returns the number of kept edges.                      */
+int64_t orc_strength_csr(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *flag,
+                         int64_t *s_rp, int32_t *s_col)
+{
+    int64_t k = 0;
+    s_rp[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+            if (flag[p]) s_col[k++] = col[p];
+        s_rp[i + 1] = k;
+    }
+    return k;
+}

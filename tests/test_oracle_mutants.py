@@ -1,0 +1,75 @@
+"""Planted mistakes: every plausible slip in the oracle must fail a pin.
+
+Each case applies one textual mutation to a temporary copy of
+oracle/amgd_oracle.c (a dropped term, a wrong sign, a wrong index, a swapped
+operand, a non-strict comparison ...), compiles it with gcc on the CPU and
+runs all pins of test_oracle_pins.py against it.  The committed oracle is
+never touched.
+"""
+import os
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+PINS = [pins.pin_philox_numpy, pins.pin_tv_init, pins.pin_jacobi_dense_power,
+        pins.pin_mcgs_proper_coloring_is_gauss_seidel, pins.pin_mcgs_snapshot_matrix_form,
+        pins.pin_target, pins.pin_ls_lstsq, pins.pin_ls_brute_force, pins.pin_ls_invariants,
+        pins.pin_ls_exact_cases, pins.pin_degree_one_rows, pins.pin_threshold,
+        pins.pin_strength_csr]
+
+# (name, text to find, replacement, occurrence index)
+MUTANTS = [
+    ("philox_hi_lo_swapped", "uint64_t n1 = lo1;", "uint64_t n1 = hi1;", 0),
+    ("philox_key_not_bumped", "k1 += W1;", "k1 += 0;", 0),
+    ("philox_wrong_multiplier_input", "orc_mulhilo64(M1, c2,", "orc_mulhilo64(M1, c1,", 0),
+    ("tv_map_drops_a_bit", "out[kappa % 4] >> 11", "out[kappa % 4] >> 12", 0),
+    ("tv_map_wrong_word", "out[kappa % 4]", "out[(kappa + 1) % 4]", 0),
+    ("jacobi_sign", "Xn[i * K + kappa] = fma(-c, s,", "Xn[i * K + kappa] = fma(c, s,", 0),
+    ("jacobi_drops_diagonal", "s = fma(val[p], X[(int64_t)col[p] * K + kappa], s);",
+     "if (col[p] != i) s = fma(val[p], X[(int64_t)col[p] * K + kappa], s);", 0),
+    ("jacobi_wrong_row", "s = fma(val[p], X[(int64_t)col[p] * K + kappa], s);",
+     "s = fma(val[p], X[i * K + kappa], s);", 0),
+    ("jacobi_ignores_omega", "double c = omega / orc_diag", "double c = 1.0 / orc_diag", 0),
+    ("mcgs_same_color_new", "(color[j] < c) ?", "(color[j] <= c) ?", 0),
+    ("mcgs_all_old", "(color[j] < c) ?", "(0) ?", 0),
+    ("mcgs_ignores_omega", "double ci = omega / orc_diag", "double ci = 1.0 / orc_diag", 0),
+    ("target_modes_swapped", "if (mode == 1) {", "if (mode == 0) {", 0),
+    ("ls_sxx_uses_y", "sxx += w[kappa] * x[kappa] * x[kappa];",
+     "sxx += w[kappa] * y[kappa] * y[kappa];", 0),
+    ("ls_unweighted_residual", "res += w[kappa] * e * e;", "res += e * e;", 0),
+    ("ls_residual_sign", "double e = y[kappa] - pij * x[kappa];",
+     "double e = y[kappa] + pij * x[kappa];", 0),
+    ("ls_transposed_roles", "const double *y = Y + i * K;", "const double *y = Y + j * K;", 0),
+    ("degree_one_sign", "a[p] = -val[p] / aii;", "a[p] = val[p] / aii;", 0),
+    ("threshold_not_strict", "(theta * ls[p] < m)", "(theta * ls[p] <= m)", 0),
+    ("threshold_uses_max", "if (col[p] != i && ls[p] < m) m = ls[p];",
+     "if (col[p] != i && (m == INFINITY || ls[p] > m)) m = ls[p];", 0),
+    ("threshold_counts_diagonal", "strong = (ls[p] == 0.0) || (theta * ls[p] < m);",
+     "strong = (ls[p] == 0.0) || (theta * ls[p] < m); else strong = 1;", 0),
+    ("csr_writes_slot_not_column", "if (flag[p]) s_col[k++] = col[p];",
+     "if (flag[p]) s_col[k++] = (int32_t)(p - rp[i]);", 0),
+]
+
+
+def _mutate(text, find, repl, occ):
+    pos = -1
+    for _ in range(occ + 1):
+        pos = text.index(find, pos + 1)
+    return text[:pos] + repl + text[pos + len(find):]
+
+
+@pytest.mark.parametrize("name,find,repl,occ", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, find, repl, occ):
+    src = oracle.source_text()
+    assert find in src, "mutation anchor missing: %s" % name
+    mutant = oracle.compile_variant(_mutate(src, find, repl, occ),
+                                    os.path.join(str(tmp_path), "liborc_%s.so" % name))
+    caught = []
+    for pin in PINS:
+        try:
+            pin(mutant)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, "planted mistake %r passed every pin" % name
