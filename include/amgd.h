@@ -1,0 +1,245 @@
+/*
+ * amgd.h -- C ABI of the GB300 (sm_103a) algebraic-distance strength-of-
+ * connection library.
+ *
+ * Method: Brandt, Brannick, Kahl, Livshits, "An algebraic distances measure
+ * of AMG strength of connection".  Given a sparse matrix A (CSR) the library
+ *   (a) draws K random test vectors and smooths them by nu relaxation sweeps
+ *       on A x = 0                                   (§3; §5.2)
+ *   (b) for every stored off-diagonal (i,j) fits the one-point least-squares
+ *       interpolation p_ij of the target y_i from x_j and returns p_ij and
+ *       the minimal functional LS_ij, whose reciprocal is the algebraic
+ *       distance r_ij                          (§4.1, Eqs. (3.2), (4.1), (4.3))
+ *   (c) keeps (i,j) when r_ij > theta * max_k r_ik and returns the kept
+ *       edges as a strength CSR                        (§4.2, Eq. (4.4))
+ * All arithmetic runs in hand-written CUDA kernels on the current device.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an int status (AMGD_OK or a negative AMGD_ERR_*);
+ *   nothing throws across the ABI.  On error the handle keeps its previous
+ *   state and amgd_last_error() holds a message.
+ * - Ownership: the caller owns every array it passes.  amgd_create copies
+ *   the matrix into device memory owned by the handle; outputs are written
+ *   into caller buffers.  amgd_destroy frees everything the handle owns.
+ * - mem = AMGD_MEM_HOST: the pointers are host memory; the call copies
+ *   through the handle's stream and returns when the data is in place.
+ *   mem = AMGD_MEM_DEVICE: the pointers are device memory of the current
+ *   device; the call only enqueues work on the handle's stream.
+ * - Ordering: every call is ordered on the handle's stream (default: the
+ *   legacy default stream).  A handle is not thread-safe; distinct handles
+ *   are independent.
+ * - Sizes: 0 <= n < 2^31, nnz < 2^31, 1 <= K <= 64.
+ * - Row order of A and the order of the columns inside each row are the
+ *   caller's and are preserved: they fix the summation order of every row
+ *   sum, and the order of the strength CSR.
+ */
+#ifndef AMGD_H
+#define AMGD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amgd_ctx *amgd_handle;
+
+/* status codes */
+#define AMGD_OK               0
+#define AMGD_ERR_ARG         -1   /* bad argument (size, pointer, enum, value)   */
+#define AMGD_ERR_CSR         -2   /* row_ptr not monotone, column out of range,
+                                     duplicate (i,j), non-finite value          */
+#define AMGD_ERR_ZERO_DIAG   -3   /* a row without a stored nonzero diagonal    */
+#define AMGD_ERR_CUDA        -4   /* a CUDA runtime error (text in last_error)  */
+#define AMGD_ERR_OOM         -5   /* device allocation failed                   */
+#define AMGD_ERR_STATE       -6   /* call out of order (e.g. strength before
+                                     distances, MCGS without a coloring)        */
+#define AMGD_ERR_CAPACITY    -7   /* output buffer too small                    */
+#define AMGD_ERR_TIMEOUT     -8   /* a bounded device wait gave up              */
+#define AMGD_ERR_UNSUPPORTED -9   /* size or mode outside the supported range   */
+
+/* where caller arrays live */
+#define AMGD_MEM_HOST   0
+#define AMGD_MEM_DEVICE 1
+
+/* relaxation sweep types (§3; §2 names Gauss-Seidel, §5.2 uses it) */
+#define AMGD_SWEEP_JACOBI 0   /* x <- x - omega D^-1 A x, all rows at once          */
+#define AMGD_SWEEP_MCGS   1   /* multicolor Gauss-Seidel / SOR over a given coloring */
+
+/* LS target of the one-point fit */
+#define AMGD_TARGET_RESIDUAL 0   /* y_i = x_i - (A x)_i / a_ii  (Eqs. (3.2), (4.1), (4.3)) */
+#define AMGD_TARGET_PLAIN    1   /* y_i = x_i                   (Eq. (3.1))               */
+
+/* test-vector storage precision */
+#define AMGD_FP64 0   /* FP64 vectors, FP64 arithmetic                                  */
+#define AMGD_FP32 1   /* FP32 vectors, FP32 arithmetic, compensated FP32 LS sums        */
+#define AMGD_BF16 2   /* BF16 vectors, FP32 arithmetic, compensated FP32 LS sums        */
+
+/*
+ * amgd_create -- build a handle for one n x n matrix A in CSR form.
+ *   row_ptr[n+1] (int64, row_ptr[0] = 0, non-decreasing), col[nnz] (int32,
+ *   0 <= col < n, no duplicate column inside a row), val[nnz] (finite
+ *   doubles); every row must store its diagonal with a nonzero value.  This
+ *   is the graph G_1 of A (§4.1, Eq. (4.2) with d = 1): the distances are
+ *   evaluated on exactly the stored off-diagonals.
+ *   K: number of test vectors (1..64).  seed: Philox4x64-10 key word 0 for
+ *   the starting vectors; amgd_create leaves the vectors at that start
+ *   (see amgd_init_vectors).  Storage starts as AMGD_FP64, target as
+ *   AMGD_TARGET_RESIDUAL, LS weights as all ones.
+ *   mem: where row_ptr/col/val live.  *out receives the handle (NULL on error).
+ *   Errors: ARG, CSR, ZERO_DIAG, UNSUPPORTED, OOM, CUDA.
+ */
+int amgd_create(const int64_t *row_ptr, const int32_t *col, const double *val, int64_t n,
+                int32_t K, uint64_t seed, int mem, amgd_handle *out);
+
+/*
+ * amgd_create_batch -- one handle over nmat independent matrices of uneven
+ *   size, processed together by every kernel launch (block-diagonal
+ *   concatenation: matrix b's rows follow matrix b-1's and its columns are
+ *   shifted by the same offset).  row_ptr[b], col[b], val[b], n[b] describe
+ *   matrix b exactly as in amgd_create.  Test vectors of matrix b use
+ *   Philox key (seed, b) and the row index local to matrix b, so a batched
+ *   build equals nmat separate builds bit for bit.  All outputs are in the
+ *   concatenated numbering (amgd_batch_offsets gives the row and slot
+ *   offsets of each matrix).  Errors as amgd_create.
+ */
+int amgd_create_batch(int32_t nmat, const int64_t *const *row_ptr, const int32_t *const *col,
+                      const double *const *val, const int64_t *n, int32_t K, uint64_t seed,
+                      int mem, amgd_handle *out);
+
+/* Row offsets (nmat+1) and CSR-slot offsets (nmat+1) of the matrices of a
+ * batch handle, written to host arrays; a single-matrix handle has nmat 1. */
+int amgd_batch_offsets(amgd_handle h, int64_t *row_off, int64_t *slot_off);
+
+/* Sizes of a handle: n (total rows), nnz (stored entries), number of stored
+ * off-diagonals E, K, nmat.  Any pointer may be NULL. */
+int amgd_sizes(amgd_handle h, int64_t *n, int64_t *nnz, int64_t *E, int32_t *K, int32_t *nmat);
+
+/* Make every later call of this handle use `stream` (a cudaStream_t of the
+ * current device; NULL = legacy default stream). */
+int amgd_set_stream(amgd_handle h, void *stream);
+
+/* Storage precision of the test vectors (AMGD_FP64/FP32/BF16).  The current
+ * vectors are converted by round-to-nearest-even; computed distances are
+ * invalidated.  Errors: ARG, OOM, CUDA. */
+int amgd_set_precision(amgd_handle h, int storage);
+
+/* LS target: AMGD_TARGET_RESIDUAL (default) or AMGD_TARGET_PLAIN. */
+int amgd_set_target(amgd_handle h, int target);
+
+/* LS weights w[K] (host doubles, each > 0 and finite; §3.1 weights
+ * omega_kappa of Eq. (3.1)); NULL restores all ones. */
+int amgd_set_weights(amgd_handle h, const double *w);
+
+/*
+ * amgd_set_coloring -- the coloring that fixes the Gauss-Seidel order of
+ *   AMGD_SWEEP_MCGS: color[n] in 0..ncolors-1 (host or device per mem).
+ *   Colors are swept in increasing order; a row of color c is updated from
+ *   the new values of rows of smaller colors and the values from the start
+ *   of the sweep of every other row, itself included.  For a proper
+ *   coloring this is Gauss-Seidel (SOR) in color order; for an improper one
+ *   (red-black on a 9-point stencil) it is the same well-defined rule.  The
+ *   handle reorders its rows by color internally; results are returned in
+ *   the caller's order.  The current vectors are kept.
+ *   Errors: ARG (color out of range), OOM, CUDA.
+ */
+int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int mem);
+
+/* Reset the test vectors to the Philox4x64-10 start for `seed`: element
+ * (i, k) of matrix b is 2 m 2^-53 - 1, m = word (k mod 4) of Philox4x64-10
+ * at counter (i, k/4, 0, 0), key (seed, b), shifted right by 11 bits;
+ * rounded to the storage precision.  (§3: relaxation starts from random
+ * vectors.) */
+int amgd_init_vectors(amgd_handle h, uint64_t seed);
+
+/* Copy the test vectors in/out as an n x K row-major block of doubles
+ * (caller's row order).  set rounds to the storage precision; get widens
+ * exactly. */
+int amgd_set_vectors(amgd_handle h, const double *X, int mem);
+int amgd_get_vectors(amgd_handle h, double *X, int mem);
+
+/* Replace the values of A (same pattern and slot order as at create;
+ * val[nnz] host or device).  The values are staged on the device and checked
+ * there (finite, nonzero diagonal) before they replace the old ones; the call
+ * synchronises the handle's stream.  Errors: ARG, CSR, ZERO_DIAG, CUDA. */
+int amgd_set_values(amgd_handle h, const double *val, int mem);
+
+/*
+ * amgd_relax -- nu sweeps on A x = 0 applied to all K vectors (§3):
+ *   AMGD_SWEEP_JACOBI: x_i <- x_i - (omega / a_ii) sum_j a_ij x_j
+ *   AMGD_SWEEP_MCGS:   as set by amgd_set_coloring, SOR weight omega
+ *   Sweeps accumulate on the current vectors.  nu >= 0, omega finite.
+ *   Errors: ARG, STATE (MCGS without coloring), CUDA.
+ */
+int amgd_relax(amgd_handle h, int32_t nu, double omega, int sweep_type);
+
+/*
+ * amgd_distances -- one-point LS fit for every stored off-diagonal slot p =
+ *   (i,j) of A (§4.1, Eq. (4.3)) on the current vectors, and the strength
+ *   flags for threshold theta (>= 0, finite; Eq. (4.4)).  Outputs are
+ *   aligned with A's CSR slots (nnz long, caller's order) and any may be NULL
+ *   (the values are kept on the device either way for amgd_strength):
+ *     a[p]    the minimiser p_ij (0 on the diagonal)
+ *     dist[p] the algebraic distance r_ij = 1 / LS_ij (+inf for LS = 0,
+ *             NaN on the diagonal)
+ *     ls[p]   the minimal LS functional LS_ij (NaN on the diagonal)
+ *   For the residual target, a row with a single off-diagonal has
+ *   y_i = -(a_ij/a_ii) x_j exactly: a = -a_ij/a_ii, LS = 0 are returned.
+ *   Mixed precisions compute in FP32 with compensated sums and redo in FP64
+ *   an edge whose LS is below 1e-4 * sum_k w_k y_k^2 (cancellation).
+ *   Errors: ARG, CUDA.
+ */
+int amgd_distances(amgd_handle h, double theta, double *a, double *dist, double *ls, int mem);
+
+/*
+ * amgd_strength -- the strength graph M^1 (§4.2) from the flags of the last
+ *   amgd_distances call: s_row_ptr[n+1] (int64), s_col[cap] (int32), kept
+ *   edges row by row in A's slot order.
+ *   mem = AMGD_MEM_DEVICE with cap >= E: enqueued without synchronising;
+ *     the total is s_row_ptr[n] on the device; *nnz_s (may be NULL) is set
+ *     after a synchronisation only if nnz_s is not NULL.
+ *   otherwise the call synchronises, sets *nnz_s and returns
+ *     AMGD_ERR_CAPACITY (nothing written to s_col) if cap is too small.
+ *   Errors: ARG, STATE (no distances yet), CAPACITY, CUDA.
+ */
+int amgd_strength(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap,
+                  int64_t *nnz_s, int mem);
+
+/*
+ * amgd_graph_capture -- record one whole build (vector start from `seed`,
+ *   nu sweeps, distances for theta, strength CSR into the DEVICE buffers
+ *   s_row_ptr[n+1], s_col[cap >= E]) as a CUDA graph owned by the handle;
+ *   amgd_graph_launch replays it on the handle's stream.  Replaces any
+ *   earlier graph.  Errors: ARG, STATE, CAPACITY (cap < E), CUDA.
+ */
+int amgd_graph_capture(amgd_handle h, uint64_t seed, int32_t nu, double omega, int sweep_type,
+                       double theta, int64_t *s_row_ptr, int32_t *s_col, int64_t cap);
+int amgd_graph_launch(amgd_handle h);
+
+/*
+ * Phase timing of captured builds.  amgd_enable_phase_timing(h, 1) before
+ *   amgd_graph_capture makes the captured graph record CUDA events (owned by
+ *   the handle) on the stream it runs on at the boundaries
+ *   start | vectors | sweeps | distances | strength.  amgd_phase_times waits
+ *   for the last replay and writes the four phase durations in milliseconds
+ *   (vector start, nu sweeps, distances, strength CSR).
+ *   Errors: ARG, STATE (no timed graph has been captured), CUDA.
+ */
+int amgd_enable_phase_timing(amgd_handle h, int enable);
+int amgd_phase_times(amgd_handle h, float *ms);
+
+/* Free everything the handle owns (synchronises its stream); NULL is a no-op. */
+int amgd_destroy(amgd_handle h);
+
+/* Static text of a status code. */
+const char *amgd_status_string(int status);
+
+/* Message of the last error of h, or of the last failed create on this
+ * thread when h is NULL.  Valid until the next call on h. */
+const char *amgd_last_error(amgd_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMGD_H */

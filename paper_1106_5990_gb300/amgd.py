@@ -1,0 +1,316 @@
+"""Thin ctypes binding of the C ABI in include/amgd.h (libamgd.so).
+
+Every function here marshals arguments and calls the library; every step of
+the strength build runs in the library's CUDA kernels.  The functions keep
+the C names (``amgd_create``, ``amgd_relax``, ...) and return the C status;
+``check`` turns a status into an exception.  ``Handle`` is a small
+convenience wrapper over the same calls that accepts numpy arrays (host
+memory) and torch tensors (device or host memory); torch is used only as a
+carrier of memory and streams.
+
+The library is loaded from the in-tree build (paper_1106_5990_gb300/_lib);
+there is no fallback: if it is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libamgd.so")
+
+AMGD_OK = 0
+AMGD_ERR_ARG = -1
+AMGD_ERR_CSR = -2
+AMGD_ERR_ZERO_DIAG = -3
+AMGD_ERR_CUDA = -4
+AMGD_ERR_OOM = -5
+AMGD_ERR_STATE = -6
+AMGD_ERR_CAPACITY = -7
+AMGD_ERR_TIMEOUT = -8
+AMGD_ERR_UNSUPPORTED = -9
+
+AMGD_MEM_HOST = 0
+AMGD_MEM_DEVICE = 1
+AMGD_SWEEP_JACOBI = 0
+AMGD_SWEEP_MCGS = 1
+AMGD_TARGET_RESIDUAL = 0
+AMGD_TARGET_PLAIN = 1
+AMGD_FP64 = 0
+AMGD_FP32 = 1
+AMGD_BF16 = 2
+
+PRECISIONS = {"fp64": AMGD_FP64, "fp32": AMGD_FP32, "bf16": AMGD_BF16}
+
+# name -> (restype, argtypes); mirrors include/amgd.h
+_P = ctypes.c_void_p
+_i32, _i64, _u64, _f64, _int = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                ctypes.c_double, ctypes.c_int)
+SIGNATURES = {
+    "amgd_create": (_int, [_P, _P, _P, _i64, _i32, _u64, _int, _P]),
+    "amgd_create_batch": (_int, [_i32, _P, _P, _P, _P, _i32, _u64, _int, _P]),
+    "amgd_batch_offsets": (_int, [_P, _P, _P]),
+    "amgd_sizes": (_int, [_P, _P, _P, _P, _P, _P]),
+    "amgd_set_stream": (_int, [_P, _P]),
+    "amgd_set_precision": (_int, [_P, _int]),
+    "amgd_set_target": (_int, [_P, _int]),
+    "amgd_set_weights": (_int, [_P, _P]),
+    "amgd_set_coloring": (_int, [_P, _P, _i32, _int]),
+    "amgd_init_vectors": (_int, [_P, _u64]),
+    "amgd_set_vectors": (_int, [_P, _P, _int]),
+    "amgd_get_vectors": (_int, [_P, _P, _int]),
+    "amgd_set_values": (_int, [_P, _P, _int]),
+    "amgd_relax": (_int, [_P, _i32, _f64, _int]),
+    "amgd_distances": (_int, [_P, _f64, _P, _P, _P, _int]),
+    "amgd_strength": (_int, [_P, _P, _P, _i64, _P, _int]),
+    "amgd_graph_capture": (_int, [_P, _u64, _i32, _f64, _int, _f64, _P, _P, _i64]),
+    "amgd_graph_launch": (_int, [_P]),
+    "amgd_enable_phase_timing": (_int, [_P, _int]),
+    "amgd_phase_times": (_int, [_P, _P]),
+    "amgd_destroy": (_int, [_P]),
+    "amgd_status_string": (ctypes.c_char_p, [_int]),
+    "amgd_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libamgd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libamgd.so is not built (%s); run __graft_entry__.build()"
+                               % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class AmgdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (amgd_status_string(status), msg))
+        self.status = status
+
+
+def amgd_status_string(status: int) -> str:
+    return lib().amgd_status_string(status).decode()
+
+
+def amgd_last_error(h) -> str:
+    return lib().amgd_last_error(h).decode()
+
+
+def check(status: int, h=None) -> int:
+    if status != AMGD_OK:
+        raise AmgdError(status, amgd_last_error(h))
+    return status
+
+
+# thin pass-throughs with the C names (pointers as ints)
+def _wrap(name):
+    def f(*args):
+        return getattr(lib(), name)(*args)
+    f.__name__ = name
+    f.__doc__ = "C ABI %s (include/amgd.h); returns the status." % name
+    return f
+
+
+for _n in SIGNATURES:
+    if _n not in ("amgd_status_string", "amgd_last_error"):
+        globals()[_n] = _wrap(_n)
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def ptr_mem(x):
+    """(address, AMGD_MEM_*) of a contiguous numpy array or torch tensor."""
+    if x is None:
+        return None, AMGD_MEM_HOST
+    if _is_torch(x):
+        assert x.is_contiguous()
+        return x.data_ptr(), (AMGD_MEM_DEVICE if x.is_cuda else AMGD_MEM_HOST)
+    assert x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data, AMGD_MEM_HOST
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Handle:
+    """Owning wrapper of an amgd_handle."""
+
+    def __init__(self, row_ptr, col, val, K: int, seed: int = 0, batch=None):
+        L = lib()
+        self.h = ctypes.c_void_p()
+        if batch is None:
+            if _is_torch(row_ptr):
+                rp, c, v = row_ptr.contiguous(), col.contiguous(), val.contiguous()
+                n = rp.numel() - 1
+            else:
+                rp, c, v = _host(row_ptr, np.int64), _host(col, np.int32), _host(val, np.float64)
+                n = len(rp) - 1
+            self._keep = (rp, c, v)
+            prp, mem = ptr_mem(rp)
+            check(L.amgd_create(prp, ptr_mem(c)[0], ptr_mem(v)[0], n, K, seed, mem,
+                                ctypes.byref(self.h)))
+        else:
+            mats = [(_host(r, np.int64), _host(c, np.int32), _host(v, np.float64))
+                    for r, c, v in batch]
+            nmat = len(mats)
+            arr = lambda xs: (ctypes.c_void_p * nmat)(*[x.ctypes.data for x in xs])
+            rps, cols, vals = arr([m[0] for m in mats]), arr([m[1] for m in mats]), \
+                arr([m[2] for m in mats])
+            ns = np.array([len(m[0]) - 1 for m in mats], dtype=np.int64)
+            self._keep = (mats, ns)
+            check(L.amgd_create_batch(nmat, rps, cols, vals, ns.ctypes.data, K, seed,
+                                      AMGD_MEM_HOST, ctypes.byref(self.h)))
+        n, nnz, E = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        k, nm = ctypes.c_int32(), ctypes.c_int32()
+        check(L.amgd_sizes(self.h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(E),
+                           ctypes.byref(k), ctypes.byref(nm)), self.h)
+        self.n, self.nnz, self.E, self.K, self.nmat = n.value, nnz.value, E.value, k.value, nm.value
+
+    # -- plumbing -------------------------------------------------------------
+    def _ck(self, status):
+        return check(status, self.h)
+
+    def close(self):
+        if self.h:
+            lib().amgd_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def offsets(self):
+        ro = np.zeros(self.nmat + 1, dtype=np.int64)
+        so = np.zeros(self.nmat + 1, dtype=np.int64)
+        self._ck(lib().amgd_batch_offsets(self.h, ro.ctypes.data, so.ctypes.data))
+        return ro, so
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        s = getattr(stream, "cuda_stream", stream)
+        self._ck(lib().amgd_set_stream(self.h, s))
+
+    def set_precision(self, storage):
+        storage = PRECISIONS.get(storage, storage)
+        self._ck(lib().amgd_set_precision(self.h, storage))
+
+    def set_target(self, target):
+        self._ck(lib().amgd_set_target(self.h, target))
+
+    def set_weights(self, w):
+        if w is None:
+            self._ck(lib().amgd_set_weights(self.h, None))
+        else:
+            w = _host(w, np.float64)
+            self._ck(lib().amgd_set_weights(self.h, w.ctypes.data))
+
+    def set_coloring(self, color, ncolors=None):
+        if _is_torch(color):
+            c = color.to(dtype=__import__("torch").int32).contiguous()
+            nc = int(c.max().item()) + 1 if ncolors is None else ncolors
+        else:
+            c = _host(color, np.int32)
+            nc = int(c.max()) + 1 if ncolors is None else ncolors
+        p, mem = ptr_mem(c)
+        self._ck(lib().amgd_set_coloring(self.h, p, nc, mem))
+
+    def init_vectors(self, seed):
+        self._ck(lib().amgd_init_vectors(self.h, seed))
+
+    def set_vectors(self, X):
+        X = X if _is_torch(X) else _host(X, np.float64)
+        p, mem = ptr_mem(X)
+        self._ck(lib().amgd_set_vectors(self.h, p, mem))
+
+    def get_vectors(self, out=None):
+        out = np.empty((self.n, self.K), dtype=np.float64) if out is None else out
+        p, mem = ptr_mem(out)
+        self._ck(lib().amgd_get_vectors(self.h, p, mem))
+        return out
+
+    def set_values(self, val):
+        val = val if _is_torch(val) else _host(val, np.float64)
+        p, mem = ptr_mem(val)
+        self._ck(lib().amgd_set_values(self.h, p, mem))
+
+    # -- the path -------------------------------------------------------------
+    def relax(self, nu, omega, sweep=AMGD_SWEEP_JACOBI):
+        self._ck(lib().amgd_relax(self.h, nu, omega, sweep))
+
+    def distances(self, theta, want=("a", "dist", "ls"), out=None):
+        """Run the edge pass; return dict of requested per-slot outputs (host numpy
+        unless `out` supplies device tensors)."""
+        if out is None:
+            out = {k: np.empty(self.nnz, dtype=np.float64) for k in want}
+        ptrs = [ptr_mem(out.get(k))[0] for k in ("a", "dist", "ls")]
+        mems = {ptr_mem(v)[1] for v in out.values()} or {AMGD_MEM_HOST}
+        assert len(mems) == 1
+        self._ck(lib().amgd_distances(self.h, theta, ptrs[0], ptrs[1], ptrs[2], mems.pop()))
+        return out
+
+    def strength(self, s_row_ptr=None, s_col=None):
+        """Strength CSR; host numpy by default, or into given device tensors."""
+        nnz_s = ctypes.c_int64()
+        if s_row_ptr is None:
+            s_rp = np.empty(self.n + 1, dtype=np.int64)
+            s_col = np.empty(max(self.E, 1), dtype=np.int32)
+            self._ck(lib().amgd_strength(self.h, s_rp.ctypes.data, s_col.ctypes.data, self.E,
+                                         ctypes.byref(nnz_s), AMGD_MEM_HOST))
+            return s_rp, s_col[:nnz_s.value]
+        p_rp, mem = ptr_mem(s_row_ptr)
+        p_col, _ = ptr_mem(s_col)
+        cap = s_col.numel() if _is_torch(s_col) else len(s_col)
+        self._ck(lib().amgd_strength(self.h, p_rp, p_col, cap, None, mem))
+        return s_row_ptr, s_col
+
+    def graph_capture(self, seed, nu, omega, sweep, theta, s_row_ptr, s_col):
+        cap = s_col.numel() if _is_torch(s_col) else len(s_col)
+        self._ck(lib().amgd_graph_capture(self.h, seed, nu, omega, sweep, theta,
+                                          ptr_mem(s_row_ptr)[0], ptr_mem(s_col)[0], cap))
+
+    def graph_launch(self):
+        self._ck(lib().amgd_graph_launch(self.h))
+
+    def enable_phase_timing(self, enable=True):
+        self._ck(lib().amgd_enable_phase_timing(self.h, int(enable)))
+
+    def phase_times(self):
+        """ms of (vector start, sweeps, distances, strength) of the last replay."""
+        ms = (ctypes.c_float * 4)()
+        self._ck(lib().amgd_phase_times(self.h, ms))
+        return list(ms)
+
+
+def header_symbols(header_path: str | None = None) -> list:
+    """Names of the functions declared in include/amgd.h."""
+    import re
+    if header_path is None:
+        header_path = os.path.join(os.path.dirname(_HERE), "include", "amgd.h")
+    text = open(header_path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(amgd_[a-z_]+)\s*\(", text)))

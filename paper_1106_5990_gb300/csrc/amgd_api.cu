@@ -1,0 +1,816 @@
+// amgd_api.cu -- host side of the C ABI declared in include/amgd.h:
+// argument and CSR validation, device memory of a handle, the row
+// permutation that makes every Gauss-Seidel color a contiguous row range,
+// kernel dispatch, and CUDA-graph capture of a whole build.
+#include "../../include/amgd.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "amgd_internal.cuh"
+
+using namespace amgd;
+
+struct amgd_ctx {
+    int device = 0;
+    int64_t n = 0, nnz = 0, E = 0;
+    int32_t K = 0, nmat = 1;
+    int storage = ST_FP64, target = AMGD_TARGET_RESIDUAL;
+    std::vector<int64_t> row_off, slot_off;
+    std::vector<int32_t> h_rp, h_col;          // caller CSR pattern (int32)
+    std::vector<int32_t> h_diag_slot;           // slot of each row's diagonal
+    // device: caller numbering
+    int32_t *rp_o = nullptr, *col_o = nullptr;
+    double *val_o = nullptr;
+    int64_t *mat_off = nullptr;
+    int32_t *diag_slot = nullptr;                // slot of each row's diagonal
+    uint32_t *err_word = nullptr;                // device error bits of value checks
+    // device: row-permuted matrix (aliases of the caller arrays without coloring)
+    int32_t *rp_p = nullptr, *col_p = nullptr, *perm = nullptr;
+    double *val64 = nullptr;
+    float *val32 = nullptr;
+    std::vector<int64_t> color_start;           // permuted row start of each color
+    // vectors
+    void *x[2] = {nullptr, nullptr};
+    int cur = 0;
+    std::vector<double> h_w;
+    double *w64 = nullptr;
+    float *w32 = nullptr;
+    // outputs
+    void *a = nullptr, *ls = nullptr;
+    uint8_t *flag = nullptr;
+    int32_t *count = nullptr, *tile = nullptr;
+    int64_t *s_rp_tmp = nullptr;
+    int32_t *s_col_tmp = nullptr;
+    double *tmp64 = nullptr;                     // n*K or nnz doubles, staging
+    size_t tmp64_len = 0;
+    bool have_dist = false;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_cur_after = 0;
+    bool phase_timing = false, graph_timed = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int V_of(int st) { return st == ST_FP64 ? 2 : (st == ST_FP32 ? 4 : 8); }
+size_t esize(int st) { return st == ST_FP64 ? 8 : (st == ST_FP32 ? 4 : 2); }
+
+int G_of(int st, int K)
+{
+    const int V = V_of(st);
+    const int need = (K + V - 1) / V;
+    int G = 1;
+    while (G < need) G <<= 1;
+    return G;
+}
+int Kp_of(int st, int K) { return G_of(st, K) * V_of(st); }
+
+int fail(amgd_ctx *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg; else g_create_err = msg;
+    return code;
+}
+
+int cuda_fail(amgd_ctx *h, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, e == cudaErrorMemoryAllocation ? AMGD_ERR_OOM : AMGD_ERR_CUDA, m);
+}
+
+#define CK(h, expr)                                              \
+    do {                                                         \
+        cudaError_t e__ = (expr);                                \
+        if (e__ != cudaSuccess) return cuda_fail((h), e__, #expr); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+cudaError_t dfree(void *p) { return p ? cudaFree(p) : cudaSuccess; }
+
+// copy `bytes` from host or device memory `src` into host vector storage
+cudaError_t fetch(void *dst, const void *src, size_t bytes, int mem)
+{
+    if (bytes == 0) return cudaSuccess;
+    if (mem == AMGD_MEM_HOST) {
+        std::memcpy(dst, src, bytes);
+        return cudaSuccess;
+    }
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+}
+
+// CSR check of one matrix: returns AMGD_OK or an error with message
+int check_csr(const int64_t *rp, const int32_t *col, const double *val, int64_t n,
+              std::vector<int32_t> &marker, std::vector<int32_t> &diag_slot, int64_t slot_base,
+              std::string &msg)
+{
+    if (rp[0] != 0) { msg = "row_ptr[0] != 0"; return AMGD_ERR_CSR; }
+    for (int64_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) { msg = "row_ptr decreases at row " + std::to_string(i); return AMGD_ERR_CSR; }
+    marker.assign((size_t)n, -1);
+    diag_slot.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t d = -1;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            const int64_t j = col[p];
+            if (j < 0 || j >= n) { msg = "column out of range in row " + std::to_string(i); return AMGD_ERR_CSR; }
+            if (!std::isfinite(val[p])) { msg = "non-finite value in row " + std::to_string(i); return AMGD_ERR_CSR; }
+            if (marker[(size_t)j] == (int32_t)i) { msg = "duplicate column in row " + std::to_string(i); return AMGD_ERR_CSR; }
+            marker[(size_t)j] = (int32_t)i;
+            if (j == i) d = p;
+        }
+        if (d < 0 || val[d] == 0.0) { msg = "missing or zero diagonal in row " + std::to_string(i); return AMGD_ERR_ZERO_DIAG; }
+        diag_slot[(size_t)i] = (int32_t)(slot_base + d);
+    }
+    return AMGD_OK;
+}
+
+cudaError_t ensure_tmp64(amgd_ctx *h, size_t count)
+{
+    if (h->tmp64_len >= count && h->tmp64) return cudaSuccess;
+    dfree(h->tmp64);
+    h->tmp64_len = 0;
+    cudaError_t e = dalloc(&h->tmp64, count);
+    if (e == cudaSuccess) h->tmp64_len = count;
+    return e;
+}
+
+// allocate the two vector buffers and the weights for the current storage
+int alloc_vectors(amgd_ctx *h, int st, void **x0, void **x1)
+{
+    const size_t bytes = (size_t)h->n * Kp_of(st, h->K) * esize(st);
+    CK(h, cudaMalloc(x0, bytes ? bytes : 16));
+    cudaError_t e = cudaMalloc(x1, bytes ? bytes : 16);
+    if (e != cudaSuccess) { cudaFree(*x0); *x0 = nullptr; return cuda_fail(h, e, "cudaMalloc(x1)"); }
+    return AMGD_OK;
+}
+
+int upload_weights(amgd_ctx *h)
+{
+    const int Kp = Kp_of(ST_FP64, h->K) > Kp_of(ST_FP32, h->K) ? Kp_of(ST_FP64, h->K)
+                                                                : Kp_of(ST_FP32, h->K);
+    const int KpMax = Kp > Kp_of(ST_BF16, h->K) ? Kp : Kp_of(ST_BF16, h->K);
+    std::vector<double> w64((size_t)KpMax, 0.0);
+    std::vector<float> w32((size_t)KpMax, 0.0f);
+    for (int k = 0; k < h->K; ++k) { w64[(size_t)k] = h->h_w[(size_t)k]; w32[(size_t)k] = (float)h->h_w[(size_t)k]; }
+    if (!h->w64) CK(h, dalloc(&h->w64, (size_t)KpMax));
+    if (!h->w32) CK(h, dalloc(&h->w32, (size_t)KpMax));
+    CK(h, cudaMemcpyAsync(h->w64, w64.data(), KpMax * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->w32, w32.data(), KpMax * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return AMGD_OK;
+}
+
+// (re)build the FP64 and FP32 permuted value arrays from h->val_o
+int permute_values(amgd_ctx *h)
+{
+    if (h->perm) {
+        CK(h, launch_permute_values(h->val_o, h->rp_o, h->perm, h->rp_p, h->val64, h->val32,
+                                    (int32_t)h->n, h->stream));
+    } else {
+        if (h->val64 != h->val_o)
+            CK(h, cudaMemcpyAsync(h->val64, h->val_o, h->nnz * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        if (h->val32)
+            CK(h, launch_permute_values(h->val_o, h->rp_o, nullptr, h->rp_o, nullptr, h->val32,
+                                        (int32_t)h->n, h->stream));
+    }
+    return AMGD_OK;
+}
+
+int run_init(amgd_ctx *h, uint64_t seed, cudaStream_t s)
+{
+    InitArgs a;
+    a.x = h->x[h->cur];
+    a.perm = h->perm;
+    a.mat_off = h->mat_off;
+    a.nmat = h->nmat;
+    a.n = (int32_t)h->n;
+    a.K = h->K;
+    a.Kp = Kp_of(h->storage, h->K);
+    a.seed = seed;
+    CK(h, launch_init(h->storage, a, s));
+    h->have_dist = false;
+    return AMGD_OK;
+}
+
+int run_relax(amgd_ctx *h, int32_t nu, double omega, int sweep, cudaStream_t s)
+{
+    const int G = G_of(h->storage, h->K);
+    RelaxArgs a;
+    a.rp = h->rp_p;
+    a.col = h->col_p;
+    a.val = h->storage == ST_FP64 ? (const void *)h->val64 : (const void *)h->val32;
+    a.Kp = Kp_of(h->storage, h->K);
+    a.omega = omega;
+    for (int32_t it = 0; it < nu; ++it) {
+        a.xold = h->x[h->cur];
+        a.xnew = h->x[1 - h->cur];
+        if (sweep == AMGD_SWEEP_JACOBI) {
+            a.r0 = 0;
+            a.r1 = (int32_t)h->n;
+            a.split = 0;
+            CK(h, launch_relax(h->storage, G, a, s));
+        } else {
+            for (size_t c = 0; c + 1 < h->color_start.size(); ++c) {
+                a.r0 = (int32_t)h->color_start[c];
+                a.r1 = (int32_t)h->color_start[c + 1];
+                a.split = a.r0;
+                CK(h, launch_relax(h->storage, G, a, s));
+            }
+        }
+        h->cur = 1 - h->cur;
+    }
+    if (nu > 0) h->have_dist = false;
+    return AMGD_OK;
+}
+
+int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
+{
+    EdgeArgs a;
+    a.rp = h->rp_p;
+    a.col = h->col_p;
+    a.val = h->storage == ST_FP64 ? (const void *)h->val64 : (const void *)h->val32;
+    a.val64 = h->val64;
+    a.x = h->x[h->cur];
+    a.w = h->storage == ST_FP64 ? (const void *)h->w64 : (const void *)h->w32;
+    a.w64 = h->w64;
+    a.perm = h->perm;
+    a.rp_orig = h->rp_o;
+    a.a_out = h->a;
+    a.ls_out = h->ls;
+    a.flag_out = h->flag;
+    a.count_out = h->count;
+    a.n = (int32_t)h->n;
+    a.Kp = Kp_of(h->storage, h->K);
+    a.target = h->target;
+    a.theta = theta;
+    CK(h, launch_edge(h->storage, G_of(h->storage, h->K), a, s));
+    h->have_dist = true;
+    return AMGD_OK;
+}
+
+// (re)allocate the per-slot a/LS buffers for the arithmetic type of `st`
+int alloc_slot_outputs(amgd_ctx *h, int st)
+{
+    dfree(h->a);
+    dfree(h->ls);
+    h->a = h->ls = nullptr;
+    const size_t es = st == ST_FP64 ? 8 : 4;
+    CK(h, cudaMalloc(&h->a, (h->nnz ? h->nnz : 1) * es));
+    CK(h, cudaMalloc(&h->ls, (h->nnz ? h->nnz : 1) * es));
+    return AMGD_OK;
+}
+
+int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const *col_in,
+                const double *const *val_in, const int64_t *n_in, int32_t K, uint64_t seed,
+                int mem, amgd_handle *out)
+{
+    if (!out) return fail(nullptr, AMGD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nmat < 1) return fail(nullptr, AMGD_ERR_ARG, "nmat < 1");
+    if (K < 1 || K > 64) return fail(nullptr, AMGD_ERR_UNSUPPORTED, "K must be in 1..64");
+    if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(nullptr, AMGD_ERR_ARG, "bad mem");
+    if (!rp_in || !col_in || !val_in || !n_in) return fail(nullptr, AMGD_ERR_ARG, "NULL array list");
+
+    // gather every matrix on the host, validate, concatenate block-diagonally
+    std::vector<int64_t> row_off(1, 0), slot_off(1, 0);
+    for (int32_t b = 0; b < nmat; ++b) {
+        if (n_in[b] < 0) return fail(nullptr, AMGD_ERR_ARG, "n < 0");
+        row_off.push_back(row_off.back() + n_in[b]);
+    }
+    const int64_t n = row_off.back();
+    if (n >= (int64_t)1 << 31) return fail(nullptr, AMGD_ERR_UNSUPPORTED, "n >= 2^31");
+    std::vector<int32_t> h_rp(1, 0), h_col, diag_slot;
+    std::vector<double> h_val;
+    std::vector<int32_t> marker, dslot;
+    for (int32_t b = 0; b < nmat; ++b) {
+        const int64_t nb = n_in[b];
+        if (!rp_in[b]) return fail(nullptr, AMGD_ERR_ARG, "NULL row_ptr");
+        std::vector<int64_t> rp((size_t)nb + 1);
+        cudaError_t e = fetch(rp.data(), rp_in[b], (nb + 1) * sizeof(int64_t), mem);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "copy row_ptr");
+        if (rp[0] != 0) return fail(nullptr, AMGD_ERR_CSR, "row_ptr[0] != 0");
+        const int64_t nnzb = rp[(size_t)nb];
+        if (nnzb < 0) return fail(nullptr, AMGD_ERR_CSR, "negative nnz");
+        if (slot_off.back() + nnzb >= ((int64_t)1 << 31) - 16)
+            return fail(nullptr, AMGD_ERR_UNSUPPORTED, "nnz >= 2^31");
+        if (nnzb > 0 && (!col_in[b] || !val_in[b])) return fail(nullptr, AMGD_ERR_ARG, "NULL col/val");
+        std::vector<int32_t> col((size_t)nnzb);
+        std::vector<double> val((size_t)nnzb);
+        e = fetch(col.data(), col_in[b], nnzb * sizeof(int32_t), mem);
+        if (e == cudaSuccess) e = fetch(val.data(), val_in[b], nnzb * sizeof(double), mem);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "copy col/val");
+        std::string msg;
+        const int rc = check_csr(rp.data(), col.data(), val.data(), nb, marker, dslot,
+                                 slot_off.back(), msg);
+        if (rc != AMGD_OK) return fail(nullptr, rc, "matrix " + std::to_string(b) + ": " + msg);
+        const int64_t ro = row_off[(size_t)b], so = slot_off.back();
+        for (int64_t i = 1; i <= nb; ++i) h_rp.push_back((int32_t)(so + rp[(size_t)i]));
+        for (int64_t p = 0; p < nnzb; ++p) h_col.push_back((int32_t)(ro + col[(size_t)p]));
+        h_val.insert(h_val.end(), val.begin(), val.end());
+        diag_slot.insert(diag_slot.end(), dslot.begin(), dslot.end());
+        slot_off.push_back(so + nnzb);
+    }
+
+    amgd_ctx *h = new amgd_ctx();
+    h->n = n;
+    h->nnz = slot_off.back();
+    h->E = h->nnz - n;
+    h->K = K;
+    h->nmat = nmat;
+    h->row_off = row_off;
+    h->slot_off = slot_off;
+    h->h_rp = std::move(h_rp);
+    h->h_col = std::move(h_col);
+    h->h_diag_slot = std::move(diag_slot);
+    h->h_w.assign((size_t)K, 1.0);
+    cudaGetDevice(&h->device);
+
+    auto bail = [&](int rc) {
+        g_create_err = h->err;
+        amgd_destroy(h);
+        return rc;
+    };
+    int rc;
+#define TRY(expr)                                                          \
+    do {                                                                   \
+        cudaError_t e__ = (expr);                                          \
+        if (e__ != cudaSuccess) return bail(cuda_fail(h, e__, #expr));     \
+    } while (0)
+    TRY(dalloc(&h->rp_o, (size_t)n + 1));
+    TRY(dalloc(&h->col_o, (size_t)h->nnz));
+    TRY(dalloc(&h->val_o, (size_t)h->nnz));
+    TRY(dalloc(&h->mat_off, (size_t)nmat + 1));
+    TRY(cudaMemcpy(h->rp_o, h->h_rp.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (h->nnz) {
+        TRY(cudaMemcpy(h->col_o, h->h_col.data(), h->nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+        TRY(cudaMemcpy(h->val_o, h_val.data(), h->nnz * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    TRY(cudaMemcpy(h->mat_off, row_off.data(), (nmat + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    TRY(dalloc(&h->diag_slot, (size_t)n));
+    TRY(dalloc(&h->err_word, 1));
+    if (n) TRY(cudaMemcpy(h->diag_slot, h->h_diag_slot.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    h->rp_p = h->rp_o;
+    h->col_p = h->col_o;
+    h->val64 = h->val_o;
+    h->color_start = {0, n};
+    TRY(dalloc(&h->flag, (size_t)h->nnz));
+    TRY(dalloc(&h->count, (size_t)n));
+    TRY(dalloc(&h->tile, (size_t)(n / kTileRows + 2)));
+    if ((rc = alloc_slot_outputs(h, ST_FP64)) != AMGD_OK) return bail(rc);
+    if ((rc = alloc_vectors(h, ST_FP64, &h->x[0], &h->x[1])) != AMGD_OK) return bail(rc);
+    if ((rc = upload_weights(h)) != AMGD_OK) return bail(rc);
+    if ((rc = run_init(h, seed, h->stream)) != AMGD_OK) return bail(rc);
+    TRY(cudaStreamSynchronize(h->stream));
+#undef TRY
+    *out = h;
+    return AMGD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int amgd_create(const int64_t *row_ptr, const int32_t *col, const double *val, int64_t n,
+                int32_t K, uint64_t seed, int mem, amgd_handle *out)
+{
+    return create_impl(1, &row_ptr, &col, &val, &n, K, seed, mem, out);
+}
+
+int amgd_create_batch(int32_t nmat, const int64_t *const *row_ptr, const int32_t *const *col,
+                      const double *const *val, const int64_t *n, int32_t K, uint64_t seed,
+                      int mem, amgd_handle *out)
+{
+    return create_impl(nmat, row_ptr, col, val, n, K, seed, mem, out);
+}
+
+int amgd_batch_offsets(amgd_handle h, int64_t *row_off, int64_t *slot_off)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (row_off) std::memcpy(row_off, h->row_off.data(), h->row_off.size() * sizeof(int64_t));
+    if (slot_off) std::memcpy(slot_off, h->slot_off.data(), h->slot_off.size() * sizeof(int64_t));
+    return AMGD_OK;
+}
+
+int amgd_sizes(amgd_handle h, int64_t *n, int64_t *nnz, int64_t *E, int32_t *K, int32_t *nmat)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (n) *n = h->n;
+    if (nnz) *nnz = h->nnz;
+    if (E) *E = h->E;
+    if (K) *K = h->K;
+    if (nmat) *nmat = h->nmat;
+    return AMGD_OK;
+}
+
+int amgd_set_stream(amgd_handle h, void *stream)
+{
+    if (!h) return AMGD_ERR_ARG;
+    h->stream = (cudaStream_t)stream;
+    return AMGD_OK;
+}
+
+int amgd_set_precision(amgd_handle h, int storage)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (storage != AMGD_FP64 && storage != AMGD_FP32 && storage != AMGD_BF16)
+        return fail(h, AMGD_ERR_ARG, "unknown storage precision");
+    if (storage == h->storage) return AMGD_OK;
+    if (storage != ST_FP64 && !h->val32) {
+        CK(h, dalloc(&h->val32, (size_t)h->nnz));
+        int rc = permute_values(h);
+        if (rc != AMGD_OK) return rc;
+    }
+    // re-layout the current vectors: export to caller-order doubles, import
+    CK(h, ensure_tmp64(h, (size_t)h->n * h->K));
+    CK(h, launch_export(h->storage, h->x[h->cur], h->tmp64, h->perm, (int32_t)h->n, h->K,
+                        Kp_of(h->storage, h->K), h->stream));
+    void *nx[2] = {nullptr, nullptr};
+    int rc = alloc_vectors(h, storage, &nx[0], &nx[1]);
+    if (rc != AMGD_OK) return rc;
+    cudaError_t e = launch_import(storage, h->tmp64, nx[0], h->perm, (int32_t)h->n, h->K,
+                                  Kp_of(storage, h->K), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        cudaFree(nx[0]);
+        cudaFree(nx[1]);
+        return cuda_fail(h, e, "import vectors");
+    }
+    const bool slot_type_changes = (storage == ST_FP64) != (h->storage == ST_FP64);
+    cudaFree(h->x[0]);
+    cudaFree(h->x[1]);
+    h->x[0] = nx[0];
+    h->x[1] = nx[1];
+    h->cur = 0;
+    h->storage = storage;
+    if (slot_type_changes) {
+        rc = alloc_slot_outputs(h, storage);
+        if (rc != AMGD_OK) return rc;
+    }
+    h->have_dist = false;
+    return AMGD_OK;
+}
+
+int amgd_set_target(amgd_handle h, int target)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (target != AMGD_TARGET_RESIDUAL && target != AMGD_TARGET_PLAIN)
+        return fail(h, AMGD_ERR_ARG, "unknown target");
+    h->target = target;
+    h->have_dist = false;
+    return AMGD_OK;
+}
+
+int amgd_set_weights(amgd_handle h, const double *w)
+{
+    if (!h) return AMGD_ERR_ARG;
+    std::vector<double> nw((size_t)h->K, 1.0);
+    if (w) {
+        for (int k = 0; k < h->K; ++k) {
+            if (!(w[k] > 0.0) || !std::isfinite(w[k])) return fail(h, AMGD_ERR_ARG, "weights must be > 0 and finite");
+            nw[(size_t)k] = w[k];
+        }
+    }
+    h->h_w = nw;
+    h->have_dist = false;
+    return upload_weights(h);
+}
+
+int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int mem)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (ncolors < 1 || (!color && h->n > 0)) return fail(h, AMGD_ERR_ARG, "bad coloring arguments");
+    const int64_t n = h->n;
+    std::vector<int32_t> c((size_t)n);
+    CK(h, fetch(c.data(), color, n * sizeof(int32_t), mem));
+    std::vector<int64_t> start((size_t)ncolors + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (c[(size_t)i] < 0 || c[(size_t)i] >= ncolors) return fail(h, AMGD_ERR_ARG, "color out of range");
+        ++start[(size_t)c[(size_t)i] + 1];
+    }
+    for (int32_t k = 0; k < ncolors; ++k) start[(size_t)k + 1] += start[(size_t)k];
+    // stable counting sort: perm[new] = old, inv[old] = new
+    std::vector<int32_t> perm((size_t)n), inv((size_t)n);
+    std::vector<int64_t> next(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t r = next[(size_t)c[(size_t)i]]++;
+        perm[(size_t)r] = (int32_t)i;
+        inv[(size_t)i] = (int32_t)r;
+    }
+    std::vector<int32_t> rp_p((size_t)n + 1, 0), col_p((size_t)h->nnz);
+    for (int64_t r = 0; r < n; ++r) {
+        const int32_t o = perm[(size_t)r];
+        const int32_t len = h->h_rp[(size_t)o + 1] - h->h_rp[(size_t)o];
+        rp_p[(size_t)r + 1] = rp_p[(size_t)r] + len;
+        for (int32_t k = 0; k < len; ++k)
+            col_p[(size_t)(rp_p[(size_t)r] + k)] = inv[(size_t)h->h_col[(size_t)(h->h_rp[(size_t)o] + k)]];
+    }
+    // current vectors out in caller order before the layout changes
+    CK(h, ensure_tmp64(h, (size_t)n * h->K));
+    CK(h, launch_export(h->storage, h->x[h->cur], h->tmp64, h->perm, (int32_t)n, h->K,
+                        Kp_of(h->storage, h->K), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (!h->perm) {
+        CK(h, dalloc(&h->perm, (size_t)n));
+        CK(h, dalloc(&h->rp_p, (size_t)n + 1));
+        CK(h, dalloc(&h->col_p, (size_t)h->nnz));
+        CK(h, dalloc(&h->val64, (size_t)h->nnz));
+    }
+    CK(h, cudaMemcpy(h->perm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->rp_p, rp_p.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->col_p, col_p.data(), h->nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    int rc = permute_values(h);
+    if (rc != AMGD_OK) return rc;
+    CK(h, launch_import(h->storage, h->tmp64, h->x[h->cur], h->perm, (int32_t)n, h->K,
+                        Kp_of(h->storage, h->K), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->color_start = start;
+    h->have_dist = false;
+    return AMGD_OK;
+}
+
+int amgd_init_vectors(amgd_handle h, uint64_t seed)
+{
+    if (!h) return AMGD_ERR_ARG;
+    return run_init(h, seed, h->stream);
+}
+
+int amgd_set_vectors(amgd_handle h, const double *X, int mem)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (!X && h->n) return fail(h, AMGD_ERR_ARG, "X is NULL");
+    const size_t cnt = (size_t)h->n * h->K;
+    const double *src = X;
+    if (mem == AMGD_MEM_HOST) {
+        CK(h, ensure_tmp64(h, cnt));
+        CK(h, cudaMemcpyAsync(h->tmp64, X, cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        src = h->tmp64;
+    } else if (mem != AMGD_MEM_DEVICE) {
+        return fail(h, AMGD_ERR_ARG, "bad mem");
+    }
+    CK(h, launch_import(h->storage, src, h->x[h->cur], h->perm, (int32_t)h->n, h->K,
+                        Kp_of(h->storage, h->K), h->stream));
+    if (mem == AMGD_MEM_HOST) CK(h, cudaStreamSynchronize(h->stream));
+    h->have_dist = false;
+    return AMGD_OK;
+}
+
+int amgd_get_vectors(amgd_handle h, double *X, int mem)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (!X && h->n) return fail(h, AMGD_ERR_ARG, "X is NULL");
+    const size_t cnt = (size_t)h->n * h->K;
+    if (mem == AMGD_MEM_DEVICE) {
+        CK(h, launch_export(h->storage, h->x[h->cur], X, h->perm, (int32_t)h->n, h->K,
+                            Kp_of(h->storage, h->K), h->stream));
+        return AMGD_OK;
+    }
+    if (mem != AMGD_MEM_HOST) return fail(h, AMGD_ERR_ARG, "bad mem");
+    CK(h, ensure_tmp64(h, cnt));
+    CK(h, launch_export(h->storage, h->x[h->cur], h->tmp64, h->perm, (int32_t)h->n, h->K,
+                        Kp_of(h->storage, h->K), h->stream));
+    CK(h, cudaMemcpyAsync(X, h->tmp64, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return AMGD_OK;
+}
+
+int amgd_set_values(amgd_handle h, const double *val, int mem)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (!val && h->nnz) return fail(h, AMGD_ERR_ARG, "val is NULL");
+    if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
+    // stage on the device, check there, then swap the staging buffer in
+    CK(h, ensure_tmp64(h, (size_t)h->nnz));
+    CK(h, cudaMemcpyAsync(h->tmp64, val, h->nnz * sizeof(double),
+                          mem == AMGD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          h->stream));
+    CK(h, cudaMemsetAsync(h->err_word, 0, sizeof(uint32_t), h->stream));
+    CK(h, launch_check_values(h->tmp64, h->nnz, h->diag_slot, (int32_t)h->n, h->err_word, h->stream));
+    uint32_t err = 0;
+    CK(h, cudaMemcpyAsync(&err, h->err_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (err & 1u) return fail(h, AMGD_ERR_CSR, "non-finite value");
+    if (err & 2u) return fail(h, AMGD_ERR_ZERO_DIAG, "zero diagonal");
+    double *old = h->val_o;
+    h->val_o = h->tmp64;
+    h->tmp64 = old;
+    h->tmp64_len = (size_t)h->nnz;
+    if (!h->perm) h->val64 = h->val_o;
+    int rc = permute_values(h);
+    if (rc != AMGD_OK) return rc;
+    h->have_dist = false;
+    return AMGD_OK;
+}
+
+int amgd_relax(amgd_handle h, int32_t nu, double omega, int sweep_type)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (nu < 0 || !std::isfinite(omega)) return fail(h, AMGD_ERR_ARG, "nu < 0 or omega not finite");
+    if (sweep_type != AMGD_SWEEP_JACOBI && sweep_type != AMGD_SWEEP_MCGS)
+        return fail(h, AMGD_ERR_ARG, "unknown sweep type");
+    if (sweep_type == AMGD_SWEEP_MCGS && !h->perm)
+        return fail(h, AMGD_ERR_STATE, "MCGS needs amgd_set_coloring first");
+    return run_relax(h, nu, omega, sweep_type, h->stream);
+}
+
+int amgd_distances(amgd_handle h, double theta, double *a, double *dist, double *ls, int mem)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(h, AMGD_ERR_ARG, "theta must be finite and >= 0");
+    if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
+    int rc = run_edge(h, theta, h->stream);
+    if (rc != AMGD_OK) return rc;
+    double *outs[3] = {a, dist, ls};
+    if (mem == AMGD_MEM_DEVICE) {
+        if (a || dist || ls)
+            CK(h, launch_export_slots(h->storage, h->a, h->ls, a, dist, ls, h->nnz, h->stream));
+        return AMGD_OK;
+    }
+    for (int k = 0; k < 3; ++k) {
+        if (!outs[k]) continue;
+        CK(h, ensure_tmp64(h, (size_t)h->nnz));
+        CK(h, launch_export_slots(h->storage, h->a, h->ls, k == 0 ? h->tmp64 : nullptr,
+                                  k == 1 ? h->tmp64 : nullptr, k == 2 ? h->tmp64 : nullptr,
+                                  h->nnz, h->stream));
+        CK(h, cudaMemcpyAsync(outs[k], h->tmp64, h->nnz * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return AMGD_OK;
+}
+
+int amgd_strength(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap,
+                  int64_t *nnz_s, int mem)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (!h->have_dist) return fail(h, AMGD_ERR_STATE, "amgd_distances must run first");
+    if (!s_row_ptr || (!s_col && cap > 0) || cap < 0) return fail(h, AMGD_ERR_ARG, "bad output buffers");
+    if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
+    if (mem == AMGD_MEM_DEVICE && cap >= h->E) {
+        CK(h, launch_strength(h->count, h->rp_o, h->col_o, h->flag, (int32_t)h->n, h->tile,
+                              s_row_ptr, s_col, h->stream));
+        if (nnz_s) {
+            CK(h, cudaMemcpyAsync(nnz_s, s_row_ptr + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        }
+        return AMGD_OK;
+    }
+    if (!h->s_rp_tmp) CK(h, dalloc(&h->s_rp_tmp, (size_t)h->n + 1));
+    if (!h->s_col_tmp) CK(h, dalloc(&h->s_col_tmp, (size_t)(h->E > 0 ? h->E : 1)));
+    CK(h, launch_strength(h->count, h->rp_o, h->col_o, h->flag, (int32_t)h->n, h->tile,
+                          h->s_rp_tmp, h->s_col_tmp, h->stream));
+    int64_t total = 0;
+    CK(h, cudaMemcpyAsync(&total, h->s_rp_tmp + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (nnz_s) *nnz_s = total;
+    if (total > cap) return fail(h, AMGD_ERR_CAPACITY, "strength output needs " + std::to_string(total) + " columns");
+    const cudaMemcpyKind k = mem == AMGD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(h, cudaMemcpyAsync(s_row_ptr, h->s_rp_tmp, (h->n + 1) * sizeof(int64_t), k, h->stream));
+    if (total) CK(h, cudaMemcpyAsync(s_col, h->s_col_tmp, total * sizeof(int32_t), k, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return AMGD_OK;
+}
+
+int amgd_graph_capture(amgd_handle h, uint64_t seed, int32_t nu, double omega, int sweep_type,
+                       double theta, int64_t *s_row_ptr, int32_t *s_col, int64_t cap)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (nu < 0 || !std::isfinite(omega)) return fail(h, AMGD_ERR_ARG, "nu < 0 or omega not finite");
+    if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(h, AMGD_ERR_ARG, "theta must be finite and >= 0");
+    if (sweep_type != AMGD_SWEEP_JACOBI && sweep_type != AMGD_SWEEP_MCGS)
+        return fail(h, AMGD_ERR_ARG, "unknown sweep type");
+    if (sweep_type == AMGD_SWEEP_MCGS && !h->perm)
+        return fail(h, AMGD_ERR_STATE, "MCGS needs amgd_set_coloring first");
+    if (!s_row_ptr || (!s_col && h->E > 0)) return fail(h, AMGD_ERR_ARG, "bad output buffers");
+    if (cap < h->E) return fail(h, AMGD_ERR_CAPACITY, "graph capture needs cap >= E");
+    if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    CK(h, cudaStreamSynchronize(h->stream));
+    const int cur0 = h->cur;
+    h->cur = 0;
+    if (h->phase_timing && !h->ev[0])
+        for (auto &e : h->ev) CK(h, cudaEventCreate(&e));
+    const bool timed = h->phase_timing;
+    auto mark = [&](int k) {
+        return timed ? cudaEventRecordWithFlags(h->ev[k], h->cap_stream, cudaEventRecordExternal)
+                     : cudaSuccess;
+    };
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = AMGD_OK;
+    cudaError_t me = mark(0);
+    if (me == cudaSuccess) rc = run_init(h, seed, h->cap_stream);
+    if (me == cudaSuccess && rc == AMGD_OK) me = mark(1);
+    if (me == cudaSuccess && rc == AMGD_OK) rc = run_relax(h, nu, omega, sweep_type, h->cap_stream);
+    if (me == cudaSuccess && rc == AMGD_OK) me = mark(2);
+    if (me == cudaSuccess && rc == AMGD_OK) rc = run_edge(h, theta, h->cap_stream);
+    if (me == cudaSuccess && rc == AMGD_OK) me = mark(3);
+    if (me == cudaSuccess && rc == AMGD_OK) {
+        cudaError_t e = launch_strength(h->count, h->rp_o, h->col_o, h->flag, (int32_t)h->n,
+                                        h->tile, s_row_ptr, s_col, h->cap_stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "launch_strength (capture)");
+    }
+    if (me == cudaSuccess && rc == AMGD_OK) me = mark(4);
+    if (me != cudaSuccess && rc == AMGD_OK) rc = cuda_fail(h, me, "cudaEventRecordWithFlags (capture)");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    h->graph_cur_after = h->cur;
+    h->cur = cur0;
+    h->have_dist = false;
+    if (rc != AMGD_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    h->graph = g;
+    CK(h, cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    h->graph_timed = timed;
+    return AMGD_OK;
+}
+
+int amgd_enable_phase_timing(amgd_handle h, int enable)
+{
+    if (!h) return AMGD_ERR_ARG;
+    h->phase_timing = enable != 0;
+    return AMGD_OK;
+}
+
+int amgd_phase_times(amgd_handle h, float *ms)
+{
+    if (!h || !ms) return AMGD_ERR_ARG;
+    if (!h->gexec || !h->graph_timed) return fail(h, AMGD_ERR_STATE, "no timed graph captured");
+    CK(h, cudaEventSynchronize(h->ev[4]));
+    for (int k = 0; k < 4; ++k) CK(h, cudaEventElapsedTime(&ms[k], h->ev[k], h->ev[k + 1]));
+    return AMGD_OK;
+}
+
+int amgd_graph_launch(amgd_handle h)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (!h->gexec) return fail(h, AMGD_ERR_STATE, "no captured graph");
+    CK(h, cudaGraphLaunch(h->gexec, h->stream));
+    h->cur = h->graph_cur_after;
+    h->have_dist = true;
+    return AMGD_OK;
+}
+
+int amgd_destroy(amgd_handle h)
+{
+    if (!h) return AMGD_OK;
+    if (h->stream || h->x[0]) cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (auto e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->perm) {
+        dfree(h->perm);
+        dfree(h->rp_p);
+        dfree(h->col_p);
+        dfree(h->val64);
+    }
+    void *ptrs[] = {h->rp_o, h->col_o, h->val_o, h->mat_off, h->diag_slot, h->err_word, h->val32, h->x[0], h->x[1],
+                    h->w64, h->w32, h->a, h->ls, h->flag, h->count, h->tile, h->s_rp_tmp,
+                    h->s_col_tmp, h->tmp64};
+    for (void *p : ptrs) dfree(p);
+    delete h;
+    return AMGD_OK;
+}
+
+const char *amgd_status_string(int status)
+{
+    switch (status) {
+    case AMGD_OK: return "AMGD_OK";
+    case AMGD_ERR_ARG: return "AMGD_ERR_ARG: bad argument";
+    case AMGD_ERR_CSR: return "AMGD_ERR_CSR: malformed CSR matrix";
+    case AMGD_ERR_ZERO_DIAG: return "AMGD_ERR_ZERO_DIAG: missing or zero diagonal";
+    case AMGD_ERR_CUDA: return "AMGD_ERR_CUDA: CUDA runtime error";
+    case AMGD_ERR_OOM: return "AMGD_ERR_OOM: device allocation failed";
+    case AMGD_ERR_STATE: return "AMGD_ERR_STATE: call out of order";
+    case AMGD_ERR_CAPACITY: return "AMGD_ERR_CAPACITY: output buffer too small";
+    case AMGD_ERR_TIMEOUT: return "AMGD_ERR_TIMEOUT: bounded device wait gave up";
+    case AMGD_ERR_UNSUPPORTED: return "AMGD_ERR_UNSUPPORTED: size or mode not supported";
+    }
+    return "unknown status";
+}
+
+const char *amgd_last_error(amgd_handle h)
+{
+    return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// amgd_internal.cuh -- types shared by the kernels and the host API of the
+// GB300 algebraic-distance library (not part of the public ABI).
+//
+// Device data layout (all in HBM, owned by the handle):
+//   * permuted CSR of A: rows reordered by color when a coloring is set
+//     (identity otherwise), slot order inside a row unchanged; int32 row_ptr
+//     and col, values as FP64 and (for the mixed paths) FP32.
+//   * original CSR row_ptr / col: the numbering of every per-slot output.
+//   * test vectors X: two n x Kp row-major buffers (ping-pong) in the
+//     storage type; Kp = G * V pads K to a whole number of 16-byte vectors
+//     per lane (V elements per 16 bytes, G lanes per row), padding is zero.
+//   * per-slot outputs a, LS (FP64 or FP32), strength flag (u8); per-row
+//     strong counts (int32, caller's row order).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace amgd {
+
+enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16 = 2 };
+
+// ---------------------------------------------------------------------------
+// storage traits: TS = stored element, C = arithmetic type, V = elements per
+// 16-byte vector, A = stored matrix value type used by the sweeps.
+// ---------------------------------------------------------------------------
+template <class TS> struct Store;
+
+template <> struct Store<double> {
+    using C = double;
+    using A = double;
+    static constexpr int V = 2;
+    __device__ __forceinline__ static void load(const double *p, C (&x)[V]) {
+        double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+        x[0] = v.x;
+        x[1] = v.y;
+    }
+    __device__ __forceinline__ static void store(double *p, const C (&x)[V]) {
+        *reinterpret_cast<double2 *>(p) = make_double2(x[0], x[1]);
+    }
+};
+
+template <> struct Store<float> {
+    using C = float;
+    using A = float;
+    static constexpr int V = 4;
+    __device__ __forceinline__ static void load(const float *p, C (&x)[V]) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        x[0] = v.x;
+        x[1] = v.y;
+        x[2] = v.z;
+        x[3] = v.w;
+    }
+    __device__ __forceinline__ static void store(float *p, const C (&x)[V]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+};
+
+template <> struct Store<__nv_bfloat16> {
+    using C = float;
+    using A = float;
+    static constexpr int V = 8;
+    // bf16 -> fp32 is exact: the bf16 bits are the high half of the fp32 bits
+    __device__ __forceinline__ static void load(const __nv_bfloat16 *p, C (&x)[V]) {
+        uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            x[2 * k] = __uint_as_float(w[k] << 16);
+            x[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    }
+    __device__ __forceinline__ static void store(__nv_bfloat16 *p, const C (&x)[V]) {
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * k], x[2 * k + 1]);
+            w[k] = (uint32_t)__bfloat16_as_ushort(h.x) | ((uint32_t)__bfloat16_as_ushort(h.y) << 16);
+        }
+        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// launch arguments
+// ---------------------------------------------------------------------------
+struct RelaxArgs {
+    const int32_t *rp;    // permuted row_ptr
+    const int32_t *col;   // permuted col
+    const void *val;      // permuted values (double or float)
+    const void *xold;     // iterate at the start of the sweep
+    void *xnew;           // rows [r0, r1) written; rows < split read from here
+    int32_t r0, r1;       // rows of this color phase
+    int32_t split;        // rows < split take new values (earlier colors)
+    int32_t Kp;           // padded row stride (elements)
+    double omega;
+};
+
+struct EdgeArgs {
+    const int32_t *rp, *col;     // permuted CSR
+    const void *val;             // permuted values, arithmetic type
+    const double *val64;         // permuted values, FP64 (mixed-path fallback)
+    const void *x;               // final test vectors (permuted rows)
+    const void *w;               // LS weights, Kp long (zero padded), arithmetic type
+    const double *w64;           // LS weights in FP64
+    const int32_t *perm;         // permuted row -> caller row (NULL = identity)
+    const int32_t *rp_orig;      // caller row_ptr (slot numbering of outputs)
+    void *a_out, *ls_out;        // per slot (caller numbering), arithmetic type
+    uint8_t *flag_out;           // per slot
+    int32_t *count_out;          // per caller row
+    int32_t n, Kp, target;       // target: 0 residual, 1 plain
+    double theta;
+};
+
+struct InitArgs {
+    void *x;                   // n x Kp, permuted rows
+    const int32_t *perm;       // permuted row -> caller row (NULL = identity)
+    const int64_t *mat_off;    // nmat+1 caller-row offsets of the batch
+    int32_t nmat, n, K, Kp;
+    uint64_t seed;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files; return cudaGetLastError())
+// ---------------------------------------------------------------------------
+cudaError_t launch_relax(int storage, int G, const RelaxArgs &a, cudaStream_t s);
+cudaError_t launch_edge(int storage, int G, const EdgeArgs &a, cudaStream_t s);
+cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t s);
+
+// scatter caller-order n x K doubles into permuted, padded storage and back
+cudaError_t launch_import(int storage, const double *src, void *x, const int32_t *perm,
+                          int32_t n, int32_t K, int32_t Kp, cudaStream_t s);
+cudaError_t launch_export(int storage, const void *x, double *dst, const int32_t *perm,
+                          int32_t n, int32_t K, int32_t Kp, cudaStream_t s);
+// convert vectors between storage types (same permutation and padding)
+cudaError_t launch_convert(int from, const void *src, int to, void *dst, int64_t count,
+                           cudaStream_t s);
+// per-slot outputs (arithmetic type of `storage`) -> doubles; NULL dst skipped
+cudaError_t launch_export_slots(int storage, const void *a_in, const void *ls_in,
+                                double *a, double *dist, double *ls, int64_t nnz,
+                                cudaStream_t s);
+// permuted values: vp[q] = v[slot of q in caller order] (double and float copies)
+cudaError_t launch_permute_values(const double *v, const int32_t *rp_orig,
+                                  const int32_t *perm, const int32_t *rp_perm, double *vp64,
+                                  float *vp32, int32_t n, cudaStream_t s);
+
+// value check of a staged val[nnz]: err |= 1 for a non-finite value, |= 2 for
+// a zero diagonal (diag_slot[n] = slot of each row's diagonal)
+cudaError_t launch_check_values(const double *v, int64_t nnz, const int32_t *diag_slot,
+                                int32_t n, uint32_t *err, cudaStream_t s);
+
+// strength CSR: tile sums of counts, scan of the tile sums, compaction
+constexpr int kTileRows = 4096;
+cudaError_t launch_strength(const int32_t *count, const int32_t *rp_orig, const int32_t *col_orig,
+                            const uint8_t *flag, int32_t n, int32_t *tile_sum,
+                            int64_t *s_row_ptr, int32_t *s_col, cudaStream_t s);
+
+}  // namespace amgd

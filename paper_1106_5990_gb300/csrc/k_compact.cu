@@ -1,0 +1,141 @@
+// k_compact.cu -- the strength graph M^1 (§4.2) as CSR from the per-slot
+// flags and per-row counts written by the edge pass.
+//
+// Three launches, no device-wide waits:
+//   1. tile sums: every block sums the strong counts of kTileRows rows
+//   2. one block turns the tile sums into exclusive tile offsets
+//   3. every block writes s_row_ptr for its rows (block scan of the counts
+//      plus the tile offset) and compacts the flagged slots of its rows'
+//      contiguous slot range into s_col (block scan of the flags), keeping
+//      A's row and slot order.
+#include "amgd_internal.cuh"
+
+namespace amgd {
+namespace {
+
+constexpr int kSumThreads = 256;
+constexpr int kCompactThreads = 512;
+constexpr int kRowsPerThread = kTileRows / kCompactThreads;
+
+// exclusive block scan of one int per thread; returns the block total
+template <int NT>
+__device__ __forceinline__ int block_exclusive_scan(int v, int &total, int *smem_warp)
+{
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) smem_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < NT / 32 ? smem_warp[lane] : 0;
+        int winc = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, winc, o);
+            if (lane >= o) winc += t;
+        }
+        if (lane < NT / 32) smem_warp[lane] = winc - w;   // exclusive warp offsets
+        if (lane == NT / 32 - 1) smem_warp[32] = winc;     // block total
+    }
+    __syncthreads();
+    const int out = smem_warp[warp] + inc - v;
+    total = smem_warp[32];
+    __syncthreads();
+    return out;
+}
+
+__global__ void __launch_bounds__(kSumThreads)
+k_tile_sums(const int32_t *__restrict__ count, int32_t n, int32_t *__restrict__ tile_sum)
+{
+    __shared__ int sm[33];
+    const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
+    int s = 0;
+    for (int k = threadIdx.x; k < kTileRows; k += kSumThreads) {
+        const int64_t r = r0 + k;
+        if (r < n) s += count[r];
+    }
+    int total;
+    block_exclusive_scan<kSumThreads>(s, total, sm);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+// in-place exclusive scan of ntiles tile sums by one block
+__global__ void __launch_bounds__(1024) k_tile_scan(int32_t *__restrict__ tile_sum, int32_t ntiles)
+{
+    __shared__ int sm[33];
+    int carry = 0;
+    for (int base = 0; base < ntiles; base += 1024) {
+        const int k = base + threadIdx.x;
+        const int v = k < ntiles ? tile_sum[k] : 0;
+        int total;
+        const int ex = block_exclusive_scan<1024>(v, total, sm);
+        if (k < ntiles) tile_sum[k] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+k_compact(const int32_t *__restrict__ count, const int32_t *__restrict__ rp,
+          const int32_t *__restrict__ col, const uint8_t *__restrict__ flag, int32_t n,
+          const int32_t *__restrict__ tile_off, int64_t *__restrict__ s_row_ptr,
+          int32_t *__restrict__ s_col)
+{
+    __shared__ int sm[33];
+    const int64_t row0 = (int64_t)blockIdx.x * kTileRows;
+    const int64_t row_end = min((int64_t)n, row0 + kTileRows);
+    const int64_t off = tile_off[blockIdx.x];
+
+    // row pointers
+    int c[kRowsPerThread];
+    int mine = 0;
+    const int64_t rbase = row0 + (int64_t)threadIdx.x * kRowsPerThread;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        c[k] = (rbase + k < row_end) ? count[rbase + k] : 0;
+        mine += c[k];
+    }
+    int total;
+    int run = block_exclusive_scan<kCompactThreads>(mine, total, sm);
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        if (rbase + k < row_end) s_row_ptr[rbase + k] = off + run;
+        run += c[k];
+    }
+    if (row_end == n && threadIdx.x == 0) s_row_ptr[n] = off + total;
+
+    // flagged slots of the tile, in slot order
+    const int64_t s0 = rp[row0], s1 = rp[row_end];
+    int64_t out = off;
+    for (int64_t base = s0; base < s1; base += kCompactThreads) {
+        const int64_t slot = base + threadIdx.x;
+        const int f = (slot < s1) ? (int)flag[slot] : 0;
+        int chunk;
+        const int pos = block_exclusive_scan<kCompactThreads>(f, chunk, sm);
+        if (f) s_col[out + pos] = col[slot];
+        out += chunk;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_strength(const int32_t *count, const int32_t *rp_orig, const int32_t *col_orig,
+                            const uint8_t *flag, int32_t n, int32_t *tile_sum,
+                            int64_t *s_row_ptr, int32_t *s_col, cudaStream_t s)
+{
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(s_row_ptr, 0, sizeof(int64_t), s);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
+    const int ntiles = (int)(((int64_t)n + kTileRows - 1) / kTileRows);
+    k_tile_sums<<<ntiles, kSumThreads, 0, s>>>(count, n, tile_sum);
+    k_tile_scan<<<1, 1024, 0, s>>>(tile_sum, ntiles);
+    k_compact<<<ntiles, kCompactThreads, 0, s>>>(count, rp_orig, col_orig, flag, n, tile_sum,
+                                                s_row_ptr, s_col);
+    return cudaGetLastError();
+}
+
+}  // namespace amgd

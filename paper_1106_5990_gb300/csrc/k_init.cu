@@ -1,0 +1,264 @@
+// k_init.cu -- test-vector start (counter-based Philox4x64-10), layout and
+// precision conversions of the vector block, per-slot output export and the
+// permutation of A's values.
+#include "amgd_internal.cuh"
+
+namespace amgd {
+namespace {
+
+constexpr int kThreads = 256;
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 64x64->128 multiplies with the published 4x64 multipliers, Weyl key
+// schedule with the published increments.
+struct U64x4 { uint64_t v[4]; };
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                               uint64_t k0, uint64_t k1)
+{
+    constexpr uint64_t kMulA = 0xD2E7470EE14C6C93ull, kMulB = 0xCA5A826395121157ull;
+    constexpr uint64_t kWeylA = 0x9E3779B97F4A7C15ull, kWeylB = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t hiA = __umul64hi(kMulA, c0), loA = kMulA * c0;
+        const uint64_t hiB = __umul64hi(kMulB, c2), loB = kMulB * c2;
+        const uint64_t n0 = hiB ^ c1 ^ k0;
+        const uint64_t n2 = hiA ^ c3 ^ k1;
+        c0 = n0;
+        c1 = loB;
+        c2 = n2;
+        c3 = loA;
+        k0 += kWeylA;
+        k1 += kWeylB;
+    }
+    U64x4 o;
+    o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+    return o;
+}
+
+template <class TS> __device__ __forceinline__ TS from_double(double x);
+template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_double<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double x)
+{
+    return __double2bfloat16(x);
+}
+template <class TS> __device__ __forceinline__ double to_double(TS x) { return (double)x; }
+template <> __device__ __forceinline__ double to_double<__nv_bfloat16>(__nv_bfloat16 x)
+{
+    return (double)__bfloat162float(x);
+}
+
+// one thread per (row, group of 4 components)
+template <class TS>
+__global__ void k_tv_init(InitArgs A)
+{
+    const int nq = (A.Kp + 3) / 4;
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (t >= (int64_t)A.n * nq) return;
+    const int64_t r = t / nq;
+    const int q = (int)(t % nq);
+    const int64_t o = A.perm ? A.perm[r] : r;
+    int lo = 0, hi = A.nmat;                 // matrix b with mat_off[b] <= o < mat_off[b+1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (A.mat_off[mid] <= o) lo = mid; else hi = mid;
+    }
+    const uint64_t li = (uint64_t)(o - A.mat_off[lo]);
+    const U64x4 u = philox4x64_10(li, (uint64_t)q, 0ull, 0ull, A.seed, (uint64_t)lo);
+    TS *x = (TS *)A.x + r * A.Kp;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int kappa = 4 * q + k;
+        if (kappa >= A.Kp) break;
+        double v = 0.0;
+        if (kappa < A.K) v = 2.0 * ((double)(u.v[k] >> 11) * 0x1.0p-53) - 1.0;
+        x[kappa] = from_double<TS>(v);
+    }
+}
+
+template <class TS>
+__global__ void k_import(const double *__restrict__ src, TS *__restrict__ x,
+                         const int32_t *__restrict__ perm, int32_t n, int32_t K, int32_t Kp)
+{
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (t >= (int64_t)n * Kp) return;
+    const int64_t r = t / Kp;
+    const int kappa = (int)(t % Kp);
+    const int64_t o = perm ? perm[r] : r;
+    x[t] = from_double<TS>(kappa < K ? src[o * K + kappa] : 0.0);
+}
+
+template <class TS>
+__global__ void k_export(const TS *__restrict__ x, double *__restrict__ dst,
+                         const int32_t *__restrict__ perm, int32_t n, int32_t K, int32_t Kp)
+{
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (t >= (int64_t)n * K) return;
+    const int64_t r = t / K;
+    const int kappa = (int)(t % K);
+    const int64_t o = perm ? perm[r] : r;
+    dst[o * K + kappa] = to_double<TS>(x[r * Kp + kappa]);
+}
+
+template <class TF, class TT>
+__global__ void k_convert(const TF *__restrict__ src, TT *__restrict__ dst, int64_t count)
+{
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (t < count) dst[t] = from_double<TT>(to_double<TF>(src[t]));
+}
+
+template <class C>
+__global__ void k_export_slots(const C *__restrict__ a_in, const C *__restrict__ ls_in,
+                               double *__restrict__ a, double *__restrict__ dist,
+                               double *__restrict__ ls, int64_t nnz)
+{
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (t >= nnz) return;
+    const double l = (double)ls_in[t];
+    if (a) a[t] = (double)a_in[t];
+    if (ls) ls[t] = l;
+    if (dist) dist[t] = 1.0 / l;   // +inf for LS = 0, NaN stays NaN
+}
+
+__global__ void k_permute_values(const double *__restrict__ v, const int32_t *__restrict__ rp_orig,
+                                 const int32_t *__restrict__ perm, const int32_t *__restrict__ rp_perm,
+                                 double *__restrict__ vp64, float *__restrict__ vp32, int32_t n)
+{
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= n) return;
+    const int64_t o = perm ? perm[r] : r;
+    const int64_t s = rp_orig[o], d = rp_perm[r];
+    const int len = rp_orig[o + 1] - rp_orig[o];
+    for (int k = 0; k < len; ++k) {
+        const double x = v[s + k];
+        if (vp64) vp64[d + k] = x;
+        if (vp32) vp32[d + k] = (float)x;
+    }
+}
+
+__global__ void k_check_values(const double *__restrict__ v, int64_t nnz,
+                               const int32_t *__restrict__ diag_slot, int32_t n,
+                               uint32_t *__restrict__ err)
+{
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    uint32_t e = 0;
+    if (t < nnz && !isfinite(v[t])) e |= 1u;
+    if (t < n && v[diag_slot[t]] == 0.0) e |= 2u;
+    e = __reduce_or_sync(0xffffffffu, e);
+    if (e && (threadIdx.x % 32) == 0) atomicOr(err, e);
+}
+
+inline unsigned blocks(int64_t work) { return (unsigned)((work + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t s)
+{
+    const int64_t work = (int64_t)a.n * ((a.Kp + 3) / 4);
+    if (work == 0) return cudaSuccess;
+    switch (storage) {
+    case ST_FP64: k_tv_init<double><<<blocks(work), kThreads, 0, s>>>(a); break;
+    case ST_FP32: k_tv_init<float><<<blocks(work), kThreads, 0, s>>>(a); break;
+    case ST_BF16: k_tv_init<__nv_bfloat16><<<blocks(work), kThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import(int storage, const double *src, void *x, const int32_t *perm,
+                          int32_t n, int32_t K, int32_t Kp, cudaStream_t s)
+{
+    const int64_t work = (int64_t)n * Kp;
+    if (work == 0) return cudaSuccess;
+    switch (storage) {
+    case ST_FP64: k_import<<<blocks(work), kThreads, 0, s>>>(src, (double *)x, perm, n, K, Kp); break;
+    case ST_FP32: k_import<<<blocks(work), kThreads, 0, s>>>(src, (float *)x, perm, n, K, Kp); break;
+    case ST_BF16:
+        k_import<<<blocks(work), kThreads, 0, s>>>(src, (__nv_bfloat16 *)x, perm, n, K, Kp);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(int storage, const void *x, double *dst, const int32_t *perm,
+                          int32_t n, int32_t K, int32_t Kp, cudaStream_t s)
+{
+    const int64_t work = (int64_t)n * K;
+    if (work == 0) return cudaSuccess;
+    switch (storage) {
+    case ST_FP64:
+        k_export<<<blocks(work), kThreads, 0, s>>>((const double *)x, dst, perm, n, K, Kp);
+        break;
+    case ST_FP32:
+        k_export<<<blocks(work), kThreads, 0, s>>>((const float *)x, dst, perm, n, K, Kp);
+        break;
+    case ST_BF16:
+        k_export<<<blocks(work), kThreads, 0, s>>>((const __nv_bfloat16 *)x, dst, perm, n, K, Kp);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+namespace {
+template <class TF>
+cudaError_t convert_to(const TF *src, int to, void *dst, int64_t count, cudaStream_t s)
+{
+    switch (to) {
+    case ST_FP64: k_convert<<<blocks(count), kThreads, 0, s>>>(src, (double *)dst, count); break;
+    case ST_FP32: k_convert<<<blocks(count), kThreads, 0, s>>>(src, (float *)dst, count); break;
+    case ST_BF16:
+        k_convert<<<blocks(count), kThreads, 0, s>>>(src, (__nv_bfloat16 *)dst, count);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_convert(int from, const void *src, int to, void *dst, int64_t count,
+                           cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    switch (from) {
+    case ST_FP64: return convert_to((const double *)src, to, dst, count, s);
+    case ST_FP32: return convert_to((const float *)src, to, dst, count, s);
+    case ST_BF16: return convert_to((const __nv_bfloat16 *)src, to, dst, count, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_export_slots(int storage, const void *a_in, const void *ls_in, double *a,
+                                double *dist, double *ls, int64_t nnz, cudaStream_t s)
+{
+    if (nnz == 0) return cudaSuccess;
+    if (storage == ST_FP64)
+        k_export_slots<<<blocks(nnz), kThreads, 0, s>>>((const double *)a_in,
+                                                        (const double *)ls_in, a, dist, ls, nnz);
+    else
+        k_export_slots<<<blocks(nnz), kThreads, 0, s>>>((const float *)a_in, (const float *)ls_in,
+                                                        a, dist, ls, nnz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_values(const double *v, int64_t nnz, const int32_t *diag_slot,
+                                int32_t n, uint32_t *err, cudaStream_t s)
+{
+    const int64_t work = nnz > n ? nnz : n;
+    if (work == 0) return cudaSuccess;
+    k_check_values<<<blocks(work), kThreads, 0, s>>>(v, nnz, diag_slot, n, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_values(const double *v, const int32_t *rp_orig, const int32_t *perm,
+                                  const int32_t *rp_perm, double *vp64, float *vp32, int32_t n,
+                                  cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_permute_values<<<blocks(n), kThreads, 0, s>>>(v, rp_orig, perm, rp_perm, vp64, vp32, n);
+    return cudaGetLastError();
+}
+
+}  // namespace amgd

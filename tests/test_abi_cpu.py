@@ -1,0 +1,92 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+symbol include/amgd.h declares, and rejects bad arguments on the host before
+touching the device."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from paper_1106_5990_gb300 import _build, amgd, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    _build.build()
+    return amgd.lib()
+
+
+def test_exports_every_header_symbol(L):
+    names = amgd.header_symbols(os.path.join(ROOT, "include", "amgd.h"))
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(amgd.SIGNATURES)
+
+
+def test_status_strings(L):
+    for code in range(0, -10, -1):
+        s = amgd.amgd_status_string(code)
+        assert s.startswith("AMGD_")
+    assert amgd.amgd_status_string(-99) == "unknown status"
+
+
+def _create(rp, col, val, K=4):
+    h = ctypes.c_void_p()
+    rp = np.ascontiguousarray(rp, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    st = amgd.lib().amgd_create(rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                len(rp) - 1, K, 0, amgd.AMGD_MEM_HOST, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("case,code", [
+    ("rp0", amgd.AMGD_ERR_CSR), ("decreasing", amgd.AMGD_ERR_CSR),
+    ("col_range", amgd.AMGD_ERR_CSR), ("duplicate", amgd.AMGD_ERR_CSR),
+    ("nonfinite", amgd.AMGD_ERR_CSR), ("zero_diag", amgd.AMGD_ERR_ZERO_DIAG),
+    ("no_diag", amgd.AMGD_ERR_ZERO_DIAG), ("K0", amgd.AMGD_ERR_UNSUPPORTED),
+    ("K65", amgd.AMGD_ERR_UNSUPPORTED)])
+def test_create_rejects_bad_input_on_host(L, case, code):
+    rp, col, val = inputs.lap1d(6)
+    rp, col, val = rp.copy(), col.copy(), val.copy()
+    K = 4
+    if case == "rp0":
+        rp = rp + 1
+    elif case == "decreasing":
+        rp[3] = rp[2] - 1
+    elif case == "col_range":
+        col[2] = 6
+    elif case == "duplicate":
+        col[1] = col[0]
+    elif case == "nonfinite":
+        val[4] = np.nan
+    elif case == "zero_diag":
+        val[0] = 0.0
+    elif case == "no_diag":
+        col[0] = 2      # row 0 becomes (2, 1): no diagonal, no duplicate
+        col[0], col[1] = 1, 2
+    elif case == "K0":
+        K = 0
+    elif case == "K65":
+        K = 65
+    st, h = _create(rp, col, val, K)
+    assert st == code, (case, st, amgd.amgd_last_error(None))
+    assert not h.value
+    assert amgd.amgd_last_error(None)
+
+
+def test_null_arguments(L):
+    assert L.amgd_create(None, None, None, 0, 4, 0, 0, None) == amgd.AMGD_ERR_ARG
+    assert L.amgd_destroy(None) == amgd.AMGD_OK
+    assert L.amgd_relax(None, 1, 1.0, 0) == amgd.AMGD_ERR_ARG
+    assert L.amgd_strength(None, None, None, 0, None, 0) == amgd.AMGD_ERR_ARG
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(amgd, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(amgd, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        amgd.lib()

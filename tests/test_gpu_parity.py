@@ -1,0 +1,307 @@
+"""GPU (C-ABI) against the FP64 oracle on the same seeded inputs.
+
+Sizes are small enough for the oracle to finish in seconds but span several
+blocks/tiles of every kernel and ragged tails; edge cases cover n = 0, a
+single row, rows without off-diagonals, degree-one rows, long rows, K = 1 and
+K = 64.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from parity import (check_a, check_flags, check_ls, edge_rows, flags_from_strength,
+                    flags_from_strength_fast, ls_scales)
+from paper_1106_5990_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+amgd = pytest.importorskip("paper_1106_5990_gb300.amgd")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1106_5990_gb300 import _build
+    _build.build()
+    torch.cuda.init()
+
+
+MATRICES = {
+    "poisson5_37": lambda: inputs.poisson2d_5pt(37),
+    "aniso9_40": lambda: inputs.aniso2d_9pt(40, 1e-3, math.pi / 6),
+    "aniso7_33": lambda: inputs.aniso2d_7pt(33, 0.1, -math.pi / 4),
+    "lap1d_1000": lambda: inputs.lap1d(1000),
+    "random_1500": lambda: inputs.random_csr(1500, 6.0, 11),
+    "random_sym_900": lambda: inputs.random_csr(900, 5.0, 12, symmetric_pattern=True),
+    "jump3d_12": lambda: inputs.jump3d_7pt(12, 2.0, 2),
+    "graph_2000": lambda: inputs.graph_laplacian(2000, 8.0, 4),
+}
+
+
+def gpu_build(rp, col, val, K, seed, nu, omega, theta, sweep=0, color=None, w=None,
+              target=0, precision="fp64", X0=None):
+    with amgd.Handle(rp, col, val, K, seed) as h:
+        if precision != "fp64":
+            h.set_precision(precision)
+        if color is not None:
+            h.set_coloring(color)
+        if w is not None:
+            h.set_weights(w)
+        if target:
+            h.set_target(target)
+        if X0 is not None:
+            h.set_vectors(X0)
+        h.relax(nu, omega, sweep)
+        X = h.get_vectors()
+        out = h.distances(theta)
+        s_rp, s_col = h.strength()
+    return dict(X=X, a=out["a"], ls=out["ls"], dist=out["dist"], s_rp=s_rp, s_col=s_col)
+
+
+def compare_fp64(rp, col, val, got, want, theta, w=None):
+    rows, cols = edge_rows(rp, col)
+    off = rows != cols
+    assert np.array_equal(got["X"], want["X"]), "test vectors differ"
+    syy, sxx = ls_scales(rp, col, want["X"], want["Y"], w)
+    check_ls(got["ls"], want["ls"], syy, off)
+    check_a(got["a"], want["a"], syy, sxx, off)
+    assert np.all(np.isnan(got["ls"][~off])) and np.all(got["a"][~off] == 0)
+    with np.errstate(divide="ignore"):
+        np.testing.assert_array_equal(got["dist"][off], 1.0 / got["ls"][off])
+    flag = flags_from_strength(rp, col, got["s_rp"], got["s_col"]) if len(rp) < 5000 else \
+        flags_from_strength_fast(rp, col, got["s_rp"], got["s_col"])
+    check_flags(flag, want, rp, col, theta, 1e-9)
+
+
+# --------------------------------------------------------------------------- X0
+@pytest.mark.parametrize("K", [1, 2, 3, 5, 8, 16, 17, 32, 33, 64])
+def test_x0_fp64_bit_exact(K):
+    rp, col, val = inputs.random_csr(777, 4.0, K)
+    with amgd.Handle(rp, col, val, K, seed=1234 + K) as h:
+        X = h.get_vectors()
+        h.init_vectors(99)
+        X2 = h.get_vectors()
+    assert np.array_equal(X, oracle.tv_init(777, K, 1234 + K))
+    assert np.array_equal(X2, oracle.tv_init(777, K, 99))
+
+
+def test_x0_rounded_storages():
+    rp, col, val = inputs.poisson2d_5pt(30)
+    want = oracle.tv_init(900, 16, 5)
+    with amgd.Handle(rp, col, val, 16, 5) as h:
+        h.set_precision("fp32")
+        assert np.array_equal(h.get_vectors(), want.astype(np.float32).astype(np.float64))
+        h.init_vectors(5)
+        assert np.array_equal(h.get_vectors(), want.astype(np.float32).astype(np.float64))
+        h.set_precision("bf16")
+        h.init_vectors(5)
+        got = h.get_vectors()
+    ulp = 2.0 ** (np.floor(np.log2(np.abs(want))) - 7)
+    assert np.all(np.abs(got - want) <= 0.5 * ulp)
+
+
+# --------------------------------------------------------------------------- sweeps
+@pytest.mark.parametrize("name", list(MATRICES))
+@pytest.mark.parametrize("K", [1, 3, 8, 16, 32])
+def test_jacobi_sweeps_bit_exact(name, K):
+    rp, col, val = MATRICES[name]()
+    n = len(rp) - 1
+    X0 = oracle.tv_init(n, K, 7)
+    want = oracle.relax(rp, col, val, X0, 3, 0.7)
+    with amgd.Handle(rp, col, val, K, 7) as h:
+        h.relax(3, 0.7, amgd.AMGD_SWEEP_JACOBI)
+        assert np.array_equal(h.get_vectors(), want)
+
+
+@pytest.mark.parametrize("name,coloring", [
+    ("aniso9_40", "redblack"), ("poisson5_37", "redblack"), ("random_1500", "greedy"),
+    ("random_sym_900", "random3"), ("graph_2000", "greedy"), ("aniso7_33", "redblack")])
+@pytest.mark.parametrize("K", [2, 16, 64])
+def test_mcgs_sweeps_bit_exact(name, coloring, K):
+    rp, col, val = MATRICES[name]()
+    n = len(rp) - 1
+    if coloring == "redblack":
+        color = inputs.red_black(int(round(math.sqrt(n))))
+    elif coloring == "greedy":
+        color = inputs.greedy_coloring(rp, col)
+    else:
+        color = np.random.default_rng(3).integers(0, 3, n).astype(np.int32)
+    X0 = oracle.tv_init(n, K, 3)
+    for omega in (1.0, 1.2):
+        want = oracle.relax(rp, col, val, X0, 2, omega, oracle.SWEEP_MCGS, color)
+        with amgd.Handle(rp, col, val, K, 3) as h:
+            h.set_coloring(color)
+            h.relax(2, omega, amgd.AMGD_SWEEP_MCGS)
+            assert np.array_equal(h.get_vectors(), want)
+
+
+# --------------------------------------------------------------------------- full build
+@pytest.mark.parametrize("name", list(MATRICES))
+@pytest.mark.parametrize("K,target", [(8, 0), (16, 0), (16, 1), (5, 0), (33, 0)])
+def test_build_fp64_parity(name, K, target):
+    rp, col, val = MATRICES[name]()
+    theta, nu, omega = 0.5, 4, 2.0 / 3.0
+    want = oracle.build(rp, col, val, K, 0, nu, omega, theta, mode=target)
+    got = gpu_build(rp, col, val, K, 0, nu, omega, theta, target=target)
+    compare_fp64(rp, col, val, got, want, theta)
+
+
+def test_build_fp64_mcgs_weights():
+    N = 48
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
+    color = inputs.red_black(N)
+    w = np.random.default_rng(0).uniform(0.5, 2.0, 16)
+    for theta in (0.25, 0.5, 0.8):
+        want = oracle.build(rp, col, val, 16, 1, 8, 1.0, theta, oracle.SWEEP_MCGS, color, w=w)
+        got = gpu_build(rp, col, val, 16, 1, 8, 1.0, theta, 1, color, w=w)
+        compare_fp64(rp, col, val, got, want, theta, w)
+
+
+# --------------------------------------------------------------------------- edge cases
+def _one_row_matrices():
+    yield "single_row", (np.array([0, 1]), np.array([0], np.int32), np.array([2.0]))
+    # rows without off-diagonals interleaved with coupled rows
+    rp, col, val = inputs.graph_laplacian(300, 0.4, 9)
+    yield "sparse_graph_isolated", (rp, col, val)
+    # one long row (dense first row and column)
+    n = 700
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        rows.append(i); cols.append(i); vals.append(float(n))
+        if i > 0:
+            rows += [0, i]; cols += [i, 0]; vals += [-1.0, -0.5]
+        if 0 < i < n - 1:
+            rows.append(i); cols.append(i + 1); vals.append(-0.25)
+    import scipy.sparse as sp
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A.sort_indices()
+    yield "long_row", (A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data)
+
+
+@pytest.mark.parametrize("K", [1, 2, 64])
+def test_edge_case_matrices(K):
+    for name, (rp, col, val) in _one_row_matrices():
+        for target in (0, 1):
+            want = oracle.build(rp, col, val, K, 2, 3, 0.6, 0.5, mode=target)
+            got = gpu_build(rp, col, val, K, 2, 3, 0.6, 0.5, target=target)
+            if K == 1:
+                # k = 1 < caliber: every fit is exact up to rounding (LS ~ 0),
+                # distances are rounding noise; compare vectors and LS scale only
+                assert np.array_equal(got["X"], want["X"]), name
+                rows, cols = edge_rows(rp, col)
+                off = rows != cols
+                syy, _ = ls_scales(rp, col, want["X"], want["Y"])
+                assert np.all(got["ls"][off] <= 1e-28 * syy[off] + 1e-300), name
+                continue
+            compare_fp64(rp, col, val, got, want, 0.5)
+
+
+def test_empty_matrix():
+    rp = np.zeros(1, np.int64)
+    col = np.zeros(0, np.int32)
+    val = np.zeros(0)
+    with amgd.Handle(rp, col, val, 4, 0) as h:
+        assert h.n == 0 and h.E == 0
+        h.relax(2, 0.7)
+        h.distances(0.5)
+        s_rp, s_col = h.strength()
+    assert list(s_rp) == [0] and len(s_col) == 0
+
+
+def test_ragged_tile_boundaries():
+    """n around the compaction tile (4096 rows) and warp/block multiples."""
+    for n in (4095, 4096, 4097, 8193):
+        rp, col, val = inputs.lap1d(n)
+        want = oracle.build(rp, col, val, 4, 1, 2, 0.6, 0.5, mode=1)
+        got = gpu_build(rp, col, val, 4, 1, 2, 0.6, 0.5, target=1)
+        compare_fp64(rp, col, val, got, want, 0.5)
+
+
+# --------------------------------------------------------------------------- batch, graph
+def test_batch_equals_separate_and_oracle():
+    mats = [inputs.graph_laplacian(n, 4.0, 5, b) for b, n in enumerate([300, 1111, 57, 2500])]
+    K, nu, omega, theta, seed = 16, 4, 2.0 / 3.0, 0.5, 6
+    with amgd.Handle(None, None, None, K, seed, batch=mats) as h:
+        h.relax(nu, omega)
+        out = h.distances(theta)
+        s_rp, s_col = h.strength()
+        X = h.get_vectors()
+        ro, so = h.offsets()
+    for b, (rp, col, val) in enumerate(mats):
+        want = oracle.build(rp, col, val, K, seed, nu, omega, theta, stream=b)
+        sl = slice(so[b], so[b + 1])
+        rs = slice(ro[b], ro[b + 1])
+        got = dict(X=X[rs], a=out["a"][sl], ls=out["ls"][sl], dist=out["dist"][sl],
+                   s_rp=s_rp[ro[b]:ro[b + 1] + 1] - s_rp[ro[b]],
+                   s_col=s_col[s_rp[ro[b]]:s_rp[ro[b + 1]]] - ro[b])
+        compare_fp64(rp, col, val, got, want, theta)
+        # identical to a single-matrix handle keyed by (seed, b): same bits
+        with amgd.Handle(rp, col, val, K, seed) as h1:
+            h1.set_vectors(oracle.tv_init(len(rp) - 1, K, seed, b))
+            h1.relax(nu, omega)
+            o1 = h1.distances(theta)
+        assert np.array_equal(o1["ls"], got["ls"], equal_nan=True)
+        assert np.array_equal(o1["a"], got["a"])
+
+
+def test_graph_capture_equals_stepwise():
+    import torch
+    N = 64
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
+    color = inputs.red_black(N)
+    for prec in ("fp64", "bf16"):
+        with amgd.Handle(rp, col, val, 16, 1) as h:
+            h.set_precision(prec)
+            h.set_coloring(color)
+            d_rp = torch.empty(N * N + 1, dtype=torch.int64, device="cuda")
+            d_col = torch.empty(h.E, dtype=torch.int32, device="cuda")
+            h.graph_capture(1, 8, 1.0, amgd.AMGD_SWEEP_MCGS, 0.5, d_rp, d_col)
+            for _ in range(3):
+                h.graph_launch()
+            torch.cuda.synchronize()
+            g_ls = h.distances(0.5)["ls"]   # recomputed from the graph's final vectors
+            g_rp, g_col = d_rp.cpu().numpy(), d_col.cpu().numpy()
+            h.init_vectors(1)
+            h.relax(8, 1.0, amgd.AMGD_SWEEP_MCGS)
+            s_ls = h.distances(0.5)["ls"]
+            s_rp, s_col = h.strength()
+        assert np.array_equal(g_ls, s_ls, equal_nan=True)
+        assert np.array_equal(g_rp, s_rp)
+        assert np.array_equal(g_col[:g_rp[-1]], s_col)
+
+
+# --------------------------------------------------------------------------- API states
+def test_state_errors_and_roundtrips():
+    rp, col, val = inputs.poisson2d_5pt(20)
+    with amgd.Handle(rp, col, val, 8, 0) as h:
+        with pytest.raises(amgd.AmgdError) as e:
+            h.relax(1, 1.0, amgd.AMGD_SWEEP_MCGS)
+        assert e.value.status == amgd.AMGD_ERR_STATE
+        with pytest.raises(amgd.AmgdError) as e:
+            h.strength()
+        assert e.value.status == amgd.AMGD_ERR_STATE
+        X = np.random.default_rng(0).uniform(-1, 1, (400, 8))
+        h.set_vectors(X)
+        assert np.array_equal(h.get_vectors(), X)
+        h.set_coloring(inputs.red_black(20))
+        assert np.array_equal(h.get_vectors(), X)
+        h.set_values(val * 3.0)
+        h.relax(2, 1.0, amgd.AMGD_SWEEP_MCGS)
+        want = oracle.relax(rp, col, val * 3.0, X, 2, 1.0, oracle.SWEEP_MCGS, inputs.red_black(20))
+        assert np.array_equal(h.get_vectors(), want)
+        h.distances(0.5)
+        s_rp = np.empty(401, np.int64)
+        s_col = np.empty(3, np.int32)
+        import ctypes
+        nnz_s = ctypes.c_int64()
+        st = amgd.lib().amgd_strength(h.h, s_rp.ctypes.data, s_col.ctypes.data, 3,
+                                      ctypes.byref(nnz_s), amgd.AMGD_MEM_HOST)
+        assert st == amgd.AMGD_ERR_CAPACITY and nnz_s.value > 3
+        with pytest.raises(amgd.AmgdError):
+            h.set_weights(np.array([1.0, -1.0] + [1.0] * 6))
+        with pytest.raises(amgd.AmgdError):
+            h.set_values(np.where(np.arange(len(val)) == 0, 0.0, val))
