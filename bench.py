@@ -1,0 +1,503 @@
+"""Throughput of the algebraic-distance strength build on GB300.
+
+One step = one whole build on one synthetic matrix already resident in HBM:
+Philox start of the K test vectors, nu relaxation sweeps, the fused
+distance/threshold pass, and the strength CSR -- replayed as one CUDA graph.
+The metric is edges/s = E (stored off-diagonals) / step time.
+
+Default workload (rotated anisotropic diffusion, 9-point stencil on a
+1024 x 1024 grid, eps = 1e-3, alpha = pi/6; K = 16 vectors, nu = 8
+red-black Gauss-Seidel sweeps, theta = 0.5): the mixed path (BF16 vector
+storage, FP32 arithmetic) is the headline, the FP64 path is measured beside
+it on the same matrix.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c2]
+                  [--precision bf16|fp32|fp64] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank builds its own copy of the workload on its
+own GPU (independent problems, no data exchange): weak scaling, rank 0
+prints the aggregate.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1106_5990_gb300 import inputs  # noqa: E402
+
+METRIC = "edges/s of algebraic-distance strength build, mixed vs FP64 on GPU; %HBM roof"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+WORKLOADS = {
+    "c1": dict(name="2D Poisson 5-point, 64x64 grid (n=4096), K=8, nu=4 Jacobi omega=2/3",
+               K=8, seed=0, nu=4, omega=2.0 / 3.0, sweep="jacobi", theta=0.5,
+               precision="fp64"),
+    "c2": dict(name="rotated anisotropic diffusion 9-point, 1024x1024 grid, eps=1e-3, "
+                    "alpha=pi/6; K=16, nu=8 red-black Gauss-Seidel, theta=0.5",
+               K=16, seed=1, nu=8, omega=1.0, sweep="mcgs", theta=0.5, precision="bf16"),
+    "c3": dict(name="3D jump-coefficient diffusion 7-point, 128^3 cells, lognormal(0,2) "
+                    "coefficients, harmonic faces; K=32, nu=6 Jacobi omega=0.8",
+               K=32, seed=3, nu=6, omega=0.8, sweep="jacobi", theta=0.5, precision="fp32"),
+    "c4": dict(name="batch of 64 graph Laplacians, n ~ U[10k,500k], Poisson(8) neighbours "
+                    "symmetrised, lognormal(0,1) weights; K=16, nu=4 Jacobi omega=2/3",
+               K=16, seed=6, nu=4, omega=2.0 / 3.0, sweep="jacobi", theta=0.5,
+               precision="bf16"),
+    "c5": dict(name="anisotropic diffusion 5-point (eps=1e-2), 512x512 grid; K=16, nu=10 "
+                    "Jacobi omega=2/3 (forward)",
+               K=16, seed=7, nu=10, omega=2.0 / 3.0, sweep="jacobi", theta=0.5,
+               precision="fp32"),
+}
+
+
+def make_matrix(cfg: str, scale: int | None = None):
+    """(list of CSR matrices, coloring or None).  ``scale`` shrinks the grid
+    (used for the bounded CPU samples)."""
+    if cfg == "c1":
+        return [inputs.poisson2d_5pt(64)], None
+    if cfg == "c2":
+        N = scale or 1024
+        return [inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)], inputs.red_black(N)
+    if cfg == "c3":
+        N = scale or 128
+        return [inputs.jump3d_7pt(N, 2.0, 2)], None
+    if cfg == "c4":
+        if scale:
+            sizes = inputs.batch_sizes(64, 10_000, 500_000, 5)[:scale]
+            return [inputs.graph_laplacian(int(s), 8.0, 4, b) for b, s in enumerate(sizes)], None
+        return inputs.graph_laplacian_batch(64, 10_000, 500_000, 8.0, 4, 5), None
+    if cfg == "c5":
+        N = scale or 512
+        return [inputs.aniso2d_5pt(N, 1e-2)], None
+    raise ValueError(cfg)
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes (what the method must move; each vector row read once
+# per pass, every stored entry of A read once per pass)
+# --------------------------------------------------------------------------
+SIZES = {"fp64": 8, "fp32": 4, "bf16": 2}
+
+
+def algorithmic_bytes(n, nnz, E, E_s, K, nu, ncolors, precision, permuted):
+    s_x = SIZES[precision]
+    s_a = 8 if precision == "fp64" else 4
+    s_c = 8 if precision == "fp64" else 4
+    csr = nnz * (4 + s_a) + 4 * (n + 1)
+    reads_per_sweep = ncolors                 # every color phase reads the vectors once
+    sweep = csr + (reads_per_sweep + 1) * n * K * s_x
+    init = n * K * s_x
+    edge = csr + n * K * s_x + nnz * (2 * s_c + 1) + 4 * n + (8 * n if permuted else 0)
+    strength = 4 * n * 2 + nnz + 4 * E_s * 2 + 8 * (n + 1)
+    return dict(init=init, sweep=sweep, relax=nu * sweep, relax_per_launch=sweep / ncolors,
+                edge=edge, strength=strength, total=init + nu * sweep + edge + strength)
+
+
+def source_sha(*names):
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_1106_5990_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key, sha):
+    """dram bytes per launch from a committed ncu capture, if the kernel
+    source is unchanged since."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = t.get(key)
+    if not e or e.get("source_sha") != sha:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+        self.path = os.path.join("/tmp", "amgd_clocks_%d_%d.csv" % (os.getpid(), device_index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None,
+                    sm_max_mhz=float(max(smax)) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_clocks=True):
+    import torch
+    from paper_1106_5990_gb300 import amgd
+
+    stream = torch.cuda.current_stream()
+    if len(mats) == 1:
+        h = amgd.Handle(*mats[0], w["K"], w["seed"])
+    else:
+        h = amgd.Handle(None, None, None, w["K"], w["seed"], batch=mats)
+    h.set_stream(stream)
+    h.set_precision(precision)
+    ncolors = 1
+    sweep = amgd.AMGD_SWEEP_JACOBI
+    if w["sweep"] == "mcgs":
+        h.set_coloring(color)
+        ncolors = int(color.max()) + 1
+        sweep = amgd.AMGD_SWEEP_MCGS
+    d_rp = torch.empty(h.n + 1, dtype=torch.int64, device="cuda")
+    d_col = torch.empty(max(h.E, 1), dtype=torch.int32, device="cuda")
+    h.enable_phase_timing(True)
+    h.graph_capture(w["seed"], w["nu"], w["omega"], sweep, w["theta"], d_rp, d_col)
+    for _ in range(warmup):
+        h.graph_launch()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device()) if want_clocks else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    phase = np.zeros(4)
+    if clocks:
+        clocks.start()
+        time.sleep(0.15)
+    _barrier()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.fill_(k & 0xFF)                     # evict L2 between steps (not timed)
+        ev[k][0].record(stream)
+        h.graph_launch()
+        ev[k][1].record(stream)
+        phase += np.array(h.phase_times())        # waits for this step's last event
+    torch.cuda.synchronize()
+    _barrier()
+    clk = clocks.stop() if clocks else None
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    E_s = int(d_rp[-1].item())
+    return dict(h=h, step_ms=step_ms, phase_ms=phase / steps, E_s=E_s, ncolors=ncolors,
+                sweep=sweep, clocks=clk, d_rp=d_rp, d_col=d_col)
+
+
+def run_e2e(h, mats, w, sweep, steps):
+    """Through the public API with host buffers: per step the matrix values
+    are copied from pinned host memory (amgd_set_values) and the strength CSR
+    is read back to pinned host memory (amgd_strength, host mode)."""
+    import ctypes
+    import torch
+    from paper_1106_5990_gb300 import amgd
+
+    vals = np.concatenate([m[2] for m in mats])
+    val_h = torch.from_numpy(vals).pin_memory()
+    s_rp = torch.empty(h.n + 1, dtype=torch.int64).pin_memory()
+    s_col = torch.empty(max(h.E, 1), dtype=torch.int32).pin_memory()
+    L = amgd.lib()
+    nnz_s = ctypes.c_int64()
+    times = []
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        h.set_values(val_h)
+        h.init_vectors(w["seed"])
+        h.relax(w["nu"], w["omega"], sweep)
+        amgd.check(L.amgd_distances(h.h, w["theta"], None, None, None, amgd.AMGD_MEM_DEVICE), h.h)
+        amgd.check(L.amgd_strength(h.h, s_rp.data_ptr(), s_col.data_ptr(), s_col.numel(),
+                                   ctypes.byref(nnz_s), amgd.AMGD_MEM_HOST), h.h)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    return dict(seconds=t, h2d=int(vals.nbytes),
+                d2h=int((h.n + 1) * 8 + nnz_s.value * 4 + 8), E_s=int(nnz_s.value))
+
+
+def cpu_oracle_time(cfg, w, budget_s=20.0):
+    """The FP64 oracle (single thread) on a bounded sample of the workload."""
+    import oracle
+    if cfg in ("c1", "c5"):
+        mats, color = make_matrix(cfg)
+        sample = "full workload"
+    elif cfg == "c2":
+        mats, color = make_matrix(cfg)
+        sample = "full workload (1024x1024)"
+    elif cfg == "c3":
+        mats, color = make_matrix(cfg, scale=64)
+        sample = "64^3 sub-problem of the same operator"
+    else:
+        mats, color = make_matrix(cfg, scale=2)
+        sample = "first 2 matrices of the batch"
+    edges = 0
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        for rp, col, val in mats:
+            oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
+                         sweep=oracle.SWEEP_MCGS if w["sweep"] == "mcgs" else oracle.SWEEP_JACOBI,
+                         color=color)
+            edges += len(col) - (len(rp) - 1)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 3 or reps >= 3:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=edges / dt, unit="edges/s", cores=1, kind="oracle",
+                sample="%s, %d repetition(s), %.1f s" % (sample, reps, dt))
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (one process per GPU)
+# --------------------------------------------------------------------------
+_PG = None
+
+
+def _barrier():
+    if _PG is not None:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float) -> float:
+    if _PG is None:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def init_dist():
+    global _PG
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        _PG = dist.group.WORLD
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args, cfg, w):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build_lib()
+    if cfg == "c2":
+        mats, color = make_matrix(cfg, scale=256)
+        sample = "256x256 sub-grid of the same operator per step"
+    elif cfg == "c3":
+        mats, color = make_matrix(cfg, scale=32)
+        sample = "32^3 sub-problem of the same operator per step"
+    elif cfg == "c4":
+        mats, color = make_matrix(cfg, scale=1)
+        sample = "first matrix of the batch per step"
+    else:
+        mats, color = make_matrix(cfg)
+        sample = "full workload per step"
+    sw = oracle.SWEEP_MCGS if w["sweep"] == "mcgs" else oracle.SWEEP_JACOBI
+
+    def step():
+        e = 0
+        for rp, col, val in mats:
+            oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
+                         sweep=sw, color=color)
+            e += len(col) - (len(rp) - 1)
+        return e
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    edges = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = edges / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "config": cfg},
+            "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-side", action="store_true", help="skip the FP64 side measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    cfg = args.config
+    w = dict(WORKLOADS[cfg])
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps are required")
+    if args.impl == "reference":
+        return run_reference(args, cfg, w)
+
+    import torch
+    ws, rank, local = init_dist()
+    torch.cuda.set_device(local)
+    from paper_1106_5990_gb300 import amgd
+    amgd.lib()
+    precision = args.precision or w["precision"]
+    mats, color = make_matrix(cfg)
+    n = sum(len(m[0]) - 1 for m in mats)
+    nnz = sum(len(m[1]) for m in mats)
+    E = nnz - n
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    r = run_gpu_arm(mats, color, w, precision, args.steps, args.warmup, rank, flush)
+    t_local = float(r["step_ms"].sum())
+    t_max = _max_over_ranks(t_local)
+    ms_per_step = t_max / args.steps
+    value = ws * E / (ms_per_step * 1e-3)
+
+    permuted = w["sweep"] == "mcgs"
+    ab = algorithmic_bytes(n, nnz, E, r["E_s"], w["K"], w["nu"], r["ncolors"], precision, permuted)
+    launches_relax = w["nu"] * r["ncolors"]
+    relax_launch_ms = r["phase_ms"][1] / launches_relax
+    peak, peak_kind = peaks()
+    achieved = ab["relax_per_launch"] / (relax_launch_ms * 1e-3) / 1e9
+    G = {"fp64": 8, "fp32": 4, "bf16": 2}[precision] if w["K"] == 16 else None
+    tkey = "relax/%s/K%d/%s" % (precision, w["K"], cfg)
+    traffic = recorded_traffic(tkey, source_sha("k_relax.cu", "amgd_internal.cuh"))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_relax (one color phase of one sweep)",
+                "peak_source": "%s hbm_gbs" % peak_kind,
+                "algorithmic_bytes_per_launch": ab["relax_per_launch"],
+                "avg_launch_us": relax_launch_ms * 1e3}
+    phases = dict(zip(["init", "relax", "distances", "strength"], r["phase_ms"].tolist()))
+    whole = ab["total"] / (ms_per_step * 1e-3) / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "config": cfg, "n": n, "nnz": nnz, "E": E,
+                       "K": w["K"], "nu": w["nu"], "sweep": w["sweep"], "theta": w["theta"],
+                       "storage": precision, "l2": "flushed between steps (256 MiB write)",
+                       "graph": "one CUDA graph per step", "lanes_per_row": G},
+            "phase_ms": phases,
+            "whole_step_gbs": whole, "whole_step_hbm_frac": whole / peak,
+            "roofline": roofline}
+
+    launches_per_step = 1 + launches_relax + 1 + 3
+    line["gpu_launches"] = launches_per_step * args.steps
+
+    if not args.no_side and precision != "fp64":
+        side_steps = max(3, min(args.steps, 100))
+        r64 = run_gpu_arm(mats, color, w, "fp64", side_steps, 3, rank, flush, want_clocks=False)
+        t64 = _max_over_ranks(float(r64["step_ms"].sum())) / side_steps
+        ab64 = algorithmic_bytes(n, nnz, E, r64["E_s"], w["K"], w["nu"], r64["ncolors"], "fp64",
+                                 permuted)
+        rl = r64["phase_ms"][1] / launches_relax
+        a64 = ab64["relax_per_launch"] / (rl * 1e-3) / 1e9
+        line["fp64"] = {"value": ws * E / (t64 * 1e-3), "unit": "edges/s", "ms_per_step": t64,
+                        "steps": side_steps,
+                        "phase_ms": dict(zip(["init", "relax", "distances", "strength"],
+                                             r64["phase_ms"].tolist())),
+                        "relax_launch_us": rl * 1e3, "relax_hbm_gbs": a64,
+                        "relax_hbm_frac": a64 / peak,
+                        "mixed_over_fp64": value / (ws * E / (t64 * 1e-3))}
+        r64["h"].close()
+
+    e2e_steps = max(3, min(args.steps, 50))
+    e = run_e2e(r["h"], mats, w, r["sweep"], e2e_steps)
+    t_e2e = _max_over_ranks(e["seconds"])
+    line["e2e"] = {"value": ws * E / t_e2e, "unit": "edges/s", "h2d_bytes_per_step": e["h2d"],
+                   "d2h_bytes_per_step": e["d2h"], "steps": e2e_steps,
+                   "api": "amgd_set_values(host) + init + relax + distances + strength(host)"}
+    line["clocks"] = {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} \
+        if r["clocks"] else None
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_time(cfg, w)
+    r["h"].close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if _PG is not None:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
