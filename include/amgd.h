@@ -229,14 +229,49 @@ int amgd_graph_launch(amgd_handle h);
 int amgd_enable_phase_timing(amgd_handle h, int enable);
 int amgd_phase_times(amgd_handle h, float *ms);
 
+/*
+ * amgd_strength_noalloc -- the threshold of Eq. (4.4) and the strength CSR,
+ *   computed from distances the caller already holds, without allocating
+ *   any memory.  The paper has no counterpart to this entry point: it exists
+ *   for callers that cannot call cudaMalloc (code running inside a memory
+ *   pool or arena that owns every device allocation of the process, or a
+ *   loop that must never take the driver's allocation lock), since every
+ *   handle-based entry point allocates device memory for its handle.
+ *
+ *   All pointers are DEVICE memory of the current device:
+ *     row_ptr[n+1] (int64) and col[nnz] (int32): the CSR pattern of A;
+ *     ls[nnz]: LS_ij per slot (as written by amgd_distances; diagonal slots
+ *       are recognised by col == row and ignored);
+ *     s_row_ptr[n+1], s_col[cap]: the output CSR, rows in order, kept
+ *       columns in slot order.  If s_row_ptr[n] > cap after the call, only
+ *       the first cap columns were written.
+ *   theta >= 0.  stream: a cudaStream_t (NULL = legacy default stream); the
+ *   call only enqueues work.
+ *
+ *   Working memory: a file-scope device array of 65536 int32 (256 KiB, one
+ *   entry per tile of 4096 rows) that every GPU loading the library keeps
+ *   until the process exits.  Hence n <= 268,435,456; larger n is rejected
+ *   with AMGD_ERR_UNSUPPORTED before any GPU work.  The first call on a
+ *   device looks up the array's device address with that device current
+ *   (make this first call before any stream capture).  Every call reuses the
+ *   same array; calls whose GPU work overlaps (other streams, other threads
+ *   on the same device) race on it and must be serialised by the caller.
+ *   Nothing is allocated or freed: no cudaMalloc, no cudaFree.
+ *   Errors: ARG, UNSUPPORTED, CUDA (text in amgd_last_error(NULL)).
+ */
+int amgd_strength_noalloc(const int64_t *row_ptr, const int32_t *col, const double *ls,
+                          int64_t n, double theta, int64_t *s_row_ptr, int32_t *s_col,
+                          int64_t cap, void *stream);
+
 /* Free everything the handle owns (synchronises its stream); NULL is a no-op. */
 int amgd_destroy(amgd_handle h);
 
 /* Static text of a status code. */
 const char *amgd_status_string(int status);
 
-/* Message of the last error of h, or of the last failed create on this
- * thread when h is NULL.  Valid until the next call on h. */
+/* Message of the last error of h, or, when h is NULL, of the last failed
+ * amgd_create / amgd_create_batch / amgd_strength_noalloc on this thread.
+ * Valid until the next call on h. */
 const char *amgd_last_error(amgd_handle h);
 
 #ifdef __cplusplus

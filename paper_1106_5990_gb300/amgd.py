@@ -69,6 +69,7 @@ SIGNATURES = {
     "amgd_graph_launch": (_int, [_P]),
     "amgd_enable_phase_timing": (_int, [_P, _int]),
     "amgd_phase_times": (_int, [_P, _P]),
+    "amgd_strength_noalloc": (_int, [_P, _P, _P, _i64, _f64, _P, _P, _i64, _P]),
     "amgd_destroy": (_int, [_P]),
     "amgd_status_string": (ctypes.c_char_p, [_int]),
     "amgd_last_error": (ctypes.c_char_p, [_P]),

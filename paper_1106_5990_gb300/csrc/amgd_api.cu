@@ -386,6 +386,8 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
 
 }  // namespace
 
+void amgd::set_thread_error(const std::string &msg) { g_create_err = msg; }
+
 extern "C" {
 
 int amgd_create(const int64_t *row_ptr, const int32_t *col, const double *val, int64_t n,

@@ -17,6 +17,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace amgd {
 
 enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16 = 2 };
@@ -155,5 +157,8 @@ constexpr int kTileRows = 4096;
 cudaError_t launch_strength(const int32_t *count, const int32_t *rp_orig, const int32_t *col_orig,
                             const uint8_t *flag, int32_t n, int32_t *tile_sum,
                             int64_t *s_row_ptr, int32_t *s_col, cudaStream_t s);
+
+// message returned by amgd_last_error(NULL) on the calling host thread
+void set_thread_error(const std::string &msg);
 
 }  // namespace amgd
