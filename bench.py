@@ -212,6 +212,8 @@ def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_cloc
         h.set_coloring(color)
         ncolors = int(color.max()) + 1
         sweep = amgd.AMGD_SWEEP_MCGS
+    shapes = h.autotune(sweep, w["omega"])           # picks (G, NV, U) per kernel; untimed
+    h.init_vectors(w["seed"])
     d_rp = torch.empty(h.n + 1, dtype=torch.int64, device="cuda")
     d_col = torch.empty(max(h.E, 1), dtype=torch.int32, device="cuda")
     h.enable_phase_timing(True)
@@ -241,7 +243,7 @@ def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_cloc
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
     E_s = int(d_rp[-1].item())
     return dict(h=h, step_ms=step_ms, phase_ms=phase / steps, E_s=E_s, ncolors=ncolors,
-                sweep=sweep, clocks=clk, d_rp=d_rp, d_col=d_col)
+                sweep=sweep, clocks=clk, d_rp=d_rp, d_col=d_col, shapes=shapes)
 
 
 def run_e2e(h, mats, w, sweep, steps):
@@ -436,7 +438,6 @@ def main():
     relax_launch_ms = r["phase_ms"][1] / launches_relax
     peak, peak_kind = peaks()
     achieved = ab["relax_per_launch"] / (relax_launch_ms * 1e-3) / 1e9
-    G = {"fp64": 8, "fp32": 4, "bf16": 2}[precision] if w["K"] == 16 else None
     tkey = "relax/%s/K%d/%s" % (precision, w["K"], cfg)
     traffic = recorded_traffic(tkey, source_sha("k_relax.cu", "amgd_internal.cuh"))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -455,7 +456,10 @@ def main():
             "config": {"workload": w["name"], "config": cfg, "n": n, "nnz": nnz, "E": E,
                        "K": w["K"], "nu": w["nu"], "sweep": w["sweep"], "theta": w["theta"],
                        "storage": precision, "l2": "flushed between steps (256 MiB write)",
-                       "graph": "one CUDA graph per step", "lanes_per_row": G},
+                       "graph": "one CUDA graph per step",
+                       "shapes": {"relax": list(r["shapes"][0]), "edge": list(r["shapes"][1]),
+                                  "legend": "(lanes per row G, 16-byte vectors per lane NV, "
+                                            "nonzeros per gather batch U), autotuned"}},
             "phase_ms": phases,
             "whole_step_gbs": whole, "whole_step_hbm_frac": whole / peak,
             "roofline": roofline}
@@ -472,7 +476,8 @@ def main():
         rl = r64["phase_ms"][1] / launches_relax
         a64 = ab64["relax_per_launch"] / (rl * 1e-3) / 1e9
         line["fp64"] = {"value": ws * E / (t64 * 1e-3), "unit": "edges/s", "ms_per_step": t64,
-                        "steps": side_steps,
+                        "steps": side_steps, "shapes": {"relax": list(r64["shapes"][0]),
+                                                        "edge": list(r64["shapes"][1])},
                         "phase_ms": dict(zip(["init", "relax", "distances", "strength"],
                                              r64["phase_ms"].tolist())),
                         "relax_launch_us": rl * 1e3, "relax_hbm_gbs": a64,

@@ -218,6 +218,29 @@ int amgd_graph_capture(amgd_handle h, uint64_t seed, int32_t nu, double omega, i
 int amgd_graph_launch(amgd_handle h);
 
 /*
+ * Kernel shapes and the autotuner.  A row of test vectors is P = Kp/V
+ *   sixteen-byte vectors (V = 2, 4, 8 elements for FP64, FP32, BF16); a
+ *   shape spreads them over G lanes with NV vectors per lane (G*NV = P,
+ *   NV in {1,2,4}) and gathers U nonzeros per batch (U in {4,8}).  Shapes
+ *   change speed only, never results.  kernel: AMGD_KERNEL_RELAX (the
+ *   sweeps) or AMGD_KERNEL_EDGE (the distance pass); the shape applies to
+ *   the current storage precision.
+ * amgd_autotune times every valid shape of both kernels on the handle's own
+ *   matrix and vectors (one sweep of sweep_type/omega into the spare vector
+ *   buffer -- the current vectors are kept -- and one distance pass;
+ *   computed distances are invalidated) and keeps the fastest.  cache_path
+ *   (may be NULL): a text file of earlier results keyed by GPU name,
+ *   storage, K, size buckets, sweep type and color count; a matching line
+ *   is used without timing, a new result is appended.
+ *   Errors: ARG, STATE (MCGS without coloring), CUDA.
+ */
+#define AMGD_KERNEL_RELAX 0
+#define AMGD_KERNEL_EDGE  1
+int amgd_set_kernel_shape(amgd_handle h, int kernel, int G, int NV, int U);
+int amgd_get_kernel_shape(amgd_handle h, int kernel, int *G, int *NV, int *U);
+int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache_path);
+
+/*
  * Phase timing of captured builds.  amgd_enable_phase_timing(h, 1) before
  *   amgd_graph_capture makes the captured graph record CUDA events (owned by
  *   the handle) on the stream it runs on at the boundaries

@@ -41,6 +41,8 @@ AMGD_TARGET_PLAIN = 1
 AMGD_FP64 = 0
 AMGD_FP32 = 1
 AMGD_BF16 = 2
+AMGD_KERNEL_RELAX = 0
+AMGD_KERNEL_EDGE = 1
 
 PRECISIONS = {"fp64": AMGD_FP64, "fp32": AMGD_FP32, "bf16": AMGD_BF16}
 
@@ -67,6 +69,9 @@ SIGNATURES = {
     "amgd_strength": (_int, [_P, _P, _P, _i64, _P, _int]),
     "amgd_graph_capture": (_int, [_P, _u64, _i32, _f64, _int, _f64, _P, _P, _i64]),
     "amgd_graph_launch": (_int, [_P]),
+    "amgd_set_kernel_shape": (_int, [_P, _int, _int, _int, _int]),
+    "amgd_get_kernel_shape": (_int, [_P, _int, _P, _P, _P]),
+    "amgd_autotune": (_int, [_P, _int, _f64, ctypes.c_char_p]),
     "amgd_enable_phase_timing": (_int, [_P, _int]),
     "amgd_phase_times": (_int, [_P, _P]),
     "amgd_strength_noalloc": (_int, [_P, _P, _P, _i64, _f64, _P, _P, _i64, _P]),
@@ -296,6 +301,20 @@ class Handle:
 
     def graph_launch(self):
         self._ck(lib().amgd_graph_launch(self.h))
+
+    def set_kernel_shape(self, kernel, G, NV, U):
+        self._ck(lib().amgd_set_kernel_shape(self.h, kernel, G, NV, U))
+
+    def kernel_shape(self, kernel):
+        g, nv, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._ck(lib().amgd_get_kernel_shape(self.h, kernel, ctypes.byref(g), ctypes.byref(nv),
+                                             ctypes.byref(u)))
+        return g.value, nv.value, u.value
+
+    def autotune(self, sweep=AMGD_SWEEP_JACOBI, omega=1.0, cache_path=None):
+        c = cache_path.encode() if cache_path else None
+        self._ck(lib().amgd_autotune(self.h, sweep, omega, c))
+        return self.kernel_shape(AMGD_KERNEL_RELAX), self.kernel_shape(AMGD_KERNEL_EDGE)
 
     def enable_phase_timing(self, enable=True):
         self._ck(lib().amgd_enable_phase_timing(self.h, int(enable)))

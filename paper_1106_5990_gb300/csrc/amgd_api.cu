@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -55,6 +56,7 @@ struct amgd_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int graph_cur_after = 0;
+    Shape relax_shape[3], edge_shape[3];         // per storage type
     bool phase_timing = false, graph_timed = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     std::string err;
@@ -67,15 +69,34 @@ thread_local std::string g_create_err;
 int V_of(int st) { return st == ST_FP64 ? 2 : (st == ST_FP32 ? 4 : 8); }
 size_t esize(int st) { return st == ST_FP64 ? 8 : (st == ST_FP32 ? 4 : 2); }
 
-int G_of(int st, int K)
+// 16-byte vectors per row: ceil(K / V) rounded up to a power of two
+int P_of(int st, int K)
 {
     const int V = V_of(st);
     const int need = (K + V - 1) / V;
-    int G = 1;
-    while (G < need) G <<= 1;
-    return G;
+    int P = 1;
+    while (P < need) P <<= 1;
+    return P;
 }
-int Kp_of(int st, int K) { return G_of(st, K) * V_of(st); }
+int Kp_of(int st, int K) { return P_of(st, K) * V_of(st); }
+
+// a shape is valid when it tiles the row exactly and stays within the
+// compiled instantiations (NV in {1,2,4}, U in {4,8}, G*NV*V <= 64)
+bool shape_ok(int st, int K, Shape sh)
+{
+    const int P = P_of(st, K);
+    if (sh.NV != 1 && sh.NV != 2 && sh.NV != 4) return false;
+    if (sh.U != 4 && sh.U != 8) return false;
+    if (sh.G < 1 || sh.G > 32 || (sh.G & (sh.G - 1))) return false;
+    return sh.G * sh.NV == P;
+}
+
+// untuned default: one vector per lane, four nonzeros per batch (the
+// lightest shape in registers)
+Shape default_shape(int st, int K)
+{
+    return Shape{P_of(st, K), 1, 4};
+}
 
 int fail(amgd_ctx *h, int code, const std::string &msg)
 {
@@ -212,7 +233,7 @@ int run_init(amgd_ctx *h, uint64_t seed, cudaStream_t s)
 
 int run_relax(amgd_ctx *h, int32_t nu, double omega, int sweep, cudaStream_t s)
 {
-    const int G = G_of(h->storage, h->K);
+    const Shape sh = h->relax_shape[h->storage];
     RelaxArgs a;
     a.rp = h->rp_p;
     a.col = h->col_p;
@@ -226,13 +247,13 @@ int run_relax(amgd_ctx *h, int32_t nu, double omega, int sweep, cudaStream_t s)
             a.r0 = 0;
             a.r1 = (int32_t)h->n;
             a.split = 0;
-            CK(h, launch_relax(h->storage, G, a, s));
+            CK(h, launch_relax(h->storage, sh, a, s));
         } else {
             for (size_t c = 0; c + 1 < h->color_start.size(); ++c) {
                 a.r0 = (int32_t)h->color_start[c];
                 a.r1 = (int32_t)h->color_start[c + 1];
                 a.split = a.r0;
-                CK(h, launch_relax(h->storage, G, a, s));
+                CK(h, launch_relax(h->storage, sh, a, s));
             }
         }
         h->cur = 1 - h->cur;
@@ -261,7 +282,9 @@ int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
     a.Kp = Kp_of(h->storage, h->K);
     a.target = h->target;
     a.theta = theta;
-    CK(h, launch_edge(h->storage, G_of(h->storage, h->K), a, s));
+    bool unit_w = true;
+    for (double wk : h->h_w) unit_w = unit_w && wk == 1.0;
+    CK(h, launch_edge(h->storage, h->edge_shape[h->storage], unit_w, a, s));
     h->have_dist = true;
     return AMGD_OK;
 }
@@ -341,6 +364,7 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
     h->h_col = std::move(h_col);
     h->h_diag_slot = std::move(diag_slot);
     h->h_w.assign((size_t)K, 1.0);
+    for (int st = 0; st < 3; ++st) h->relax_shape[st] = h->edge_shape[st] = default_shape(st, K);
     cudaGetDevice(&h->device);
 
     auto bail = [&](int rc) {
@@ -371,7 +395,7 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
     h->col_p = h->col_o;
     h->val64 = h->val_o;
     h->color_start = {0, n};
-    TRY(dalloc(&h->flag, (size_t)h->nnz));
+    TRY(dalloc(&h->flag, (size_t)h->nnz + 16));   // 16-byte loads past the end
     TRY(dalloc(&h->count, (size_t)n));
     TRY(dalloc(&h->tile, (size_t)(n / kTileRows + 2)));
     if ((rc = alloc_slot_outputs(h, ST_FP64)) != AMGD_OK) return bail(rc);
@@ -741,6 +765,153 @@ int amgd_graph_capture(amgd_handle h, uint64_t seed, int32_t nu, double omega, i
     h->graph = g;
     CK(h, cudaGraphInstantiate(&h->gexec, h->graph, 0));
     h->graph_timed = timed;
+    return AMGD_OK;
+}
+
+int amgd_set_kernel_shape(amgd_handle h, int kernel, int G, int NV, int U)
+{
+    if (!h) return AMGD_ERR_ARG;
+    const Shape sh{G, NV, U};
+    if ((kernel != AMGD_KERNEL_RELAX && kernel != AMGD_KERNEL_EDGE) || !shape_ok(h->storage, h->K, sh))
+        return fail(h, AMGD_ERR_ARG, "invalid kernel shape for this storage and K");
+    (kernel == AMGD_KERNEL_RELAX ? h->relax_shape : h->edge_shape)[h->storage] = sh;
+    return AMGD_OK;
+}
+
+int amgd_get_kernel_shape(amgd_handle h, int kernel, int *G, int *NV, int *U)
+{
+    if (!h || (kernel != AMGD_KERNEL_RELAX && kernel != AMGD_KERNEL_EDGE)) return AMGD_ERR_ARG;
+    const Shape sh = (kernel == AMGD_KERNEL_RELAX ? h->relax_shape : h->edge_shape)[h->storage];
+    if (G) *G = sh.G;
+    if (NV) *NV = sh.NV;
+    if (U) *U = sh.U;
+    return AMGD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+std::string tune_key(amgd_ctx *h, int sweep_type)
+{
+    cudaDeviceProp prop;
+    std::string gpu = "unknown";
+    if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) gpu = prop.name;
+    for (char &c : gpu)
+        if (c == ';' || c == '=' || c == '\n') c = '_';
+    int nb = 0;
+    while (((int64_t)1 << (nb + 1)) <= h->n) ++nb;
+    const long db = h->n ? (long)((h->nnz + h->n / 2) / h->n) : 0;
+    return "gpu=" + gpu + ";st=" + std::to_string(h->storage) + ";K=" + std::to_string(h->K) +
+           ";nb=" + std::to_string(nb) + ";db=" + std::to_string(db) +
+           ";sweep=" + std::to_string(sweep_type) + ";colors=" +
+           std::to_string(h->color_start.size() - 1);
+}
+
+bool parse_shape(const std::string &line, const char *tag, Shape &sh)
+{
+    const std::string t = std::string(";") + tag + "=";
+    const size_t p = line.find(t);
+    if (p == std::string::npos) return false;
+    return sscanf(line.c_str() + p + t.size(), "%d,%d,%d", &sh.G, &sh.NV, &sh.U) == 3;
+}
+
+// median of `reps` timings (ms) of fn() on the handle's stream
+template <class F>
+int time_ms(amgd_ctx *h, F fn, int reps, float &out)
+{
+    cudaEvent_t a, b;
+    CK(h, cudaEventCreate(&a));
+    CK(h, cudaEventCreate(&b));
+    std::vector<float> t;
+    int rc = fn();                       // warm-up
+    for (int k = 0; k < reps && rc == AMGD_OK; ++k) {
+        cudaEventRecord(a, h->stream);
+        rc = fn();
+        cudaEventRecord(b, h->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        t.push_back(ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != AMGD_OK) return rc;
+    std::sort(t.begin(), t.end());
+    out = t[t.size() / 2];
+    return AMGD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache_path)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (sweep_type != AMGD_SWEEP_JACOBI && sweep_type != AMGD_SWEEP_MCGS)
+        return fail(h, AMGD_ERR_ARG, "unknown sweep type");
+    if (sweep_type == AMGD_SWEEP_MCGS && !h->perm)
+        return fail(h, AMGD_ERR_STATE, "MCGS needs amgd_set_coloring first");
+    if (!std::isfinite(omega)) return fail(h, AMGD_ERR_ARG, "omega not finite");
+    const std::string key = tune_key(h, sweep_type);
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char buf[1024];
+            Shape r{0, 0, 0}, e{0, 0, 0};
+            bool found = false;
+            while (fgets(buf, sizeof buf, f)) {
+                std::string line(buf);
+                if (line.compare(0, key.size(), key) == 0 && line.size() > key.size() &&
+                    line[key.size()] == ';' && parse_shape(line, "relax", r) &&
+                    parse_shape(line, "edge", e) && shape_ok(h->storage, h->K, r) &&
+                    shape_ok(h->storage, h->K, e))
+                    found = true;       // the last matching line wins
+            }
+            fclose(f);
+            if (found) {
+                h->relax_shape[h->storage] = r;
+                h->edge_shape[h->storage] = e;
+                return AMGD_OK;
+            }
+        }
+    }
+    std::vector<Shape> cands;
+    const int P = P_of(h->storage, h->K);
+    for (int NV : {1, 2, 4})
+        for (int U : {4, 8})
+            if (P % NV == 0 && shape_ok(h->storage, h->K, Shape{P / NV, NV, U}))
+                cands.push_back(Shape{P / NV, NV, U});
+    const Shape keep_r = h->relax_shape[h->storage], keep_e = h->edge_shape[h->storage];
+    const int cur = h->cur;
+    Shape best_r = keep_r, best_e = keep_e;
+    float tr = 1e30f, te = 1e30f;
+    for (const Shape &c : cands) {
+        float ms = 0.f;
+        h->relax_shape[h->storage] = c;
+        // one sweep from the current vectors into the spare buffer (the
+        // current vectors are not touched), then restore the buffer index
+        int rc = time_ms(h, [&]() { int q = run_relax(h, 1, omega, sweep_type, h->stream); h->cur = cur; return q; }, 5, ms);
+        if (rc != AMGD_OK) { h->relax_shape[h->storage] = keep_r; return rc; }
+        if (ms < tr) { tr = ms; best_r = c; }
+        h->edge_shape[h->storage] = c;
+        rc = time_ms(h, [&]() { return run_edge(h, 0.5, h->stream); }, 5, ms);
+        if (rc != AMGD_OK) { h->edge_shape[h->storage] = keep_e; return rc; }
+        if (ms < te) { te = ms; best_e = c; }
+    }
+    h->relax_shape[h->storage] = best_r;
+    h->edge_shape[h->storage] = best_e;
+    h->cur = cur;
+    h->have_dist = false;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s;relax=%d,%d,%d;edge=%d,%d,%d;relax_ms=%.5f;edge_ms=%.5f\n", key.c_str(),
+                    best_r.G, best_r.NV, best_r.U, best_e.G, best_e.NV, best_e.U, tr, te);
+            fclose(f);
+        }
+    }
     return AMGD_OK;
 }
 

@@ -33,6 +33,10 @@ template <> struct Store<double> {
     using C = double;
     using A = double;
     static constexpr int V = 2;
+    __device__ __forceinline__ static void unpack(const uint4 &v, C (&x)[V]) {
+        x[0] = __hiloint2double((int)v.y, (int)v.x);
+        x[1] = __hiloint2double((int)v.w, (int)v.z);
+    }
     __device__ __forceinline__ static void load(const double *p, C (&x)[V]) {
         double2 v = __ldg(reinterpret_cast<const double2 *>(p));
         x[0] = v.x;
@@ -47,6 +51,12 @@ template <> struct Store<float> {
     using C = float;
     using A = float;
     static constexpr int V = 4;
+    __device__ __forceinline__ static void unpack(const uint4 &v, C (&x)[V]) {
+        x[0] = __uint_as_float(v.x);
+        x[1] = __uint_as_float(v.y);
+        x[2] = __uint_as_float(v.z);
+        x[3] = __uint_as_float(v.w);
+    }
     __device__ __forceinline__ static void load(const float *p, C (&x)[V]) {
         float4 v = __ldg(reinterpret_cast<const float4 *>(p));
         x[0] = v.x;
@@ -64,6 +74,14 @@ template <> struct Store<__nv_bfloat16> {
     using A = float;
     static constexpr int V = 8;
     // bf16 -> fp32 is exact: the bf16 bits are the high half of the fp32 bits
+    __device__ __forceinline__ static void unpack(const uint4 &v, C (&x)[V]) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            x[2 * k] = __uint_as_float(w[k] << 16);
+            x[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    }
     __device__ __forceinline__ static void load(const __nv_bfloat16 *p, C (&x)[V]) {
         uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -82,6 +100,19 @@ template <> struct Store<__nv_bfloat16> {
         }
         *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
     }
+};
+
+// 16-byte read-only load of a vector chunk
+__device__ __forceinline__ uint4 ldg16(const void *p)
+{
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// Kernel shape of one storage type: G lanes per row, NV 16-byte vectors per
+// lane (so a row holds P = G * NV vectors, Kp = P * V elements), U nonzeros
+// gathered per batch.  P is fixed by (storage, K); G, NV and U are free.
+struct Shape {
+    int G, NV, U;
 };
 
 // ---------------------------------------------------------------------------
@@ -126,8 +157,8 @@ struct InitArgs {
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files; return cudaGetLastError())
 // ---------------------------------------------------------------------------
-cudaError_t launch_relax(int storage, int G, const RelaxArgs &a, cudaStream_t s);
-cudaError_t launch_edge(int storage, int G, const EdgeArgs &a, cudaStream_t s);
+cudaError_t launch_relax(int storage, Shape sh, const RelaxArgs &a, cudaStream_t s);
+cudaError_t launch_edge(int storage, Shape sh, bool unit_w, const EdgeArgs &a, cudaStream_t s);
 cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t s);
 
 // scatter caller-order n x K doubles into permuted, padded storage and back
@@ -153,7 +184,7 @@ cudaError_t launch_check_values(const double *v, int64_t nnz, const int32_t *dia
                                 int32_t n, uint32_t *err, cudaStream_t s);
 
 // strength CSR: tile sums of counts, scan of the tile sums, compaction
-constexpr int kTileRows = 4096;
+constexpr int kTileRows = 1024;   // rows per compaction tile (multiple of 4)
 cudaError_t launch_strength(const int32_t *count, const int32_t *rp_orig, const int32_t *col_orig,
                             const uint8_t *flag, int32_t n, int32_t *tile_sum,
                             int64_t *s_row_ptr, int32_t *s_col, cudaStream_t s);

@@ -6,16 +6,18 @@
 //   2. one block turns the tile sums into exclusive tile offsets
 //   3. every block writes s_row_ptr for its rows (block scan of the counts
 //      plus the tile offset) and compacts the flagged slots of its rows'
-//      contiguous slot range into s_col (block scan of the flags), keeping
-//      A's row and slot order.
+//      contiguous slot range into s_col (16 flag bytes per thread, counted
+//      with popc, one block scan per 4096 slots), keeping A's row and slot
+//      order.
 #include "amgd_internal.cuh"
 
 namespace amgd {
 namespace {
 
 constexpr int kSumThreads = 256;
-constexpr int kCompactThreads = 512;
-constexpr int kRowsPerThread = kTileRows / kCompactThreads;
+constexpr int kCompactThreads = 256;
+constexpr int kRowsPerThread = kTileRows / kCompactThreads;     // 4
+constexpr int kSlotsPerThread = 16;                             // one 16-byte flag load
 
 // exclusive block scan of one int per thread; returns the block total
 template <int NT>
@@ -52,11 +54,13 @@ __global__ void __launch_bounds__(kSumThreads)
 k_tile_sums(const int32_t *__restrict__ count, int32_t n, int32_t *__restrict__ tile_sum)
 {
     __shared__ int sm[33];
-    const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
+    const int64_t r = (int64_t)blockIdx.x * kTileRows + threadIdx.x * 4;
     int s = 0;
-    for (int k = threadIdx.x; k < kTileRows; k += kSumThreads) {
-        const int64_t r = r0 + k;
-        if (r < n) s += count[r];
+    if (r + 3 < n) {
+        const int4 c = __ldg(reinterpret_cast<const int4 *>(count + r));
+        s = c.x + c.y + c.z + c.w;
+    } else {
+        for (int k = 0; k < 4; ++k) s += (r + k < n) ? count[r + k] : 0;
     }
     int total;
     block_exclusive_scan<kSumThreads>(s, total, sm);
@@ -89,7 +93,7 @@ k_compact(const int32_t *__restrict__ count, const int32_t *__restrict__ rp,
     const int64_t row_end = min((int64_t)n, row0 + kTileRows);
     const int64_t off = tile_off[blockIdx.x];
 
-    // row pointers
+    // row pointers: four consecutive rows per thread, block scan of the sums
     int c[kRowsPerThread];
     int mine = 0;
     const int64_t rbase = row0 + (int64_t)threadIdx.x * kRowsPerThread;
@@ -107,15 +111,30 @@ k_compact(const int32_t *__restrict__ count, const int32_t *__restrict__ rp,
     }
     if (row_end == n && threadIdx.x == 0) s_row_ptr[n] = off + total;
 
-    // flagged slots of the tile, in slot order
+    // kept slots of the tile's slot range [s0, s1), in slot order: every
+    // thread takes 16 consecutive flag bytes (one 16-byte load from a
+    // 16-byte-aligned base; the flag array is padded by 16 bytes)
     const int64_t s0 = rp[row0], s1 = rp[row_end];
     int64_t out = off;
-    for (int64_t base = s0; base < s1; base += kCompactThreads) {
-        const int64_t slot = base + threadIdx.x;
-        const int f = (slot < s1) ? (int)flag[slot] : 0;
+    for (int64_t base = s0 & ~(int64_t)15; base < s1;
+         base += (int64_t)kCompactThreads * kSlotsPerThread) {
+        const int64_t first = base + (int64_t)threadIdx.x * kSlotsPerThread;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (first < s1) v = __ldg(reinterpret_cast<const uint4 *>(flag + first));
+        uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        // clear the bytes outside [s0, s1)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int64_t slot = first + k;
+            if (slot < s0 || slot >= s1) w[k / 4] &= ~(0xffu << (8 * (k % 4)));
+        }
+        const int cnt = __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
         int chunk;
-        const int pos = block_exclusive_scan<kCompactThreads>(f, chunk, sm);
-        if (f) s_col[out + pos] = col[slot];
+        int pos = block_exclusive_scan<kCompactThreads>(cnt, chunk, sm);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if ((w[k / 4] >> (8 * (k % 4))) & 1u) s_col[out + pos++] = col[first + k];
+        }
         out += chunk;
     }
 }

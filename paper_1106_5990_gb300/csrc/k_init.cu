@@ -49,6 +49,47 @@ template <> __device__ __forceinline__ double to_double<__nv_bfloat16>(__nv_bflo
     return (double)__bfloat162float(x);
 }
 
+// The start value of a component is x = d * 2^-52 with the integer
+// d = (word >> 11) - 2^52, |d| <= 2^52 (2u - 1 with u = (word >> 11) 2^-53).
+// It is produced in the storage type with integer arithmetic only -- the
+// FP64 pipe of the GPU is narrow -- and rounded to nearest even exactly once.
+template <class TS> __device__ __forceinline__ TS start_value(int64_t d);
+
+template <> __device__ __forceinline__ double start_value<double>(int64_t d)
+{
+    if (d == 0) return 0.0;                       // |d| < 2^53: exact in FP64
+    const uint64_t sgn = d < 0 ? (1ull << 63) : 0ull;
+    const uint64_t a = d < 0 ? (uint64_t)(-d) : (uint64_t)d;
+    const int lead = 63 - __clzll((long long)a);  // 0..52
+    const uint64_t mant = (a << (52 - lead)) & ((1ull << 52) - 1ull);
+    const uint64_t expo = (uint64_t)(lead - 52 + 1023);
+    return __longlong_as_double((long long)(sgn | (expo << 52) | mant));
+}
+
+template <> __device__ __forceinline__ float start_value<float>(int64_t d)
+{
+    return __ll2float_rn(d) * 0x1.0p-52f;         // one rounding, exact scaling
+}
+
+template <> __device__ __forceinline__ __nv_bfloat16 start_value<__nv_bfloat16>(int64_t d)
+{
+    // round |d| to 8 significant bits (nearest, ties to even), then the value
+    // is exact in FP32 and in BF16
+    uint64_t a = d < 0 ? (uint64_t)(-d) : (uint64_t)d;
+    if (a != 0) {
+        const int lead = 63 - __clzll((long long)a);
+        if (lead > 7) {
+            const int sh = lead - 7;
+            uint64_t q = a >> sh;
+            const uint64_t rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+            if (rem > half || (rem == half && (q & 1ull))) ++q;
+            a = q << sh;
+        }
+    }
+    const float f = __ull2float_rn(a) * 0x1.0p-52f;
+    return __float2bfloat16_rn(d < 0 ? -f : f);
+}
+
 // one thread per (row, group of 4 components)
 template <class TS>
 __global__ void k_tv_init(InitArgs A)
@@ -71,9 +112,8 @@ __global__ void k_tv_init(InitArgs A)
     for (int k = 0; k < 4; ++k) {
         const int kappa = 4 * q + k;
         if (kappa >= A.Kp) break;
-        double v = 0.0;
-        if (kappa < A.K) v = 2.0 * ((double)(u.v[k] >> 11) * 0x1.0p-53) - 1.0;
-        x[kappa] = from_double<TS>(v);
+        const int64_t d = (int64_t)(u.v[k] >> 11) - (1ll << 52);
+        x[kappa] = kappa < A.K ? start_value<TS>(d) : start_value<TS>(0);
     }
 }
 

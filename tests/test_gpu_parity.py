@@ -305,3 +305,64 @@ def test_state_errors_and_roundtrips():
             h.set_weights(np.array([1.0, -1.0] + [1.0] * 6))
         with pytest.raises(amgd.AmgdError):
             h.set_values(np.where(np.arange(len(val)) == 0, 0.0, val))
+
+
+# --------------------------------------------------------------------------- shapes, tuner
+def _valid_shapes(prec, K):
+    V = {"fp64": 2, "fp32": 4, "bf16": 8}[prec]
+    P = 1
+    while P * V < K:
+        P *= 2
+    return [(P // nv, nv, u) for nv in (1, 2, 4) for u in (4, 8) if P % nv == 0]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("K", [5, 16, 32])
+def test_kernel_shapes_agree(prec, K):
+    """Shapes change speed, not results: sweeps are identical bit for bit
+    (every component's row sum keeps its order); distances agree to the
+    rounding of the K-term sums; strength sets agree outside a tiny band."""
+    N = 40
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
+    color = inputs.red_black(N)
+    ref = None
+    for G, NV, U in _valid_shapes(prec, K):
+        with amgd.Handle(rp, col, val, K, 4) as h:
+            h.set_precision(prec)
+            h.set_coloring(color)
+            h.set_kernel_shape(amgd.AMGD_KERNEL_RELAX, G, NV, U)
+            h.set_kernel_shape(amgd.AMGD_KERNEL_EDGE, G, NV, U)
+            assert h.kernel_shape(amgd.AMGD_KERNEL_EDGE) == (G, NV, U)
+            h.relax(3, 1.0, amgd.AMGD_SWEEP_MCGS)
+            X = h.get_vectors()
+            out = h.distances(0.5)
+        if ref is None:
+            ref = (X, out["ls"])
+            continue
+        assert np.array_equal(X, ref[0]), (G, NV, U)
+        tol = 1e-12 if prec == "fp64" else 2e-5
+        off = ~np.isnan(ref[1])
+        rel = np.abs(out["ls"][off] - ref[1][off]) / np.maximum(ref[1][off], 1e-300)
+        assert rel.max() <= tol, (G, NV, U, rel.max())
+    with amgd.Handle(rp, col, val, K, 4) as h:
+        h.set_precision(prec)
+        with pytest.raises(amgd.AmgdError):
+            h.set_kernel_shape(amgd.AMGD_KERNEL_RELAX, 3, 1, 4)
+
+
+def test_autotune_and_cache(tmp_path):
+    N = 64
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
+    cache = str(tmp_path / "tune.txt")
+    with amgd.Handle(rp, col, val, 16, 1) as h:
+        h.set_precision("bf16")
+        h.set_coloring(inputs.red_black(N))
+        X0 = h.get_vectors()
+        r1 = h.autotune(amgd.AMGD_SWEEP_MCGS, 1.0, cache)
+        assert np.array_equal(h.get_vectors(), X0)       # the vectors are kept
+        lines = open(cache).read().strip().splitlines()
+        assert len(lines) == 1 and "relax=" in lines[0] and "edge=" in lines[0]
+        r2 = h.autotune(amgd.AMGD_SWEEP_MCGS, 1.0, cache)   # served from the cache
+        assert r2 == r1 and len(open(cache).read().strip().splitlines()) == 1
+        h.relax(2, 1.0, amgd.AMGD_SWEEP_MCGS)
+        h.distances(0.5)
