@@ -195,7 +195,8 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
-def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_clocks=True):
+def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_clocks=True,
+                tune_cache=None):
     import torch
     from paper_1106_5990_gb300 import amgd
 
@@ -212,7 +213,7 @@ def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_cloc
         h.set_coloring(color)
         ncolors = int(color.max()) + 1
         sweep = amgd.AMGD_SWEEP_MCGS
-    shapes = h.autotune(sweep, w["omega"])           # picks (G, NV, U) per kernel; untimed
+    shapes = h.autotune(sweep, w["omega"], tune_cache)   # kernel shapes; untimed
     h.init_vectors(w["seed"])
     d_rp = torch.empty(h.n + 1, dtype=torch.int64, device="cuda")
     d_col = torch.empty(max(h.E, 1), dtype=torch.int32, device="cuda")
@@ -406,6 +407,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-side", action="store_true", help="skip the FP64 side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file (a matching entry skips the tuning launches)")
     args = ap.parse_args()
     cfg = args.config
     w = dict(WORKLOADS[cfg])
@@ -426,7 +429,8 @@ def main():
     E = nnz - n
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    r = run_gpu_arm(mats, color, w, precision, args.steps, args.warmup, rank, flush)
+    r = run_gpu_arm(mats, color, w, precision, args.steps, args.warmup, rank, flush,
+                    tune_cache=args.tune_cache)
     t_local = float(r["step_ms"].sum())
     t_max = _max_over_ranks(t_local)
     ms_per_step = t_max / args.steps
@@ -459,7 +463,8 @@ def main():
                        "graph": "one CUDA graph per step",
                        "shapes": {"relax": list(r["shapes"][0]), "edge": list(r["shapes"][1]),
                                   "legend": "(lanes per row G, 16-byte vectors per lane NV, "
-                                            "nonzeros per gather batch U), autotuned"}},
+                                            "nonzeros per gather batch U, TMA-staged CSR), "
+                                            "autotuned"}},
             "phase_ms": phases,
             "whole_step_gbs": whole, "whole_step_hbm_frac": whole / peak,
             "roofline": roofline}
@@ -469,7 +474,8 @@ def main():
 
     if not args.no_side and precision != "fp64":
         side_steps = max(3, min(args.steps, 100))
-        r64 = run_gpu_arm(mats, color, w, "fp64", side_steps, 3, rank, flush, want_clocks=False)
+        r64 = run_gpu_arm(mats, color, w, "fp64", side_steps, 3, rank, flush, want_clocks=False,
+                          tune_cache=args.tune_cache)
         t64 = _max_over_ranks(float(r64["step_ms"].sum())) / side_steps
         ab64 = algorithmic_bytes(n, nnz, E, r64["E_s"], w["K"], w["nu"], r64["ncolors"], "fp64",
                                  permuted)

@@ -56,7 +56,8 @@ typedef struct amgd_ctx *amgd_handle;
 #define AMGD_ERR_STATE       -6   /* call out of order (e.g. strength before
                                      distances, MCGS without a coloring)        */
 #define AMGD_ERR_CAPACITY    -7   /* output buffer too small                    */
-#define AMGD_ERR_TIMEOUT     -8   /* a bounded device wait gave up              */
+#define AMGD_ERR_TIMEOUT     -8   /* a bounded device wait gave up; reported by the
+                                     next call that synchronises the stream     */
 #define AMGD_ERR_UNSUPPORTED -9   /* size or mode outside the supported range   */
 
 /* where caller arrays live */
@@ -221,10 +222,16 @@ int amgd_graph_launch(amgd_handle h);
  * Kernel shapes and the autotuner.  A row of test vectors is P = Kp/V
  *   sixteen-byte vectors (V = 2, 4, 8 elements for FP64, FP32, BF16); a
  *   shape spreads them over G lanes with NV vectors per lane (G*NV = P,
- *   NV in {1,2,4}) and gathers U nonzeros per batch (U in {4,8}).  Shapes
- *   change speed only, never results.  kernel: AMGD_KERNEL_RELAX (the
- *   sweeps) or AMGD_KERNEL_EDGE (the distance pass); the shape applies to
- *   the current storage precision.
+ *   NV in {1,2,4}) and gathers U nonzeros per batch (U in {4,8}).  For the
+ *   relaxation, staged selects the kernel: 0 direct; 1 persistent, each
+ *   tile's CSR slice copied into shared memory with TMA bulk copies ahead of
+ *   use (waits bounded to about one second; a wait that runs out makes the
+ *   next synchronising call return AMGD_ERR_TIMEOUT); 2 warp-pipelined, CSR
+ *   slices and neighbour rows copied with cp.async two and one row groups
+ *   ahead (U must be 4).  Shapes change speed
+ *   only, never results.  kernel: AMGD_KERNEL_RELAX (the sweeps) or
+ *   AMGD_KERNEL_EDGE (the distance pass); the shape applies to the current
+ *   storage precision.
  * amgd_autotune times every valid shape of both kernels on the handle's own
  *   matrix and vectors (one sweep of sweep_type/omega into the spare vector
  *   buffer -- the current vectors are kept -- and one distance pass;
@@ -236,8 +243,8 @@ int amgd_graph_launch(amgd_handle h);
  */
 #define AMGD_KERNEL_RELAX 0
 #define AMGD_KERNEL_EDGE  1
-int amgd_set_kernel_shape(amgd_handle h, int kernel, int G, int NV, int U);
-int amgd_get_kernel_shape(amgd_handle h, int kernel, int *G, int *NV, int *U);
+int amgd_set_kernel_shape(amgd_handle h, int kernel, int G, int NV, int U, int staged);
+int amgd_get_kernel_shape(amgd_handle h, int kernel, int *G, int *NV, int *U, int *staged);
 int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache_path);
 
 /*

@@ -69,8 +69,8 @@ SIGNATURES = {
     "amgd_strength": (_int, [_P, _P, _P, _i64, _P, _int]),
     "amgd_graph_capture": (_int, [_P, _u64, _i32, _f64, _int, _f64, _P, _P, _i64]),
     "amgd_graph_launch": (_int, [_P]),
-    "amgd_set_kernel_shape": (_int, [_P, _int, _int, _int, _int]),
-    "amgd_get_kernel_shape": (_int, [_P, _int, _P, _P, _P]),
+    "amgd_set_kernel_shape": (_int, [_P, _int, _int, _int, _int, _int]),
+    "amgd_get_kernel_shape": (_int, [_P, _int, _P, _P, _P, _P]),
     "amgd_autotune": (_int, [_P, _int, _f64, ctypes.c_char_p]),
     "amgd_enable_phase_timing": (_int, [_P, _int]),
     "amgd_phase_times": (_int, [_P, _P]),
@@ -302,14 +302,15 @@ class Handle:
     def graph_launch(self):
         self._ck(lib().amgd_graph_launch(self.h))
 
-    def set_kernel_shape(self, kernel, G, NV, U):
-        self._ck(lib().amgd_set_kernel_shape(self.h, kernel, G, NV, U))
+    def set_kernel_shape(self, kernel, G, NV, U, staged=0):
+        self._ck(lib().amgd_set_kernel_shape(self.h, kernel, G, NV, U, staged))
 
     def kernel_shape(self, kernel):
-        g, nv, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        """(G, NV, U, staged) of a kernel for the current storage."""
+        g, nv, u, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._ck(lib().amgd_get_kernel_shape(self.h, kernel, ctypes.byref(g), ctypes.byref(nv),
-                                             ctypes.byref(u)))
-        return g.value, nv.value, u.value
+                                             ctypes.byref(u), ctypes.byref(st)))
+        return g.value, nv.value, u.value, st.value
 
     def autotune(self, sweep=AMGD_SWEEP_JACOBI, omega=1.0, cache_path=None):
         c = cache_path.encode() if cache_path else None

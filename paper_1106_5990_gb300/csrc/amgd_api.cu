@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -31,10 +32,19 @@ struct amgd_ctx {
     int64_t *mat_off = nullptr;
     int32_t *diag_slot = nullptr;                // slot of each row's diagonal
     uint32_t *err_word = nullptr;                // device error bits of value checks
+    uint32_t *status = nullptr;                  // device status bits of bounded waits
+    long long wait_limit = 2000000000LL;         // cycles (about 1 s) per staged wait
+    uint32_t test_extra_tx = 0;                  // test hook, see amgd_create
     // device: row-permuted matrix (aliases of the caller arrays without coloring)
     int32_t *rp_p = nullptr, *col_p = nullptr, *perm = nullptr;
     double *val64 = nullptr;
     float *val32 = nullptr;
+    double *diag64 = nullptr;                    // permuted diagonal
+    float *diag32 = nullptr;
+    float *val32_o = nullptr;                    // caller-order FP32 values (edge pass)
+    double *diag64_o = nullptr;                  // caller-order diagonal (edge pass)
+    float *diag32_o = nullptr;
+    void *x_caller = nullptr;                    // caller-order copy of permuted vectors
     std::vector<int64_t> color_start;           // permuted row start of each color
     // vectors
     void *x[2] = {nullptr, nullptr};
@@ -88,15 +98,18 @@ bool shape_ok(int st, int K, Shape sh)
     if (sh.NV != 1 && sh.NV != 2 && sh.NV != 4) return false;
     if (sh.U != 4 && sh.U != 8) return false;
     if (sh.G < 1 || sh.G > 32 || (sh.G & (sh.G - 1))) return false;
+    if (sh.stage < 0 || sh.stage > 2) return false;
     return sh.G * sh.NV == P;
 }
 
 // untuned default: one vector per lane, four nonzeros per batch (the
-// lightest shape in registers)
+// lightest shape in registers), CSR read directly
 Shape default_shape(int st, int K)
 {
-    return Shape{P_of(st, K), 1, 4};
+    return Shape{P_of(st, K), 1, 4, 0};
 }
+
+
 
 int fail(amgd_ctx *h, int code, const std::string &msg)
 {
@@ -115,6 +128,21 @@ int cuda_fail(amgd_ctx *h, cudaError_t e, const char *where)
         cudaError_t e__ = (expr);                                \
         if (e__ != cudaSuccess) return cuda_fail((h), e__, #expr); \
     } while (0)
+
+// read and clear the device status word (synchronises the stream)
+int poll_status(amgd_ctx *h)
+{
+    uint32_t st = 0;
+    CK(h, cudaMemcpyAsync(&st, h->status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (st) {
+        CK(h, cudaMemsetAsync(h->status, 0, sizeof st, h->stream));
+        return fail(h, AMGD_ERR_TIMEOUT,
+                    "a staged relaxation kernel gave up waiting for its shared-memory copies; "
+                    "the test vectors are not valid");
+    }
+    return AMGD_OK;
+}
 
 template <class T>
 cudaError_t dalloc(T **p, size_t count)
@@ -199,8 +227,22 @@ int upload_weights(amgd_ctx *h)
     return AMGD_OK;
 }
 
-// (re)build the FP64 and FP32 permuted value arrays from h->val_o
+// (re)build the FP64 and FP32 permuted value arrays from h->val_o, and the
+// permuted diagonal
+int permute_values_only(amgd_ctx *h);
 int permute_values(amgd_ctx *h)
+{
+    const int rc = permute_values_only(h);
+    if (rc != AMGD_OK) return rc;
+    CK(h, launch_diagonal(h->rp_p, h->col_p, h->val64, h->diag64, h->diag32, (int32_t)h->n, h->stream));
+    CK(h, launch_diagonal(h->rp_o, h->col_o, h->val_o, h->diag64_o, h->diag32_o, (int32_t)h->n, h->stream));
+    if (h->val32_o && h->val32_o != h->val32)
+        CK(h, launch_permute_values(h->val_o, h->rp_o, nullptr, h->rp_o, nullptr, h->val32_o,
+                                    (int32_t)h->n, h->stream));
+    return AMGD_OK;
+}
+
+int permute_values_only(amgd_ctx *h)
 {
     if (h->perm) {
         CK(h, launch_permute_values(h->val_o, h->rp_o, h->perm, h->rp_p, h->val64, h->val32,
@@ -235,9 +277,13 @@ int run_relax(amgd_ctx *h, int32_t nu, double omega, int sweep, cudaStream_t s)
 {
     const Shape sh = h->relax_shape[h->storage];
     RelaxArgs a;
+    a.status = h->status;
+    a.wait_limit = h->wait_limit;
+    a.extra_tx = h->test_extra_tx;
     a.rp = h->rp_p;
     a.col = h->col_p;
     a.val = h->storage == ST_FP64 ? (const void *)h->val64 : (const void *)h->val32;
+    a.diag = h->storage == ST_FP64 ? (const void *)h->diag64 : (const void *)h->diag32;
     a.Kp = Kp_of(h->storage, h->K);
     a.omega = omega;
     for (int32_t it = 0; it < nu; ++it) {
@@ -264,16 +310,24 @@ int run_relax(amgd_ctx *h, int32_t nu, double omega, int sweep, cudaStream_t s)
 
 int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
 {
+    // the edge pass runs on the caller's numbering: bring a row-permuted
+    // vector block back to caller order first
+    const void *xc = h->x[h->cur];
+    if (h->perm) {
+        if (!h->x_caller) return fail(h, AMGD_ERR_STATE, "caller-order vector buffer missing");
+        CK(h, launch_unpermute(h->storage, h->x[h->cur], h->x_caller, h->perm, (int32_t)h->n,
+                               Kp_of(h->storage, h->K), s));
+        xc = h->x_caller;
+    }
     EdgeArgs a;
-    a.rp = h->rp_p;
-    a.col = h->col_p;
-    a.val = h->storage == ST_FP64 ? (const void *)h->val64 : (const void *)h->val32;
-    a.val64 = h->val64;
-    a.x = h->x[h->cur];
+    a.rp = h->rp_o;
+    a.col = h->col_o;
+    a.val = h->storage == ST_FP64 ? (const void *)h->val_o : (const void *)h->val32_o;
+    a.diag = h->storage == ST_FP64 ? (const void *)h->diag64_o : (const void *)h->diag32_o;
+    a.val64 = h->val_o;
+    a.x = xc;
     a.w = h->storage == ST_FP64 ? (const void *)h->w64 : (const void *)h->w32;
     a.w64 = h->w64;
-    a.perm = h->perm;
-    a.rp_orig = h->rp_o;
     a.a_out = h->a;
     a.ls_out = h->ls;
     a.flag_out = h->flag;
@@ -378,9 +432,9 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
         cudaError_t e__ = (expr);                                          \
         if (e__ != cudaSuccess) return bail(cuda_fail(h, e__, #expr));     \
     } while (0)
-    TRY(dalloc(&h->rp_o, (size_t)n + 1));
-    TRY(dalloc(&h->col_o, (size_t)h->nnz));
-    TRY(dalloc(&h->val_o, (size_t)h->nnz));
+    TRY(dalloc(&h->rp_o, (size_t)n + 1 + 4));      // +16 bytes: widened bulk copies
+    TRY(dalloc(&h->col_o, (size_t)h->nnz + 4));   // +16 bytes: widened bulk copies
+    TRY(dalloc(&h->val_o, (size_t)h->nnz + 4));
     TRY(dalloc(&h->mat_off, (size_t)nmat + 1));
     TRY(cudaMemcpy(h->rp_o, h->h_rp.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     if (h->nnz) {
@@ -390,10 +444,29 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
     TRY(cudaMemcpy(h->mat_off, row_off.data(), (nmat + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
     TRY(dalloc(&h->diag_slot, (size_t)n));
     TRY(dalloc(&h->err_word, 1));
+    TRY(dalloc(&h->status, 1));
+    TRY(cudaMemset(h->status, 0, sizeof(uint32_t)));
+    // test hooks for the bounded-wait path (never set in normal use):
+    // AMGD_TEST_STAGING_EXTRA_TX declares bytes that no copy delivers, so the
+    // first staged wait runs out; AMGD_TEST_WAIT_LIMIT shortens the waits.
+    if (const char *e = getenv("AMGD_TEST_STAGING_EXTRA_TX")) h->test_extra_tx = (uint32_t)atoi(e);
+    if (const char *e = getenv("AMGD_TEST_WAIT_LIMIT")) h->wait_limit = atoll(e);
     if (n) TRY(cudaMemcpy(h->diag_slot, h->h_diag_slot.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
     h->rp_p = h->rp_o;
     h->col_p = h->col_o;
     h->val64 = h->val_o;
+    TRY(dalloc(&h->diag64, (size_t)n));
+    TRY(dalloc(&h->diag32, (size_t)n));
+    TRY(dalloc(&h->diag64_o, (size_t)n));
+    TRY(dalloc(&h->diag32_o, (size_t)n));
+    {
+        cudaError_t e = launch_diagonal(h->rp_p, h->col_p, h->val64, h->diag64, h->diag32,
+                                        (int32_t)n, h->stream);
+        if (e == cudaSuccess)
+            e = launch_diagonal(h->rp_o, h->col_o, h->val_o, h->diag64_o, h->diag32_o, (int32_t)n,
+                                h->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "launch_diagonal"));
+    }
     h->color_start = {0, n};
     TRY(dalloc(&h->flag, (size_t)h->nnz + 16));   // 16-byte loads past the end
     TRY(dalloc(&h->count, (size_t)n));
@@ -460,7 +533,8 @@ int amgd_set_precision(amgd_handle h, int storage)
         return fail(h, AMGD_ERR_ARG, "unknown storage precision");
     if (storage == h->storage) return AMGD_OK;
     if (storage != ST_FP64 && !h->val32) {
-        CK(h, dalloc(&h->val32, (size_t)h->nnz));
+        CK(h, dalloc(&h->val32, (size_t)h->nnz + 4));
+        CK(h, dalloc(&h->val32_o, (size_t)h->nnz + 4));
         int rc = permute_values(h);
         if (rc != AMGD_OK) return rc;
     }
@@ -484,6 +558,12 @@ int amgd_set_precision(amgd_handle h, int storage)
     cudaFree(h->x[1]);
     h->x[0] = nx[0];
     h->x[1] = nx[1];
+    if (h->x_caller) {
+        cudaFree(h->x_caller);
+        h->x_caller = nullptr;
+        const size_t bytes = (size_t)h->n * Kp_of(storage, h->K) * esize(storage);
+        CK(h, cudaMalloc(&h->x_caller, bytes ? bytes : 16));
+    }
     h->cur = 0;
     h->storage = storage;
     if (slot_type_changes) {
@@ -555,9 +635,13 @@ int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int 
     CK(h, cudaStreamSynchronize(h->stream));
     if (!h->perm) {
         CK(h, dalloc(&h->perm, (size_t)n));
-        CK(h, dalloc(&h->rp_p, (size_t)n + 1));
-        CK(h, dalloc(&h->col_p, (size_t)h->nnz));
-        CK(h, dalloc(&h->val64, (size_t)h->nnz));
+        CK(h, dalloc(&h->rp_p, (size_t)n + 1 + 4));
+        CK(h, dalloc(&h->col_p, (size_t)h->nnz + 4));
+        CK(h, dalloc(&h->val64, (size_t)h->nnz + 4));
+    }
+    if (!h->x_caller) {
+        const size_t bytes = (size_t)n * Kp_of(h->storage, h->K) * esize(h->storage);
+        CK(h, cudaMalloc(&h->x_caller, bytes ? bytes : 16));
     }
     CK(h, cudaMemcpy(h->perm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->rp_p, rp_p.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -614,7 +698,7 @@ int amgd_get_vectors(amgd_handle h, double *X, int mem)
                         Kp_of(h->storage, h->K), h->stream));
     CK(h, cudaMemcpyAsync(X, h->tmp64, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    return AMGD_OK;
+    return poll_status(h);
 }
 
 int amgd_set_values(amgd_handle h, const double *val, int mem)
@@ -623,7 +707,7 @@ int amgd_set_values(amgd_handle h, const double *val, int mem)
     if (!val && h->nnz) return fail(h, AMGD_ERR_ARG, "val is NULL");
     if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
     // stage on the device, check there, then swap the staging buffer in
-    CK(h, ensure_tmp64(h, (size_t)h->nnz));
+    CK(h, ensure_tmp64(h, (size_t)h->nnz + 4));
     CK(h, cudaMemcpyAsync(h->tmp64, val, h->nnz * sizeof(double),
                           mem == AMGD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                           h->stream));
@@ -637,7 +721,7 @@ int amgd_set_values(amgd_handle h, const double *val, int mem)
     double *old = h->val_o;
     h->val_o = h->tmp64;
     h->tmp64 = old;
-    h->tmp64_len = (size_t)h->nnz;
+    h->tmp64_len = (size_t)h->nnz + 4;
     if (!h->perm) h->val64 = h->val_o;
     int rc = permute_values(h);
     if (rc != AMGD_OK) return rc;
@@ -678,8 +762,7 @@ int amgd_distances(amgd_handle h, double theta, double *a, double *dist, double 
         CK(h, cudaMemcpyAsync(outs[k], h->tmp64, h->nnz * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
     }
-    CK(h, cudaStreamSynchronize(h->stream));
-    return AMGD_OK;
+    return poll_status(h);
 }
 
 int amgd_strength(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap,
@@ -705,6 +788,10 @@ int amgd_strength(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap
     int64_t total = 0;
     CK(h, cudaMemcpyAsync(&total, h->s_rp_tmp + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    {
+        const int rc = poll_status(h);
+        if (rc != AMGD_OK) return rc;
+    }
     if (nnz_s) *nnz_s = total;
     if (total > cap) return fail(h, AMGD_ERR_CAPACITY, "strength output needs " + std::to_string(total) + " columns");
     const cudaMemcpyKind k = mem == AMGD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -768,23 +855,26 @@ int amgd_graph_capture(amgd_handle h, uint64_t seed, int32_t nu, double omega, i
     return AMGD_OK;
 }
 
-int amgd_set_kernel_shape(amgd_handle h, int kernel, int G, int NV, int U)
+int amgd_set_kernel_shape(amgd_handle h, int kernel, int G, int NV, int U, int staged)
 {
     if (!h) return AMGD_ERR_ARG;
-    const Shape sh{G, NV, U};
-    if ((kernel != AMGD_KERNEL_RELAX && kernel != AMGD_KERNEL_EDGE) || !shape_ok(h->storage, h->K, sh))
+    const Shape sh{G, NV, U, staged};
+    if ((kernel != AMGD_KERNEL_RELAX && kernel != AMGD_KERNEL_EDGE) || !shape_ok(h->storage, h->K, sh) ||
+        (kernel == AMGD_KERNEL_EDGE && staged) ||
+        (kernel == AMGD_KERNEL_RELAX && !relax_shape_available(h->storage, sh)))
         return fail(h, AMGD_ERR_ARG, "invalid kernel shape for this storage and K");
     (kernel == AMGD_KERNEL_RELAX ? h->relax_shape : h->edge_shape)[h->storage] = sh;
     return AMGD_OK;
 }
 
-int amgd_get_kernel_shape(amgd_handle h, int kernel, int *G, int *NV, int *U)
+int amgd_get_kernel_shape(amgd_handle h, int kernel, int *G, int *NV, int *U, int *staged)
 {
     if (!h || (kernel != AMGD_KERNEL_RELAX && kernel != AMGD_KERNEL_EDGE)) return AMGD_ERR_ARG;
     const Shape sh = (kernel == AMGD_KERNEL_RELAX ? h->relax_shape : h->edge_shape)[h->storage];
     if (G) *G = sh.G;
     if (NV) *NV = sh.NV;
     if (U) *U = sh.U;
+    if (staged) *staged = sh.stage;
     return AMGD_OK;
 }
 
@@ -813,7 +903,7 @@ bool parse_shape(const std::string &line, const char *tag, Shape &sh)
     const std::string t = std::string(";") + tag + "=";
     const size_t p = line.find(t);
     if (p == std::string::npos) return false;
-    return sscanf(line.c_str() + p + t.size(), "%d,%d,%d", &sh.G, &sh.NV, &sh.U) == 3;
+    return sscanf(line.c_str() + p + t.size(), "%d,%d,%d,%d", &sh.G, &sh.NV, &sh.U, &sh.stage) == 4;
 }
 
 // median of `reps` timings (ms) of fn() on the handle's stream
@@ -859,7 +949,7 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
         FILE *f = fopen(cache_path, "r");
         if (f) {
             char buf[1024];
-            Shape r{0, 0, 0}, e{0, 0, 0};
+            Shape r{0, 0, 0, 0}, e{0, 0, 0, 0};
             bool found = false;
             while (fgets(buf, sizeof buf, f)) {
                 std::string line(buf);
@@ -879,10 +969,12 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
     }
     std::vector<Shape> cands;
     const int P = P_of(h->storage, h->K);
-    for (int NV : {1, 2, 4})
-        for (int U : {4, 8})
-            if (P % NV == 0 && shape_ok(h->storage, h->K, Shape{P / NV, NV, U}))
-                cands.push_back(Shape{P / NV, NV, U});
+    for (int stage : {0, 1, 2})
+        for (int NV : {1, 2, 4})
+            for (int U : {4, 8})
+                if (P % NV == 0 && shape_ok(h->storage, h->K, Shape{P / NV, NV, U, stage}) &&
+                    relax_shape_available(h->storage, Shape{P / NV, NV, U, stage}))
+                    cands.push_back(Shape{P / NV, NV, U, stage});
     const Shape keep_r = h->relax_shape[h->storage], keep_e = h->edge_shape[h->storage];
     const int cur = h->cur;
     Shape best_r = keep_r, best_e = keep_e;
@@ -895,6 +987,11 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
         int rc = time_ms(h, [&]() { int q = run_relax(h, 1, omega, sweep_type, h->stream); h->cur = cur; return q; }, 5, ms);
         if (rc != AMGD_OK) { h->relax_shape[h->storage] = keep_r; return rc; }
         if (ms < tr) { tr = ms; best_r = c; }
+        {
+            const int prc = poll_status(h);
+            if (prc != AMGD_OK) { h->relax_shape[h->storage] = keep_r; return prc; }
+        }
+        if (c.stage) continue;               // the edge pass has no staged variant
         h->edge_shape[h->storage] = c;
         rc = time_ms(h, [&]() { return run_edge(h, 0.5, h->stream); }, 5, ms);
         if (rc != AMGD_OK) { h->edge_shape[h->storage] = keep_e; return rc; }
@@ -907,8 +1004,9 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
     if (cache_path) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s;relax=%d,%d,%d;edge=%d,%d,%d;relax_ms=%.5f;edge_ms=%.5f\n", key.c_str(),
-                    best_r.G, best_r.NV, best_r.U, best_e.G, best_e.NV, best_e.U, tr, te);
+            fprintf(f, "%s;relax=%d,%d,%d,%d;edge=%d,%d,%d,%d;relax_ms=%.5f;edge_ms=%.5f\n",
+                    key.c_str(), best_r.G, best_r.NV, best_r.U, best_r.stage, best_e.G, best_e.NV,
+                    best_e.U, best_e.stage, tr, te);
             fclose(f);
         }
     }
@@ -928,7 +1026,7 @@ int amgd_phase_times(amgd_handle h, float *ms)
     if (!h->gexec || !h->graph_timed) return fail(h, AMGD_ERR_STATE, "no timed graph captured");
     CK(h, cudaEventSynchronize(h->ev[4]));
     for (int k = 0; k < 4; ++k) CK(h, cudaEventElapsedTime(&ms[k], h->ev[k], h->ev[k + 1]));
-    return AMGD_OK;
+    return poll_status(h);
 }
 
 int amgd_graph_launch(amgd_handle h)
@@ -956,7 +1054,9 @@ int amgd_destroy(amgd_handle h)
         dfree(h->col_p);
         dfree(h->val64);
     }
-    void *ptrs[] = {h->rp_o, h->col_o, h->val_o, h->mat_off, h->diag_slot, h->err_word, h->val32, h->x[0], h->x[1],
+    void *ptrs[] = {h->rp_o, h->col_o, h->val_o, h->mat_off, h->diag_slot, h->err_word, h->status,
+                    h->diag64, h->diag32, h->val32_o, h->diag64_o, h->diag32_o, h->x_caller,
+                    h->val32, h->x[0], h->x[1],
                     h->w64, h->w32, h->a, h->ls, h->flag, h->count, h->tile, h->s_rp_tmp,
                     h->s_col_tmp, h->tmp64};
     for (void *p : ptrs) dfree(p);

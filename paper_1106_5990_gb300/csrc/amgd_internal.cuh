@@ -113,15 +113,23 @@ __device__ __forceinline__ uint4 ldg16(const void *p)
 // gathered per batch.  P is fixed by (storage, K); G, NV and U are free.
 struct Shape {
     int G, NV, U;
+    int stage = 0;   // 1: persistent kernel with TMA-staged CSR tiles (relax only)
 };
+
+// device status bits set by bounded waits that gave up
+constexpr uint32_t kStatusStagingTimeout = 1u;
 
 // ---------------------------------------------------------------------------
 // launch arguments
 // ---------------------------------------------------------------------------
 struct RelaxArgs {
+    uint32_t *status = nullptr;     // device status word (bounded-wait time-outs)
+    long long wait_limit = 0;       // cycles a staged wait may take
+    uint32_t extra_tx = 0;          // test hook: bytes declared but never sent
     const int32_t *rp;    // permuted row_ptr
     const int32_t *col;   // permuted col
     const void *val;      // permuted values (double or float)
+    const void *diag;     // permuted diagonal a_ii, same type as val
     const void *xold;     // iterate at the start of the sweep
     void *xnew;           // rows [r0, r1) written; rows < split read from here
     int32_t r0, r1;       // rows of this color phase
@@ -130,18 +138,17 @@ struct RelaxArgs {
     double omega;
 };
 
-struct EdgeArgs {
-    const int32_t *rp, *col;     // permuted CSR
-    const void *val;             // permuted values, arithmetic type
-    const double *val64;         // permuted values, FP64 (mixed-path fallback)
-    const void *x;               // final test vectors (permuted rows)
+struct EdgeArgs {                // everything in the caller's numbering
+    const int32_t *rp, *col;     // CSR pattern
+    const void *val;             // values, arithmetic type
+    const void *diag;            // diagonal a_ii, arithmetic type
+    const double *val64;         // values in FP64 (mixed-path fallback)
+    const void *x;               // final test vectors, caller row order
     const void *w;               // LS weights, Kp long (zero padded), arithmetic type
     const double *w64;           // LS weights in FP64
-    const int32_t *perm;         // permuted row -> caller row (NULL = identity)
-    const int32_t *rp_orig;      // caller row_ptr (slot numbering of outputs)
-    void *a_out, *ls_out;        // per slot (caller numbering), arithmetic type
+    void *a_out, *ls_out;        // per slot, arithmetic type
     uint8_t *flag_out;           // per slot
-    int32_t *count_out;          // per caller row
+    int32_t *count_out;          // per row
     int32_t n, Kp, target;       // target: 0 residual, 1 plain
     double theta;
 };
@@ -158,6 +165,8 @@ struct InitArgs {
 // launchers (defined in the .cu files; return cudaGetLastError())
 // ---------------------------------------------------------------------------
 cudaError_t launch_relax(int storage, Shape sh, const RelaxArgs &a, cudaStream_t s);
+// false for a staged shape whose shared memory exceeds the per-block limit
+bool relax_shape_available(int storage, Shape sh);
 cudaError_t launch_edge(int storage, Shape sh, bool unit_w, const EdgeArgs &a, cudaStream_t s);
 cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t s);
 
@@ -173,6 +182,12 @@ cudaError_t launch_convert(int from, const void *src, int to, void *dst, int64_t
 cudaError_t launch_export_slots(int storage, const void *a_in, const void *ls_in,
                                 double *a, double *dist, double *ls, int64_t nnz,
                                 cudaStream_t s);
+// x_caller[perm[r]] = x[r] (rows of Kp storage elements)
+cudaError_t launch_unpermute(int storage, const void *x, void *x_caller, const int32_t *perm,
+                             int32_t n, int32_t Kp, cudaStream_t s);
+// diagonal of every permuted row (double and float copies)
+cudaError_t launch_diagonal(const int32_t *rp_perm, const int32_t *col_perm, const double *vp64,
+                            double *d64, float *d32, int32_t n, cudaStream_t s);
 // permuted values: vp[q] = v[slot of q in caller order] (double and float copies)
 cudaError_t launch_permute_values(const double *v, const int32_t *rp_orig,
                                   const int32_t *perm, const int32_t *rp_perm, double *vp64,

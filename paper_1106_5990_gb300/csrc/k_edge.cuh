@@ -19,13 +19,15 @@
 //      values of A, so cancellation never decides a distance.
 //   3. m_i = min_p LS_ip; slot p is strong iff LS_p = 0 or theta LS_p < m_i
 //      (§4.2, Eq. (4.4), r = 1/LS); per-row strong count.
-// Outputs go to the caller's slot numbering (row i of the permuted matrix is
-// row perm[i] of the caller, slot order unchanged).  Neighbour rows are
-// gathered U at a time with all loads in flight, as in k_relax.cu.
+// The pass runs on the caller's numbering (a row-permuted vector block is
+// copied back first), so every output lands where the caller expects it and
+// a warp's outputs form one contiguous run.  Neighbour rows are gathered U
+// at a time with all loads in flight, as in k_relax.cu.
 #pragma once
 #include <type_traits>
 
 #include "amgd_internal.cuh"
+#include "rowops.cuh"
 
 namespace amgd {
 namespace edge_impl {
@@ -104,6 +106,79 @@ template <> __device__ __forceinline__ float divide<float>(float a, float b)
     return __fdividef(a, b);
 }
 
+// sums over one 16-byte piece of (w) x x and (w) y x; FP32 pieces in packed pairs
+template <class C, int V, bool UW> struct PieceSums;
+
+template <int V, bool UW> struct PieceSums<double, V, UW> {
+    double xx = 0.0, yx = 0.0;
+    __device__ __forceinline__ void add(const double (&x)[V], const double (&y)[V], const double (&w)[V]) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const double wx = UW ? x[e] : w[e] * x[e];
+            xx = fma(wx, x[e], xx);
+            yx = fma(wx, y[e], yx);
+        }
+    }
+    __device__ __forceinline__ double sxx() const { return xx; }
+    __device__ __forceinline__ double syx() const { return yx; }
+};
+
+template <int V, bool UW> struct PieceSums<float, V, UW> {
+    float2 xx = make_float2(0.f, 0.f), yx = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(const float (&x)[V], const float (&y)[V], const float (&w)[V]) {
+#pragma unroll
+        for (int e = 0; e < V / 2; ++e) {
+            float2 x2 = make_float2(x[2 * e], x[2 * e + 1]);
+            const float2 wx = UW ? x2 : make_float2(w[2 * e] * x2.x, w[2 * e + 1] * x2.y);
+            xx = __ffma2_rn(wx, x2, xx);
+            yx = __ffma2_rn(wx, make_float2(y[2 * e], y[2 * e + 1]), yx);
+        }
+    }
+    __device__ __forceinline__ float sxx() const { return xx.x + xx.y; }
+    __device__ __forceinline__ float syx() const { return yx.x + yx.y; }
+};
+
+// sum over one piece of w (y - a x)^2, each residual one fused multiply-add
+template <class C, int V, bool UW>
+__device__ __forceinline__ void residual_add(C a, const C (&x)[V], const C (&y)[V], const C (&w)[V], C &res)
+{
+    if constexpr (std::is_same<C, float>::value) {
+        const float2 na = make_float2(-a, -a);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < V / 2; ++e) {
+            const float2 d = __ffma2_rn(na, make_float2(x[2 * e], x[2 * e + 1]),
+                                        make_float2(y[2 * e], y[2 * e + 1]));
+            const float2 wd = UW ? d : make_float2(w[2 * e] * d.x, w[2 * e + 1] * d.y);
+            acc = __ffma2_rn(wd, d, acc);
+        }
+        res += acc.x + acc.y;
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const C d = fma(-a, x[e], y[e]);
+            res = fma(UW ? d : w[e] * d, d, res);
+        }
+    }
+}
+
+// Per-warp output staging: a warp owns 32/G consecutive rows of the caller's
+// numbering, i.e. one contiguous run of CSR slots.  a, LS and the flags of
+// that run are collected in shared memory and written out with coalesced
+// stores (a run wider than warp_slots<G>() -- 16 slots per row on average --
+// is written directly).
+template <int G>
+constexpr int warp_slots()
+{
+    return (32 / G) * 16;
+}
+
+template <class C, int G>
+constexpr int edge_smem_bytes()
+{
+    return (kEdgeThreads / 32) * warp_slots<G>() * (2 * (int)sizeof(C) + 1);
+}
+
 template <class TS, int G, int NV, int U, bool UW>
 __global__ void __launch_bounds__(kEdgeThreads) k_edge(EdgeArgs A)
 {
@@ -112,17 +187,30 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge(EdgeArgs A)
     using AV = typename S::A;
     constexpr int V = S::V;
     constexpr bool kMixed = !std::is_same<C, double>::value;
+    constexpr int kWarpSlots = warp_slots<G>();
+    extern __shared__ __align__(16) unsigned char esm[];
 
-    const int lane = threadIdx.x % G;
-    const int grp_in_warp = (threadIdx.x % 32) / G;
+    const int lane = threadIdx.x % G, lane32 = threadIdx.x % 32, warp = threadIdx.x / 32;
+    const int grp_in_warp = lane32 / G;
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp_in_warp * G));
     const int64_t r = (int64_t)blockIdx.x * (kEdgeThreads / G) + threadIdx.x / G;
-    if (r >= A.n) return;
+    const int64_t wr0 = (int64_t)blockIdx.x * (kEdgeThreads / G) + (int64_t)warp * (32 / G);
+    if (wr0 >= A.n) return;                      // whole warp past the end
+    const bool active = r < A.n;
+
+    C *a_s = reinterpret_cast<C *>(esm) + (size_t)warp * kWarpSlots;
+    C *ls_s = reinterpret_cast<C *>(esm) + (size_t)(kEdgeThreads / 32) * kWarpSlots + (size_t)warp * kWarpSlots;
+    uint8_t *fl_s = esm + (size_t)(kEdgeThreads / 32) * kWarpSlots * 2 * sizeof(C) + (size_t)warp * kWarpSlots;
 
     const int32_t *__restrict__ col = A.col;
     const AV *__restrict__ val = (const AV *)A.val;
     const TS *__restrict__ X = (const TS *)A.x;
     const int Kp = A.Kp;
+    const int64_t wr1 = min((int64_t)A.n, wr0 + 32 / G);
+    const int wbase = __ldg(A.rp + wr0), wend = __ldg(A.rp + wr1);
+    const bool staged = wend - wbase <= kWarpSlots;
+    C *a_out = (C *)A.a_out;
+    C *ls_out = (C *)A.ls_out;
 
     C w[NV][V];
     if constexpr (!UW) {
@@ -132,151 +220,121 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge(EdgeArgs A)
             for (int e = 0; e < V; ++e) w[t][e] = ((const C *)A.w)[(t * G + lane) * V + e];
     }
 
-    const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
+    int p0 = 0, p1 = 0;
+    C m = C(INFINITY), diag = C(1);
+    if (active) {
+        p0 = __ldg(A.rp + r);
+        p1 = __ldg(A.rp + r + 1);
+        diag = (C)__ldg((const AV *)A.diag + r);
 
-    // ---- 1. target ------------------------------------------------------
-    C acc[NV][V], y[NV][V];
-#pragma unroll
-    for (int t = 0; t < NV; ++t)
-#pragma unroll
-        for (int e = 0; e < V; ++e) { acc[t][e] = C(0); y[t][e] = C(0); }
-    C diag = C(1);
-    for (int pb = p0; pb < p1; pb += U) {
-        int jj[U];
-        C vv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool ok = pb + u < p1;
-            jj[u] = ok ? __ldg(col + pb + u) : -1;
-            vv[u] = ok ? (C)__ldg(val + pb + u) : C(0);
-        }
-        uint4 raw[U][NV];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (jj[u] >= 0)
-#pragma unroll
-                for (int t = 0; t < NV; ++t)
-                    raw[u][t] = ldg16(X + (int64_t)jj[u] * Kp + (t * G + lane) * V);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (jj[u] < 0) break;
+        // ---- 1. target --------------------------------------------------
+        C y[NV][V];
+        {
+            Acc<C, V> acc[NV];
+            row_sum<TS, G, NV, U, false>(col, val, X, X, 0, Kp, lane, p0, p1, acc);
+            const C d = C(1) / diag;
 #pragma unroll
             for (int t = 0; t < NV; ++t) {
-                C x[V];
-                S::unpack(raw[u][t], x);
+                S::unpack(ldg16(X + r * Kp + (t * G + lane) * V), y[t]);      // x_i
+                if (A.target == 0) {
 #pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    if (jj[u] == r) y[t][e] = x[e];     // x_i for now
-                    acc[t][e] = fma(vv[u], x[e], acc[t][e]);
+                    for (int e = 0; e < V; ++e) y[t][e] = fma(-d, acc[t].get(e), y[t][e]);
                 }
             }
-            if (jj[u] == r) diag = vv[u];
         }
-    }
-    if (A.target == 0) {
-        const C d = C(1) / diag;
+        C syy = C(0);
+        if constexpr (kMixed) {
 #pragma unroll
-        for (int t = 0; t < NV; ++t)
+            for (int t = 0; t < NV; ++t)
 #pragma unroll
-            for (int e = 0; e < V; ++e) y[t][e] = fma(-d, acc[t][e], y[t][e]);
-    }
-    C syy = C(0);
-    if constexpr (kMixed) {
-#pragma unroll
-        for (int t = 0; t < NV; ++t)
-#pragma unroll
-            for (int e = 0; e < V; ++e)
-                syy = fma(UW ? y[t][e] : w[t][e] * y[t][e], y[t][e], syy);
-        syy = group_sum<G>(syy, gmask);
-    }
+                for (int e = 0; e < V; ++e)
+                    syy = fma(UW ? y[t][e] : w[t][e] * y[t][e], y[t][e], syy);
+            syy = group_sum<G>(syy, gmask);
+        }
+        const int off = p1 - p0 - 1;
 
-    const int off = p1 - p0 - 1;
-    const int32_t orow = A.perm ? __ldg(A.perm + r) : (int32_t)r;
-    const int64_t obase = __ldg(A.rp_orig + orow);
-    C *a_out = (C *)A.a_out;
-    C *ls_out = (C *)A.ls_out;
-
-    // ---- 2. one-point LS per off-diagonal ---------------------------------
-    C m = C(INFINITY);
-    for (int pb = p0; pb < p1; pb += U) {
-        int jj[U];
+        // ---- 2. one-point LS per off-diagonal -----------------------------
+        for (int pb = p0; pb < p1; pb += U) {
+            int jj[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) jj[u] = (pb + u < p1) ? __ldg(col + pb + u) : -1;
-        uint4 raw[U][NV];
+            for (int u = 0; u < U; ++u) jj[u] = (pb + u < p1) ? __ldg(col + pb + u) : -1;
+            uint4 raw[U][NV];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (jj[u] >= 0 && jj[u] != r)
+            for (int u = 0; u < U; ++u)
+                if (jj[u] >= 0 && jj[u] != r)
 #pragma unroll
-                for (int t = 0; t < NV; ++t)
-                    raw[u][t] = ldg16(X + (int64_t)jj[u] * Kp + (t * G + lane) * V);
+                    for (int t = 0; t < NV; ++t)
+                        raw[u][t] = ldg16(X + (int64_t)jj[u] * Kp + (t * G + lane) * V);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (jj[u] < 0) break;
-            const int p = pb + u;
-            C a_, ls_;
-            if (jj[u] == r) {
-                a_ = C(0);
-                ls_ = C(NAN);
-            } else if (A.target == 0 && off == 1) {
-                a_ = -(C)__ldg(val + p) / diag;
-                ls_ = C(0);
-            } else {
-                C xj[NV][V];
-                C sxx = C(0), syx = C(0);
+            for (int u = 0; u < U; ++u) {
+                if (jj[u] < 0) break;
+                const int p = pb + u;
+                C a_, ls_;
+                if (jj[u] == r) {
+                    a_ = C(0);
+                    ls_ = C(NAN);
+                } else if (A.target == 0 && off == 1) {
+                    a_ = -(C)__ldg(val + p) / diag;
+                    ls_ = C(0);
+                } else {
+                    C xj[NV][V];
+                    PieceSums<C, V, UW> ps;
 #pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    S::unpack(raw[u][t], xj[t]);
+                    for (int t = 0; t < NV; ++t) {
+                        S::unpack(raw[u][t], xj[t]);
+                        ps.add(xj[t], y[t], w[t]);
+                    }
+                    const C sxx = group_sum<G>(ps.sxx(), gmask);
+                    const C syx = group_sum<G>(ps.syx(), gmask);
+                    a_ = (sxx == C(0)) ? C(0) : divide(syx, sxx);
+                    C res = C(0);
 #pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        const C wx = UW ? xj[t][e] : w[t][e] * xj[t][e];
-                        sxx = fma(wx, xj[t][e], sxx);
-                        syx = fma(wx, y[t][e], syx);
+                    for (int t = 0; t < NV; ++t) residual_add<C, V, UW>(a_, xj[t], y[t], w[t], res);
+                    ls_ = group_sum<G>(res, gmask);
+                    if constexpr (kMixed) {
+                        if (ls_ < C(1e-4) * syy) {
+                            double a64, ls64;
+                            edge_fp64<TS, G, NV>(A, r, p0, p1, jj[u], lane, gmask, a64, ls64);
+                            a_ = (C)a64;
+                            ls_ = (C)ls64;
+                        }
                     }
                 }
-                sxx = group_sum<G>(sxx, gmask);
-                syx = group_sum<G>(syx, gmask);
-                a_ = (sxx == C(0)) ? C(0) : divide(syx, sxx);
-                C res = C(0);
-#pragma unroll
-                for (int t = 0; t < NV; ++t)
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        const C d = fma(-a_, xj[t][e], y[t][e]);
-                        res = fma(UW ? d : w[t][e] * d, d, res);
-                    }
-                ls_ = group_sum<G>(res, gmask);
-                if constexpr (kMixed) {
-                    if (ls_ < C(1e-4) * syy) {
-                        double a64, ls64;
-                        edge_fp64<TS, G, NV>(A, r, p0, p1, jj[u], lane, gmask, a64, ls64);
-                        a_ = (C)a64;
-                        ls_ = (C)ls64;
-                    }
+                if (jj[u] != r) m = fmin(m, ls_);
+                if (lane == 0) {
+                    if (staged) { a_s[p - wbase] = a_; ls_s[p - wbase] = ls_; }
+                    else { a_out[p] = a_; ls_out[p] = ls_; }
                 }
-            }
-            if (jj[u] != r) m = fmin(m, ls_);
-            if (lane == 0) {
-                const int64_t slot = obase + (p - p0);
-                a_out[slot] = a_;
-                ls_out[slot] = ls_;
             }
         }
     }
+    __syncwarp();
 
-    // ---- 3. strength flags -------------------------------------------------
-    __syncwarp(gmask);
+    // ---- 3. strength flags (from the LS values just produced) ----------------
     const C theta = (C)A.theta;
     int cnt = 0;
-    for (int p = p0 + lane; p < p1; p += G) {
-        const int64_t slot = obase + (p - p0);
-        const int j = __ldg(col + p);
-        const C l = ls_out[slot];
-        const int strong = (j != r) && (l == C(0) || theta * l < m);
-        A.flag_out[slot] = (uint8_t)strong;
-        cnt += strong;
+    if (active) {
+        for (int p = p0 + lane; p < p1; p += G) {
+            const int j = __ldg(col + p);
+            const C l = staged ? ls_s[p - wbase] : ls_out[p];
+            const int strong = (j != r) && (l == C(0) || theta * l < m);
+            if (staged) fl_s[p - wbase] = (uint8_t)strong;
+            else A.flag_out[p] = (uint8_t)strong;
+            cnt += strong;
+        }
+        cnt = group_sum<G>(cnt, gmask);
+        if (lane == 0) A.count_out[r] = cnt;
     }
-    cnt = group_sum<G>(cnt, gmask);
-    if (lane == 0) A.count_out[orow] = cnt;
+    __syncwarp();
+
+    // ---- coalesced write-out of the warp's slot run --------------------------
+    if (staged) {
+        for (int q = lane32; q < wend - wbase; q += 32) {
+            a_out[wbase + q] = a_s[q];
+            ls_out[wbase + q] = ls_s[q];
+            A.flag_out[wbase + q] = fl_s[q];
+        }
+    }
 }
 
 template <class TS, int G, int NV, int U, bool UW>
@@ -285,7 +343,17 @@ cudaError_t go(const EdgeArgs &a, cudaStream_t s)
     if (a.n <= 0) return cudaSuccess;
     const int rows_per_block = kEdgeThreads / G;
     const unsigned grid = (unsigned)(((int64_t)a.n + rows_per_block - 1) / rows_per_block);
-    k_edge<TS, G, NV, U, UW><<<grid, kEdgeThreads, 0, s>>>(a);
+    constexpr int smem = edge_smem_bytes<typename Store<TS>::C, G>();
+    if constexpr (smem > 48 * 1024) {
+        static bool opted = false;
+        if (!opted) {
+            const cudaError_t e = cudaFuncSetAttribute(k_edge<TS, G, NV, U, UW>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            opted = true;
+        }
+    }
+    k_edge<TS, G, NV, U, UW><<<grid, kEdgeThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -177,6 +177,29 @@ __global__ void k_permute_values(const double *__restrict__ v, const int32_t *__
     }
 }
 
+__global__ void k_unpermute(const uint4 *__restrict__ x, uint4 *__restrict__ xc,
+                            const int32_t *__restrict__ perm, int32_t n, int32_t pieces)
+{
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (t >= (int64_t)n * pieces) return;
+    const int64_t r = t / pieces;
+    const int q = (int)(t % pieces);
+    xc[(int64_t)perm[r] * pieces + q] = x[t];
+}
+
+__global__ void k_diagonal(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           const double *__restrict__ v, double *__restrict__ d64,
+                           float *__restrict__ d32, int32_t n)
+{
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= n) return;
+    double d = 0.0;
+    for (int p = rp[r]; p < rp[r + 1]; ++p)
+        if (col[p] == r) d = v[p];
+    if (d64) d64[r] = d;
+    if (d32) d32[r] = (float)d;
+}
+
 __global__ void k_check_values(const double *__restrict__ v, int64_t nnz,
                                const int32_t *__restrict__ diag_slot, int32_t n,
                                uint32_t *__restrict__ err)
@@ -280,6 +303,25 @@ cudaError_t launch_export_slots(int storage, const void *a_in, const void *ls_in
     else
         k_export_slots<<<blocks(nnz), kThreads, 0, s>>>((const float *)a_in, (const float *)ls_in,
                                                         a, dist, ls, nnz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute(int storage, const void *x, void *x_caller, const int32_t *perm,
+                             int32_t n, int32_t Kp, cudaStream_t s)
+{
+    const int esz = storage == ST_FP64 ? 8 : (storage == ST_FP32 ? 4 : 2);
+    const int32_t pieces = (int32_t)((int64_t)Kp * esz / 16);
+    const int64_t work = (int64_t)n * pieces;
+    if (work == 0) return cudaSuccess;
+    k_unpermute<<<blocks(work), kThreads, 0, s>>>((const uint4 *)x, (uint4 *)x_caller, perm, n, pieces);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagonal(const int32_t *rp_perm, const int32_t *col_perm, const double *vp64,
+                            double *d64, float *d32, int32_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_diagonal<<<blocks(n), kThreads, 0, s>>>(rp_perm, col_perm, vp64, d64, d32, n);
     return cudaGetLastError();
 }
 
