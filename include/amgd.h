@@ -148,10 +148,10 @@ int amgd_set_weights(amgd_handle h, const double *w);
 int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int mem);
 
 /* Reset the test vectors to the Philox4x64-10 start for `seed`: element
- * (i, k) of matrix b is 2 m 2^-53 - 1, m = word (k mod 4) of Philox4x64-10
- * at counter (i, k/4, 0, 0), key (seed, b), shifted right by 11 bits;
- * rounded to the storage precision.  (§3: relaxation starts from random
- * vectors.) */
+ * (i, k) of matrix b is (2m + 1) 2^-32 - 1, where m is the 32-bit half
+ * (k mod 2, low half first) of word ((k/2) mod 4) of Philox4x64-10 at counter
+ * (i, k/8, 0, 0), key (seed, b); rounded to the storage precision.  (§3:
+ * relaxation starts from random vectors.) */
 int amgd_init_vectors(amgd_handle h, uint64_t seed);
 
 /* Copy the test vectors in/out as an n x K row-major block of doubles

@@ -10,7 +10,7 @@
  *
  * What it computes, step by step (one row at a time, CSR order):
  *   1. test vectors X0: Philox4x64-10 counter-based random numbers mapped
- *      to uniform[-1,1)                         (§3: relax Ax=0 from random
+ *      to uniform(-1,1), 32 bits per element      (§3: relax Ax=0 from random
  *                                                 starting vectors)
  *   2. nu relaxation sweeps on A x = 0: weighted Jacobi, or multicolor
  *      Gauss-Seidel with snapshot semantics      (§3, §2: Gauss-Seidel)
@@ -74,10 +74,11 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
 
 /*
  * Test vectors X0 (n x K, row-major): §3 starts each test vector from a
- * random vector before relaxing A x = 0.  Element (i, kappa) takes word
- * (kappa mod 4) of Philox4x64-10 at counter (i, kappa / 4, 0, 0) and key
- * (seed, stream); the top 53 bits m give u = m * 2^-53 in [0,1) and
- * x = 2u - 1 in [-1,1).  Both steps are exact in double precision.
+ * random vector before relaxing A x = 0.  Element (i, kappa) takes the
+ * 32-bit half (kappa mod 2; 0 = low half) of word ((kappa / 2) mod 4) of
+ * Philox4x64-10 at counter (i, kappa / 8, 0, 0) and key (seed, stream): with
+ * that 32-bit integer m, x = (2m + 1) 2^-32 - 1, the midpoint of the m-th of
+ * 2^32 equal cells of (-1, 1).  Exact in double precision.
  * stream distinguishes the matrices of a batch (0 for a single matrix).
  */
 void orc_tv_init(int64_t n, int32_t K, uint64_t seed, uint64_t stream, double *X)
@@ -85,12 +86,12 @@ void orc_tv_init(int64_t n, int32_t K, uint64_t seed, uint64_t stream, double *X
     const uint64_t key[2] = {seed, stream};
     for (int64_t i = 0; i < n; ++i) {
         for (int32_t kappa = 0; kappa < K; ++kappa) {
-            uint64_t ctr[4] = {(uint64_t)i, (uint64_t)(kappa / 4), 0, 0};
+            uint64_t ctr[4] = {(uint64_t)i, (uint64_t)(kappa / 8), 0, 0};
             uint64_t out[4];
             orc_philox4x64_10(ctr, key, out);
-            uint64_t m = out[kappa % 4] >> 11;
-            double u = (double)m * 0x1.0p-53;
-            X[i * K + kappa] = 2.0 * u - 1.0;
+            uint64_t word = out[(kappa / 2) % 4];
+            uint64_t m = (kappa % 2 == 0) ? (word & 0xffffffffULL) : (word >> 32);
+            X[i * K + kappa] = ((double)(2 * m + 1)) * 0x1.0p-32 - 1.0;
         }
     }
 }
@@ -299,3 +300,4 @@ int64_t orc_strength_csr(int64_t n, const int64_t *rp, const int32_t *col, const
     }
     return k;
 }
+

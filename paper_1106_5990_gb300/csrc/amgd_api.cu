@@ -45,6 +45,8 @@ struct amgd_ctx {
     double *diag64_o = nullptr;                  // caller-order diagonal (edge pass)
     float *diag32_o = nullptr;
     void *x_caller = nullptr;                    // caller-order copy of permuted vectors
+    uint32_t *defer_count = nullptr;             // rows the mixed edge pass redoes in FP64
+    int32_t *defer_list = nullptr;
     std::vector<int64_t> color_start;           // permuted row start of each color
     // vectors
     void *x[2] = {nullptr, nullptr};
@@ -332,6 +334,8 @@ int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
     a.ls_out = h->ls;
     a.flag_out = h->flag;
     a.count_out = h->count;
+    a.defer_count = h->defer_count;
+    a.defer_list = h->defer_list;
     a.n = (int32_t)h->n;
     a.Kp = Kp_of(h->storage, h->K);
     a.target = h->target;
@@ -433,7 +437,7 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
         if (e__ != cudaSuccess) return bail(cuda_fail(h, e__, #expr));     \
     } while (0)
     TRY(dalloc(&h->rp_o, (size_t)n + 1 + 4));      // +16 bytes: widened bulk copies
-    TRY(dalloc(&h->col_o, (size_t)h->nnz + 4));   // +16 bytes: widened bulk copies
+    TRY(dalloc(&h->col_o, (size_t)h->nnz + 16));  // +64 bytes: widened bulk copies, 16-slot loads
     TRY(dalloc(&h->val_o, (size_t)h->nnz + 4));
     TRY(dalloc(&h->mat_off, (size_t)nmat + 1));
     TRY(cudaMemcpy(h->rp_o, h->h_rp.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -469,6 +473,8 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
     }
     h->color_start = {0, n};
     TRY(dalloc(&h->flag, (size_t)h->nnz + 16));   // 16-byte loads past the end
+    TRY(dalloc(&h->defer_count, 1));
+    TRY(dalloc(&h->defer_list, (size_t)n));
     TRY(dalloc(&h->count, (size_t)n));
     TRY(dalloc(&h->tile, (size_t)(n / kTileRows + 2)));
     if ((rc = alloc_slot_outputs(h, ST_FP64)) != AMGD_OK) return bail(rc);
@@ -1056,6 +1062,7 @@ int amgd_destroy(amgd_handle h)
     }
     void *ptrs[] = {h->rp_o, h->col_o, h->val_o, h->mat_off, h->diag_slot, h->err_word, h->status,
                     h->diag64, h->diag32, h->val32_o, h->diag64_o, h->diag32_o, h->x_caller,
+                    h->defer_count, h->defer_list,
                     h->val32, h->x[0], h->x[1],
                     h->w64, h->w32, h->a, h->ls, h->flag, h->count, h->tile, h->s_rp_tmp,
                     h->s_col_tmp, h->tmp64};

@@ -149,6 +149,8 @@ struct EdgeArgs {                // everything in the caller's numbering
     void *a_out, *ls_out;        // per slot, arithmetic type
     uint8_t *flag_out;           // per slot
     int32_t *count_out;          // per row
+    uint32_t *defer_count;       // rows appended to defer_list (mixed paths)
+    int32_t *defer_list;         // rows to redo in FP64 (capacity n)
     int32_t n, Kp, target;       // target: 0 residual, 1 plain
     double theta;
 };

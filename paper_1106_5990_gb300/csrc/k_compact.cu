@@ -113,7 +113,11 @@ k_compact(const int32_t *__restrict__ count, const int32_t *__restrict__ rp,
 
     // kept slots of the tile's slot range [s0, s1), in slot order: every
     // thread takes 16 consecutive flag bytes (one 16-byte load from a
-    // 16-byte-aligned base; the flag array is padded by 16 bytes)
+    // 16-byte-aligned base; the flag array is padded by 16 bytes) and, if any
+    // is set, their 16 column indices (four 16-byte loads; the column array is
+    // padded by 64 bytes).  The kept columns of a chunk are collected in
+    // shared memory and written out with coalesced stores.
+    __shared__ int32_t kept[kCompactThreads * kSlotsPerThread];
     const int64_t s0 = rp[row0], s1 = rp[row_end];
     int64_t out = off;
     for (int64_t base = s0 & ~(int64_t)15; base < s1;
@@ -131,10 +135,20 @@ k_compact(const int32_t *__restrict__ count, const int32_t *__restrict__ rp,
         const int cnt = __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
         int chunk;
         int pos = block_exclusive_scan<kCompactThreads>(cnt, chunk, sm);
+        if (cnt) {
+            int c16[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if ((w[k / 4] >> (8 * (k % 4))) & 1u) s_col[out + pos++] = col[first + k];
+            for (int q = 0; q < 4; ++q) {
+                const int4 c4 = __ldg(reinterpret_cast<const int4 *>(col + first) + q);
+                c16[4 * q] = c4.x; c16[4 * q + 1] = c4.y; c16[4 * q + 2] = c4.z; c16[4 * q + 3] = c4.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if ((w[k / 4] >> (8 * (k % 4))) & 1u) kept[pos++] = c16[k];
         }
+        __syncthreads();
+        for (int q = threadIdx.x; q < chunk; q += kCompactThreads) s_col[out + q] = kept[q];
+        __syncthreads();
         out += chunk;
     }
 }

@@ -42,62 +42,6 @@ __device__ __forceinline__ T group_sum(T v, unsigned mask)
     return v;
 }
 
-// Mixed-path fallback: the one-point fit of slot (r, j) in FP64 from the
-// stored vectors (widened exactly) and the FP64 values of A, y_i rebuilt
-// with the FP64 path's rounding.  Called by all G lanes of the row's group.
-// It runs only for edges whose FP32 functional cancelled, so it trades work
-// for registers: every component is rebuilt from scalar loads, twice.
-template <class TS>
-__device__ __forceinline__ double load_elem(const TS *p)
-{
-    if constexpr (std::is_same<TS, __nv_bfloat16>::value)
-        return (double)__bfloat162float(*p);
-    else
-        return (double)*p;
-}
-
-template <class TS>
-__device__ __forceinline__ double y64_elem(const EdgeArgs &A, int64_t r, int p0, int p1, int k)
-{
-    const TS *X = (const TS *)A.x;
-    double acc = 0.0, xi = 0.0, diag = 1.0;
-    for (int q = p0; q < p1; ++q) {
-        const int jj = __ldg(A.col + q);
-        const double v = __ldg(A.val64 + q);
-        const double x = load_elem<TS>(X + (int64_t)jj * A.Kp + k);
-        if (jj == r) { xi = x; diag = v; }
-        acc = fma(v, x, acc);
-    }
-    return (A.target == 0) ? fma(-(1.0 / diag), acc, xi) : xi;
-}
-
-template <class TS, int G, int NV>
-__device__ __forceinline__ void edge_fp64(const EdgeArgs &A, int64_t r, int p0, int p1, int j,
-                                       int lane, unsigned gmask, double &a64, double &ls64)
-{
-    constexpr int V = Store<TS>::V;
-    const TS *xj = (const TS *)A.x + (int64_t)j * A.Kp;
-    double sxx = 0.0, syx = 0.0;
-#pragma unroll 1
-    for (int c = 0; c < NV * V; ++c) {
-        const int k = ((c / V) * G + lane) * V + c % V;
-        const double x = load_elem<TS>(xj + k), wx = A.w64[k] * x;
-        sxx = fma(wx, x, sxx);
-        syx = fma(wx, y64_elem<TS>(A, r, p0, p1, k), syx);
-    }
-    sxx = group_sum<G>(sxx, gmask);
-    syx = group_sum<G>(syx, gmask);
-    a64 = (sxx == 0.0) ? 0.0 : syx / sxx;
-    double res = 0.0;
-#pragma unroll 1
-    for (int c = 0; c < NV * V; ++c) {
-        const int k = ((c / V) * G + lane) * V + c % V;
-        const double d = fma(-a64, load_elem<TS>(xj + k), y64_elem<TS>(A, r, p0, p1, k));
-        res = fma(A.w64[k] * d, d, res);
-    }
-    ls64 = group_sum<G>(res, gmask);
-}
-
 template <class C> __device__ __forceinline__ C divide(C a, C b) { return a / b; }
 // the mixed path's coefficient only needs FP32 relative accuracy (its error
 // enters LS at second order): the fast division is enough
@@ -179,8 +123,18 @@ constexpr int edge_smem_bytes()
     return (kEdgeThreads / 32) * warp_slots<G>() * (2 * (int)sizeof(C) + 1);
 }
 
+// AMGD_EDGE_MINB: minimum resident blocks per SM asked of the compiler (0: none)
+#ifndef AMGD_EDGE_MINB
+#define AMGD_EDGE_MINB 3
+#endif
+#if AMGD_EDGE_MINB > 0
+#define AMGD_EDGE_BOUNDS __launch_bounds__(kEdgeThreads, AMGD_EDGE_MINB)
+#else
+#define AMGD_EDGE_BOUNDS __launch_bounds__(kEdgeThreads)
+#endif
+
 template <class TS, int G, int NV, int U, bool UW>
-__global__ void __launch_bounds__(kEdgeThreads) k_edge(EdgeArgs A)
+__global__ void AMGD_EDGE_BOUNDS k_edge(EdgeArgs A)
 {
     using S = Store<TS>;
     using C = typename S::C;
@@ -222,6 +176,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge(EdgeArgs A)
 
     int p0 = 0, p1 = 0;
     C m = C(INFINITY), diag = C(1);
+    bool defer = false;       // a fit of this row cancelled in FP32: redo the row in FP64
     if (active) {
         p0 = __ldg(A.rp + r);
         p1 = __ldg(A.rp + r + 1);
@@ -291,14 +246,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge(EdgeArgs A)
 #pragma unroll
                     for (int t = 0; t < NV; ++t) residual_add<C, V, UW>(a_, xj[t], y[t], w[t], res);
                     ls_ = group_sum<G>(res, gmask);
-                    if constexpr (kMixed) {
-                        if (ls_ < C(1e-4) * syy) {
-                            double a64, ls64;
-                            edge_fp64<TS, G, NV>(A, r, p0, p1, jj[u], lane, gmask, a64, ls64);
-                            a_ = (C)a64;
-                            ls_ = (C)ls64;
-                        }
-                    }
+                    if constexpr (kMixed) defer = defer || ls_ < C(1e-4) * syy;
                 }
                 if (jj[u] != r) m = fmin(m, ls_);
                 if (lane == 0) {
@@ -324,6 +272,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge(EdgeArgs A)
         }
         cnt = group_sum<G>(cnt, gmask);
         if (lane == 0) A.count_out[r] = cnt;
+        if (kMixed && defer && lane == 0) A.defer_list[atomicAdd(A.defer_count, 1u)] = (int32_t)r;
     }
     __syncwarp();
 
@@ -334,6 +283,100 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge(EdgeArgs A)
             ls_out[wbase + q] = ls_s[q];
             A.flag_out[wbase + q] = fl_s[q];
         }
+    }
+}
+
+// Mixed paths: rows listed by k_edge (a fit cancelled in FP32, LS < 1e-4 S_yy)
+// are recomputed here entirely in FP64 from the stored vectors (widened
+// exactly) and the FP64 values of A: target with the FP64 path's rounding,
+// every one-point fit, the row minimum, flags and count.  One warp per row,
+// lanes over the K components (K <= 64: two per lane).
+template <class TS>
+__device__ __forceinline__ double elem64(const TS *p)
+{
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value)
+        return (double)__bfloat162float(*p);
+    else
+        return (double)*p;
+}
+
+template <class TS>
+__global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
+{
+    using C = typename Store<TS>::C;
+    const unsigned count = *A.defer_count;
+    const int lane = threadIdx.x % 32;
+    const TS *X = (const TS *)A.x;
+    const int Kp = A.Kp;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; q < count; q += warps) {
+        const int64_t r = A.defer_list[q];
+        const int p0 = A.rp[r], p1 = A.rp[r + 1];
+        double diag = 1.0;
+        for (int p = p0; p < p1; ++p)
+            if (A.col[p] == r) diag = A.val64[p];
+        const double d = 1.0 / diag;
+        double y[2], w[2];
+        for (int h = 0; h < 2; ++h) {
+            const int k = lane + 32 * h;
+            w[h] = k < Kp ? A.w64[k] : 0.0;
+            double acc = 0.0;
+            const double xi = k < Kp ? elem64(X + r * Kp + k) : 0.0;
+            if (k < Kp)
+                for (int p = p0; p < p1; ++p) acc = fma(A.val64[p], elem64(X + (int64_t)A.col[p] * Kp + k), acc);
+            y[h] = (A.target == 0) ? fma(-d, acc, xi) : xi;
+        }
+        const int off = p1 - p0 - 1;
+        double m = INFINITY;
+        C *a_out = (C *)A.a_out;
+        C *ls_out = (C *)A.ls_out;
+        for (int p = p0; p < p1; ++p) {
+            const int64_t j = A.col[p];
+            double a64, ls64;
+            if (j == r) {
+                a64 = 0.0;
+                ls64 = NAN;
+            } else if (A.target == 0 && off == 1) {
+                a64 = -A.val64[p] / diag;
+                ls64 = 0.0;
+            } else {
+                double xj[2], sxx = 0.0, syx = 0.0;
+                for (int h = 0; h < 2; ++h) {
+                    const int k = lane + 32 * h;
+                    xj[h] = k < Kp ? elem64(X + j * Kp + k) : 0.0;
+                    sxx = fma(w[h] * xj[h], xj[h], sxx);
+                    syx = fma(w[h] * xj[h], y[h], syx);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    sxx += __shfl_xor_sync(0xffffffffu, sxx, o);
+                    syx += __shfl_xor_sync(0xffffffffu, syx, o);
+                }
+                a64 = (sxx == 0.0) ? 0.0 : syx / sxx;
+                double res = 0.0;
+                for (int h = 0; h < 2; ++h) {
+                    const double e = fma(-a64, xj[h], y[h]);
+                    res = fma(w[h] * e, e, res);
+                }
+                for (int o = 16; o > 0; o >>= 1) res += __shfl_xor_sync(0xffffffffu, res, o);
+                ls64 = res;
+            }
+            if (j != r) m = fmin(m, ls64);
+            if (lane == 0) {
+                a_out[p] = (C)a64;
+                ls_out[p] = (C)ls64;
+            }
+        }
+        __syncwarp();
+        int cnt = 0;
+        for (int p = p0 + lane; p < p1; p += 32) {
+            const double l = (double)ls_out[p];
+            const int strong = (A.col[p] != r) && (l == 0.0 || A.theta * l < m);
+            A.flag_out[p] = (uint8_t)strong;
+            cnt += strong;
+        }
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) A.count_out[r] = cnt;
+        __syncwarp();
     }
 }
 

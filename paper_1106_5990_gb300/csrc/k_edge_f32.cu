@@ -5,7 +5,12 @@ namespace amgd {
 
 cudaError_t launch_edge_f32(Shape sh, bool unit_w, const EdgeArgs &a, cudaStream_t s)
 {
-    return edge_impl::dispatch_g<float>(sh, unit_w, a, s);
+    cudaError_t e = cudaMemsetAsync(a.defer_count, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    e = edge_impl::dispatch_g<float>(sh, unit_w, a, s);
+    if (e != cudaSuccess || a.n == 0) return e;
+    edge_impl::k_edge_fixup<float><<<152, 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace amgd

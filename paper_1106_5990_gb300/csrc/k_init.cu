@@ -49,26 +49,26 @@ template <> __device__ __forceinline__ double to_double<__nv_bfloat16>(__nv_bflo
     return (double)__bfloat162float(x);
 }
 
-// The start value of a component is x = d * 2^-52 with the integer
-// d = (word >> 11) - 2^52, |d| <= 2^52 (2u - 1 with u = (word >> 11) 2^-53).
+// The start value of a component is x = d * 2^-32 with the odd integer
+// d = 2m + 1 - 2^32, |d| < 2^32, m the component's 32-bit random integer.
 // It is produced in the storage type with integer arithmetic only -- the
 // FP64 pipe of the GPU is narrow -- and rounded to nearest even exactly once.
 template <class TS> __device__ __forceinline__ TS start_value(int64_t d);
 
 template <> __device__ __forceinline__ double start_value<double>(int64_t d)
 {
-    if (d == 0) return 0.0;                       // |d| < 2^53: exact in FP64
+    if (d == 0) return 0.0;                       // |d| < 2^33: exact in FP64
     const uint64_t sgn = d < 0 ? (1ull << 63) : 0ull;
     const uint64_t a = d < 0 ? (uint64_t)(-d) : (uint64_t)d;
-    const int lead = 63 - __clzll((long long)a);  // 0..52
+    const int lead = 63 - __clzll((long long)a);  // 0..31
     const uint64_t mant = (a << (52 - lead)) & ((1ull << 52) - 1ull);
-    const uint64_t expo = (uint64_t)(lead - 52 + 1023);
+    const uint64_t expo = (uint64_t)(lead - 32 + 1023);
     return __longlong_as_double((long long)(sgn | (expo << 52) | mant));
 }
 
 template <> __device__ __forceinline__ float start_value<float>(int64_t d)
 {
-    return __ll2float_rn(d) * 0x1.0p-52f;         // one rounding, exact scaling
+    return __ll2float_rn(d) * 0x1.0p-32f;         // one rounding, exact scaling
 }
 
 template <> __device__ __forceinline__ __nv_bfloat16 start_value<__nv_bfloat16>(int64_t d)
@@ -86,15 +86,16 @@ template <> __device__ __forceinline__ __nv_bfloat16 start_value<__nv_bfloat16>(
             a = q << sh;
         }
     }
-    const float f = __ull2float_rn(a) * 0x1.0p-52f;
+    const float f = __ull2float_rn(a) * 0x1.0p-32f;
     return __float2bfloat16_rn(d < 0 ? -f : f);
 }
 
-// one thread per (row, group of 4 components)
+// one thread per (row, block of 8 components): one Philox4x64-10 call
+// gives 4 x 64 bits = 8 components of 32 bits (low half first)
 template <class TS>
 __global__ void k_tv_init(InitArgs A)
 {
-    const int nq = (A.Kp + 3) / 4;
+    const int nq = (A.Kp + 7) / 8;
     const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (t >= (int64_t)A.n * nq) return;
     const int64_t r = t / nq;
@@ -109,11 +110,12 @@ __global__ void k_tv_init(InitArgs A)
     const U64x4 u = philox4x64_10(li, (uint64_t)q, 0ull, 0ull, A.seed, (uint64_t)lo);
     TS *x = (TS *)A.x + r * A.Kp;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int kappa = 4 * q + k;
+    for (int k = 0; k < 8; ++k) {
+        const int kappa = 8 * q + k;
         if (kappa >= A.Kp) break;
-        const int64_t d = (int64_t)(u.v[k] >> 11) - (1ll << 52);
-        x[kappa] = kappa < A.K ? start_value<TS>(d) : start_value<TS>(0);
+        const uint64_t m = (k & 1) ? (u.v[k / 2] >> 32) : (u.v[k / 2] & 0xffffffffull);
+        const int64_t d = (int64_t)(2 * m + 1) - (1ll << 32);
+        x[kappa] = kappa < A.K ? start_value<TS>(d) : from_double<TS>(0.0);
     }
 }
 
@@ -218,7 +220,7 @@ inline unsigned blocks(int64_t work) { return (unsigned)((work + kThreads - 1) /
 
 cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t s)
 {
-    const int64_t work = (int64_t)a.n * ((a.Kp + 3) / 4);
+    const int64_t work = (int64_t)a.n * ((a.Kp + 7) / 8);
     if (work == 0) return cudaSuccess;
     switch (storage) {
     case ST_FP64: k_tv_init<double><<<blocks(work), kThreads, 0, s>>>(a); break;

@@ -28,8 +28,19 @@ namespace {
 
 constexpr int kRelaxThreads = 256;
 
+// AMGD_RELAX_MINB: minimum resident blocks per SM asked of the compiler (0:
+// none -- an explicit minimum, even 1, changes the compiler's register target)
+#ifndef AMGD_RELAX_MINB
+#define AMGD_RELAX_MINB 0
+#endif
+#if AMGD_RELAX_MINB > 0
+#define AMGD_RELAX_BOUNDS __launch_bounds__(kRelaxThreads, AMGD_RELAX_MINB)
+#else
+#define AMGD_RELAX_BOUNDS __launch_bounds__(kRelaxThreads)
+#endif
+
 template <class TS, int G, int NV, int U, bool SPLIT>
-__global__ void __launch_bounds__(kRelaxThreads) k_relax(RelaxArgs A)
+__global__ void AMGD_RELAX_BOUNDS k_relax(RelaxArgs A)
 {
     using S = Store<TS>;
     using C = typename S::C;
@@ -42,10 +53,10 @@ __global__ void __launch_bounds__(kRelaxThreads) k_relax(RelaxArgs A)
     TS *xnew = (TS *)A.xnew;
     const int Kp = A.Kp;
 
-    const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
+    const int p0 = ld_csr(A.rp + r), p1 = ld_csr(A.rp + r + 1);
     Acc<C, V> acc[NV];
     row_sum<TS, G, NV, U, SPLIT>(A.col, (const AV *)A.val, xold, xnew, A.split, Kp, lane, p0, p1, acc);
-    const C c = (C)A.omega / __ldg((const AV *)A.diag + r);
+    const C c = (C)A.omega / ld_csr((const AV *)A.diag + r);
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
         C xi[V], out[V];

@@ -13,6 +13,13 @@
 
 namespace amgd {
 
+// read-only load of a CSR entry
+template <class T>
+__device__ __forceinline__ T ld_csr(const T *p)
+{
+    return __ldg(p);
+}
+
 // accumulator of the V components of one 16-byte piece
 template <class C, int V> struct Acc;
 
@@ -46,6 +53,8 @@ template <int V> struct Acc<float, V> {
 
 // s[tt][e] = sum_{p in [p0,p1)} val[p] * X[col[p]] (lane's pieces), in CSR
 // order.  SPLIT: rows j < split are read from xnew, the others from xold.
+// Nonzeros are taken U at a time: U column indices and values, then all U
+// gathers in flight before any is consumed.
 template <class TS, int G, int NV, int U, bool SPLIT>
 __device__ __forceinline__ void row_sum(const int32_t *__restrict__ col,
                                         const typename Store<TS>::A *__restrict__ val,
@@ -64,8 +73,8 @@ __device__ __forceinline__ void row_sum(const int32_t *__restrict__ col,
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const bool ok = pb + u < p1;
-            jj[u] = ok ? __ldg(col + pb + u) : -1;
-            vv[u] = ok ? (C)__ldg(val + pb + u) : C(0);
+            jj[u] = ok ? ld_csr(col + pb + u) : -1;
+            vv[u] = ok ? (C)ld_csr(val + pb + u) : C(0);
         }
         uint4 raw[U][NV];
 #pragma unroll

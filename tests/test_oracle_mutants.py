@@ -24,8 +24,9 @@ MUTANTS = [
     ("philox_hi_lo_swapped", "uint64_t n1 = lo1;", "uint64_t n1 = hi1;", 0),
     ("philox_key_not_bumped", "k1 += W1;", "k1 += 0;", 0),
     ("philox_wrong_multiplier_input", "orc_mulhilo64(M1, c2,", "orc_mulhilo64(M1, c1,", 0),
-    ("tv_map_drops_a_bit", "out[kappa % 4] >> 11", "out[kappa % 4] >> 12", 0),
-    ("tv_map_wrong_word", "out[kappa % 4]", "out[(kappa + 1) % 4]", 0),
+    ("tv_map_halves_swapped", "(kappa % 2 == 0) ?", "(kappa % 2 == 1) ?", 0),
+    ("tv_map_wrong_word", "out[(kappa / 2) % 4]", "out[(kappa / 2 + 1) % 4]", 0),
+    ("tv_map_not_centred", "((double)(2 * m + 1))", "((double)(2 * m))", 0),
     ("jacobi_sign", "Xn[i * K + kappa] = fma(-c, s,", "Xn[i * K + kappa] = fma(c, s,", 0),
     ("jacobi_drops_diagonal", "s = fma(val[p], X[(int64_t)col[p] * K + kappa], s);",
      "if (col[p] != i) s = fma(val[p], X[(int64_t)col[p] * K + kappa], s);", 0),
