@@ -76,6 +76,9 @@ class Oracle:
         L.orc_threshold.restype = None
         L.orc_strength_csr.argtypes = [i64, P, P, P, P, P]
         L.orc_strength_csr.restype = i64
+        L.orc_adjoint_jacobi.argtypes = [i64, P, P, P, i32, P, i32, P, i32, f64, f64, P, P, P,
+                                         P, P]
+        L.orc_adjoint_jacobi.restype = ctypes.c_int
         self.L = L
         self.path = path
 
@@ -179,6 +182,27 @@ class Oracle:
         s_rp, s_col = self.strength_csr(rp, col, flag)
         return dict(X=Xnu, Y=Y, a=a, ls=ls, flag=flag, count=count, s_rp=s_rp, s_col=s_col)
 
+    def adjoint_jacobi(self, rp, col, val, X0, nu: int, omega: float, theta: float, w=None,
+                       mode: int = TARGET_RESIDUAL, ls_bar=None):
+        """Reverse pass through nu Jacobi sweeps, the target and the one-point
+        fits.  ls_bar None: the loss is the sum of r^2 = LS^-2 over the kept
+        slots with LS > 0.  Returns dict(val_bar, omega_bar, loss, x0_bar)."""
+        rp, col, val = _csr(rp, col, val)
+        X0 = np.ascontiguousarray(X0, dtype=np.float64)
+        n, K = X0.shape
+        w = np.ones(K) if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        lsb = None if ls_bar is None else np.ascontiguousarray(ls_bar, dtype=np.float64)
+        vb = np.empty(len(col))
+        xb = np.empty_like(X0)
+        wb = ctypes.c_double()
+        loss = ctypes.c_double()
+        rc = self.L.orc_adjoint_jacobi(n, _p(rp), _p(col), _p(val), K, _p(w), mode, _p(X0), nu,
+                                       omega, theta, None if lsb is None else _p(lsb), _p(vb),
+                                       ctypes.byref(wb), ctypes.byref(loss), _p(xb))
+        if rc != 0:
+            raise MemoryError("oracle adjoint: out of memory")
+        return dict(val_bar=vb, omega_bar=wb.value, loss=loss.value, x0_bar=xb)
+
 
 _default = None
 
@@ -260,6 +284,22 @@ def build(rp, col, val, K, seed, nu, omega, theta, sweep=SWEEP_JACOBI, color=Non
           w=None, mode=TARGET_RESIDUAL, X0=None, stream=0):
     return default().build(rp, col, val, K, seed, nu, omega, theta, sweep, color, w, mode,
                            X0, stream)
+
+
+def adjoint_jacobi(rp, col, val, X0, nu, omega, theta, w=None, mode=TARGET_RESIDUAL, ls_bar=None):
+    return default().adjoint_jacobi(rp, col, val, X0, nu, omega, theta, w, mode, ls_bar)
+
+
+def strength_loss(rp, col, val, X0, nu, omega, theta, w=None, mode=TARGET_RESIDUAL):
+    """(loss, flag): the sum of r^2 = LS^-2 over the kept slots with LS > 0,
+    by the forward path alone (Jacobi sweeps)."""
+    o = default()
+    Xnu = o.relax(rp, col, val, X0, nu, omega, SWEEP_JACOBI)
+    Y = o.target(rp, col, val, Xnu, mode)
+    a, ls = o.edge_ls(rp, col, val, Xnu, Y, w, mode)
+    flag, _ = o.threshold(rp, col, ls, theta)
+    keep = (flag == 1) & (ls > 0)
+    return float(np.sum(1.0 / ls[keep] ** 2)), flag
 
 
 def strength_ratio(rp, col, ls) -> np.ndarray:

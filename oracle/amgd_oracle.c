@@ -21,6 +21,8 @@
  *                                                 (§4.1, Eq. (4.3))
  *   5. row-relative threshold r_ij > theta * max_k r_ik  (§4.2, Eq. (4.4))
  *   6. the strength graph as CSR                  (§4.2)
+ *   7. (extension) the reverse pass of steps 2-5 for Jacobi sweeps: the
+ *      gradient of a loss on LS with respect to A's values, omega and X0
  *
  * Rounding conventions (the paper fixes none): every multiply-accumulate of
  * a row sum is one fused multiply-add (C99 fma, a single rounding), sums run
@@ -301,3 +303,153 @@ int64_t orc_strength_csr(int64_t n, const int64_t *rp, const int32_t *col, const
     return k;
 }
 
+/* ------------------------------------------------------------------------ */
+/* 7. Reverse pass.  The paper differentiates nothing; this is the chain    */
+/*    rule applied to steps 2-5 for weighted-Jacobi sweeps, written out     */
+/*    term by term.  Forward:                                               */
+/*      X_{s+1} = X_s - omega D^{-1} A X_s          (s = 0 .. nu-1)         */
+/*      Y       = X_nu - D^{-1} A X_nu  (mode 0)    or Y = X_nu (mode 1)    */
+/*      a_p, LS_p from (y_i, x_j) per off-diagonal slot p = (i,j)           */
+/*    and a scalar loss L(LS) whose gradient ls_bar = dL/dLS is given, or   */
+/*    (ls_bar == NULL) L = sum of r_p^2 = LS_p^-2 over the slots the        */
+/*    threshold keeps with LS_p > 0 (the kept set is held fixed).          */
+/*    Since a_p minimises LS_p(a), dLS_p/da_p = 0 there and                 */
+/*      dLS_p/dy_i = 2 w (y_i - a_p x_j),  dLS_p/dx_j = -2 w a_p (y_i - a_p x_j). */
+/*    LS_p of a one-off-diagonal row in mode 0 is the constant 0: no        */
+/*    gradient flows through it.  A diagonal value a_ii enters both A and   */
+/*    D; val_bar holds the sum of both contributions.                       */
+/*    Outputs: val_bar (nnz, aligned with A's slots), omega_bar, loss (only */
+/*    for the built-in loss), x0_bar (n*K, may be NULL).  Returns 0, or -5  */
+/*    when memory runs out.                                                 */
+/* ------------------------------------------------------------------------ */
+int orc_adjoint_jacobi(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                       int32_t K, const double *w, int32_t mode, const double *X0, int32_t nu,
+                       double omega, double theta, const double *ls_bar, double *val_bar,
+                       double *omega_bar, double *loss, double *x0_bar)
+{
+    const int64_t nnz = rp[n];
+    const size_t nk = (size_t)n * (size_t)K;
+    double *Xs = (double *)malloc((size_t)(nu + 1) * nk * sizeof(double) + 1);
+    double *Y = (double *)malloc(nk * sizeof(double) + 1);
+    double *Ybar = (double *)calloc(nk + 1, sizeof(double));
+    double *Xbar = (double *)calloc(nk + 1, sizeof(double));
+    double *Xnext = (double *)malloc(nk * sizeof(double) + 1);
+    double *a = (double *)malloc((size_t)nnz * sizeof(double) + 1);
+    double *ls = (double *)malloc((size_t)nnz * sizeof(double) + 1);
+    double *lsb = (double *)calloc((size_t)nnz + 1, sizeof(double));
+    uint8_t *flag = (uint8_t *)malloc((size_t)nnz + 1);
+    int64_t *count = (int64_t *)malloc((size_t)n * sizeof(int64_t) + 1);
+    int rc = 0;
+    if (!Xs || !Y || !Ybar || !Xbar || !Xnext || !a || !ls || !lsb || !flag || !count) {
+        rc = -5;
+        goto done;
+    }
+
+    /* forward, keeping every iterate */
+    memcpy(Xs, X0, nk * sizeof(double));
+    for (int32_t s = 0; s < nu; ++s)
+        orc_jacobi_sweep(n, rp, col, val, K, omega, Xs + (size_t)s * nk, Xs + (size_t)(s + 1) * nk);
+    const double *Xnu = Xs + (size_t)nu * nk;
+    orc_target(n, rp, col, val, K, mode, Xnu, Y);
+    orc_edge_ls(n, rp, col, val, K, w, mode, Xnu, Y, a, ls);
+    orc_threshold(n, rp, col, ls, theta, flag, count);
+
+    /* upstream gradient dL/dLS */
+    double L = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t off = 0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+            if (col[p] != i) ++off;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            if (col[p] == i || (mode == 0 && off == 1)) continue;
+            if (ls_bar) {
+                lsb[p] = ls_bar[p];
+            } else if (flag[p] && ls[p] > 0.0) {
+                L += 1.0 / (ls[p] * ls[p]);
+                lsb[p] = -2.0 / (ls[p] * ls[p] * ls[p]);
+            }
+        }
+    }
+    if (loss) *loss = ls_bar ? NAN : L;
+
+    /* through the one-point fits: Ybar and the direct part of Xbar(nu) */
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            int64_t j = col[p];
+            if (j == i || lsb[p] == 0.0) continue;
+            for (int32_t kappa = 0; kappa < K; ++kappa) {
+                double e = Y[i * K + kappa] - a[p] * Xnu[j * K + kappa];
+                Ybar[i * K + kappa] += lsb[p] * 2.0 * w[kappa] * e;
+                Xbar[j * K + kappa] += -lsb[p] * 2.0 * w[kappa] * a[p] * e;
+            }
+        }
+    }
+
+    for (int64_t p = 0; p < nnz; ++p) val_bar[p] = 0.0;
+    double wbar = 0.0;
+
+    /* through the target */
+    if (mode == 1) {
+        for (size_t q = 0; q < nk; ++q) Xbar[q] += Ybar[q];
+    } else {
+        for (int64_t i = 0; i < n; ++i) {
+            double aii = orc_diag(rp, col, val, i);
+            int64_t pd = -1;
+            double yr = 0.0;                 /* <Ybar_i, (A X_nu)_i> */
+            for (int32_t kappa = 0; kappa < K; ++kappa) {
+                double r = 0.0;
+                for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+                    r += val[p] * Xnu[(int64_t)col[p] * K + kappa];
+                yr += Ybar[i * K + kappa] * r;
+                Xbar[i * K + kappa] += Ybar[i * K + kappa];
+            }
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                int64_t j = col[p];
+                if (j == i) pd = p;
+                double g = 0.0;              /* <Ybar_i, X_nu,j> */
+                for (int32_t kappa = 0; kappa < K; ++kappa) {
+                    g += Ybar[i * K + kappa] * Xnu[j * K + kappa];
+                    Xbar[j * K + kappa] -= (val[p] / aii) * Ybar[i * K + kappa];
+                }
+                val_bar[p] -= g / aii;
+            }
+            val_bar[pd] += yr / (aii * aii);
+        }
+    }
+
+    /* through the sweeps, last to first: Xbar holds Xbar(s+1) on entry */
+    for (int32_t s = nu - 1; s >= 0; --s) {
+        const double *Xc = Xs + (size_t)s * nk;
+        memcpy(Xnext, Xbar, nk * sizeof(double));   /* Xbar(s+1) */
+        for (int64_t i = 0; i < n; ++i) {
+            double aii = orc_diag(rp, col, val, i);
+            int64_t pd = -1;
+            double xr = 0.0;                 /* <Xbar_i(s+1), (A X_s)_i> */
+            for (int32_t kappa = 0; kappa < K; ++kappa) {
+                double r = 0.0;
+                for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+                    r += val[p] * Xc[(int64_t)col[p] * K + kappa];
+                xr += Xnext[i * K + kappa] * r;
+            }
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                int64_t j = col[p];
+                if (j == i) pd = p;
+                double g = 0.0;              /* <Xbar_i(s+1), X_s,j> */
+                for (int32_t kappa = 0; kappa < K; ++kappa) {
+                    g += Xnext[i * K + kappa] * Xc[j * K + kappa];
+                    Xbar[j * K + kappa] -= omega * (val[p] / aii) * Xnext[i * K + kappa];
+                }
+                val_bar[p] -= omega * g / aii;
+            }
+            val_bar[pd] += omega * xr / (aii * aii);
+            wbar -= xr / aii;
+        }
+    }
+    if (omega_bar) *omega_bar = wbar;
+    if (x0_bar) memcpy(x0_bar, Xbar, nk * sizeof(double));
+
+done:
+    free(Xs); free(Y); free(Ybar); free(Xbar); free(Xnext);
+    free(a); free(ls); free(lsb); free(flag); free(count);
+    return rc;
+}

@@ -11,13 +11,15 @@ import os
 import pytest
 
 import oracle
+import test_oracle_adjoint as adj
 import test_oracle_pins as pins
 
 PINS = [pins.pin_philox_numpy, pins.pin_tv_init, pins.pin_jacobi_dense_power,
         pins.pin_mcgs_proper_coloring_is_gauss_seidel, pins.pin_mcgs_snapshot_matrix_form,
         pins.pin_target, pins.pin_ls_lstsq, pins.pin_ls_brute_force, pins.pin_ls_invariants,
         pins.pin_ls_exact_cases, pins.pin_degree_one_rows, pins.pin_threshold,
-        pins.pin_strength_csr]
+        pins.pin_strength_csr, adj.pin_adjoint_fd, adj.pin_adjoint_homogeneity,
+        adj.pin_adjoint_special_cases]
 
 # (name, text to find, replacement, occurrence index)
 MUTANTS = [
@@ -51,6 +53,22 @@ MUTANTS = [
      "strong = (ls[p] == 0.0) || (theta * ls[p] < m); else strong = 1;", 0),
     ("csr_writes_slot_not_column", "if (flag[p]) s_col[k++] = col[p];",
      "if (flag[p]) s_col[k++] = (int32_t)(p - rp[i]);", 0),
+    ("adj_drops_target_diagonal", "val_bar[pd] += yr / (aii * aii);", "val_bar[pd] += 0.0 * yr;", 0),
+    ("adj_drops_sweep_diagonal", "val_bar[pd] += omega * xr / (aii * aii);",
+     "val_bar[pd] += 0.0 * xr;", 0),
+    ("adj_omega_sign", "wbar -= xr / aii;", "wbar += xr / aii;", 0),
+    ("adj_ybar_missing_two", "Ybar[i * K + kappa] += lsb[p] * 2.0 * w[kappa] * e;",
+     "Ybar[i * K + kappa] += lsb[p] * w[kappa] * e;", 0),
+    ("adj_envelope_sign", "Xbar[j * K + kappa] += -lsb[p] * 2.0 * w[kappa] * a[p] * e;",
+     "Xbar[j * K + kappa] += lsb[p] * 2.0 * w[kappa] * a[p] * e;", 0),
+    ("adj_not_transposed", "Xbar[j * K + kappa] -= omega * (val[p] / aii) * Xnext[i * K + kappa];",
+     "Xbar[i * K + kappa] -= omega * (val[p] / aii) * Xnext[j * K + kappa];", 0),
+    ("adj_uses_later_iterate", "const double *Xc = Xs + (size_t)s * nk;",
+     "const double *Xc = Xs + (size_t)(s + 1) * nk;", 0),
+    ("adj_loss_power", "lsb[p] = -2.0 / (ls[p] * ls[p] * ls[p]);",
+     "lsb[p] = -1.0 / (ls[p] * ls[p] * ls[p]);", 0),
+    ("adj_weights_dropped", "Xbar[j * K + kappa] += -lsb[p] * 2.0 * w[kappa] * a[p] * e;",
+     "Xbar[j * K + kappa] += -lsb[p] * 2.0 * a[p] * e;", 0),
 ]
 
 
