@@ -61,9 +61,10 @@ WORKLOADS = {
                K=16, seed=6, nu=4, omega=2.0 / 3.0, sweep="jacobi", theta=0.5,
                precision="bf16"),
     "c5": dict(name="anisotropic diffusion 5-point (eps=1e-2), 512x512 grid; K=16, nu=10 "
-                    "Jacobi omega=2/3 (forward)",
+                    "Jacobi omega=2/3; forward + reverse pass of sum r^2 over strong edges, "
+                    "checkpoints every 2 sweeps",
                K=16, seed=7, nu=10, omega=2.0 / 3.0, sweep="jacobi", theta=0.5,
-               precision="fp32"),
+               precision="fp32", adjoint=2),
 }
 
 
@@ -108,6 +109,34 @@ def algorithmic_bytes(n, nnz, E, E_s, K, nu, ncolors, precision, permuted):
     strength = 4 * n * 2 + nnz + 4 * E_s * 2 + 8 * (n + 1)
     return dict(init=init, sweep=sweep, relax=nu * sweep, relax_per_launch=sweep / ncolors,
                 edge=edge, strength=strength, total=init + nu * sweep + edge + strength)
+
+
+def adjoint_bytes(n, nnz, K, nu, every, precision):
+    """Algorithmic bytes of one forward + reverse step (Jacobi sweeps,
+    checkpoints every `every` sweeps, built-in loss): every array the step
+    must touch, each once per pass that needs it."""
+    s_x = SIZES[precision]
+    cs = 8 if precision == "fp64" else 4
+    s_a = cs
+    X = n * K * s_x                     # one stored iterate
+    Xc = n * K * cs                     # one arithmetic-type block (Y, Ybar, Xbar)
+    csr = nnz * (4 + s_a) + 4 * (n + 1)
+    csr_t = nnz * (4 + 4) + 4 * (n + 1)  # transposed pattern: rows and slots
+    sweep = csr + 2 * X
+    nck = -(-nu // every)
+    fwd = X + 2 * X + nu * sweep                               # start, checkpoint 0, sweeps
+    edge = csr + X + nnz * (2 * cs + 1) + 4 * n
+    up = 4 * (n + 1) + nnz * (4 + cs + 1 + 8)
+    bvals = csr_t + nnz * 8 + 8 * n + nnz * cs
+    edge_bwd = csr + X + nnz * (8 + cs) + 2 * Xc + nnz * cs
+    xbar_nu = csr_t + nnz * (8 + 2 * cs) + X + 3 * Xc
+    recompute = (nu - nck) * sweep
+    gram = nnz * 4 + 4 * (n + 1) + X + Xc + nnz * cs * 2
+    spmm_t = csr_t - nnz * 4 + nnz * cs + 2 * Xc
+    finish = nnz * (4 + 8 + 2 * cs + 8) + n * (4 + 8 + 4)
+    bwd = up + bvals + edge_bwd + xbar_nu + recompute + nu * (gram + spmm_t) + finish
+    return dict(forward=fwd, edge=edge, backward=bwd, relax_per_launch=sweep,
+                total=fwd + edge + bwd)
 
 
 def source_sha(*names):
@@ -197,6 +226,8 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_clocks=True,
                 tune_cache=None):
+    """One step = one captured build (or, for a workload with a checkpoint
+    interval, one captured forward + reverse step)."""
     import torch
     from paper_1106_5990_gb300 import amgd
 
@@ -217,8 +248,14 @@ def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_cloc
     h.init_vectors(w["seed"])
     d_rp = torch.empty(h.n + 1, dtype=torch.int64, device="cuda")
     d_col = torch.empty(max(h.E, 1), dtype=torch.int32, device="cuda")
+    d_vb = None
     h.enable_phase_timing(True)
-    h.graph_capture(w["seed"], w["nu"], w["omega"], sweep, w["theta"], d_rp, d_col)
+    if w.get("adjoint"):
+        h.set_checkpointing(w["adjoint"])
+        d_vb = torch.empty(max(h.nnz, 1), dtype=torch.float64, device="cuda")
+        h.graph_capture_backward(w["seed"], w["nu"], w["omega"], w["theta"], d_vb)
+    else:
+        h.graph_capture(w["seed"], w["nu"], w["omega"], sweep, w["theta"], d_rp, d_col)
     for _ in range(warmup):
         h.graph_launch()
     torch.cuda.synchronize()
@@ -242,12 +279,14 @@ def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_cloc
     _barrier()
     clk = clocks.stop() if clocks else None
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    E_s = int(d_rp[-1].item())
+    E_s = int(d_rp[-1].item()) if d_vb is None else None
+    scal = h.backward_scalars() if d_vb is not None else None
     return dict(h=h, step_ms=step_ms, phase_ms=phase / steps, E_s=E_s, ncolors=ncolors,
-                sweep=sweep, clocks=clk, d_rp=d_rp, d_col=d_col, shapes=shapes)
+                sweep=sweep, clocks=clk, d_rp=d_rp, d_col=d_col, shapes=shapes, d_vb=d_vb,
+                scalars=scal)
 
 
-def run_e2e(h, mats, w, sweep, steps):
+def run_e2e(h, mats, w, sweep, steps, adjoint=None):
     """Through the public API with host buffers: per step the matrix values
     are copied from pinned host memory (amgd_set_values) and the strength CSR
     is read back to pinned host memory (amgd_strength, host mode)."""
@@ -261,6 +300,9 @@ def run_e2e(h, mats, w, sweep, steps):
     s_col = torch.empty(max(h.E, 1), dtype=torch.int32).pin_memory()
     L = amgd.lib()
     nnz_s = ctypes.c_int64()
+    vb_h = torch.empty(len(vals), dtype=torch.float64).pin_memory() if adjoint else None
+    if adjoint:
+        h.set_checkpointing(adjoint)
     times = []
     torch.cuda.synchronize()
     for _ in range(steps):
@@ -269,12 +311,31 @@ def run_e2e(h, mats, w, sweep, steps):
         h.init_vectors(w["seed"])
         h.relax(w["nu"], w["omega"], sweep)
         amgd.check(L.amgd_distances(h.h, w["theta"], None, None, None, amgd.AMGD_MEM_DEVICE), h.h)
-        amgd.check(L.amgd_strength(h.h, s_rp.data_ptr(), s_col.data_ptr(), s_col.numel(),
-                                   ctypes.byref(nnz_s), amgd.AMGD_MEM_HOST), h.h)
+        if adjoint:
+            h.backward(out=vb_h)                 # dL/dvalues to pinned host memory
+        else:
+            amgd.check(L.amgd_strength(h.h, s_rp.data_ptr(), s_col.data_ptr(), s_col.numel(),
+                                       ctypes.byref(nnz_s), amgd.AMGD_MEM_HOST), h.h)
         times.append(time.perf_counter() - t0)
     t = float(np.mean(times))
+    if adjoint:
+        return dict(seconds=t, h2d=int(vals.nbytes), d2h=int(vals.nbytes) + 16, E_s=None)
     return dict(seconds=t, h2d=int(vals.nbytes),
                 d2h=int((h.n + 1) * 8 + nnz_s.value * 4 + 8), E_s=int(nnz_s.value))
+
+
+def oracle_step(oracle, rp, col, val, w, color):
+    """One step of the workload on the FP64 oracle: the strength build, or
+    for a workload with a checkpoint interval the forward path and its
+    reverse pass (the oracle keeps every iterate)."""
+    if w.get("adjoint"):
+        X0 = oracle.tv_init(len(rp) - 1, w["K"], w["seed"])
+        oracle.adjoint_jacobi(rp, col, val, X0, w["nu"], w["omega"], w["theta"])
+    else:
+        oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
+                     sweep=oracle.SWEEP_MCGS if w["sweep"] == "mcgs" else oracle.SWEEP_JACOBI,
+                     color=color)
+    return len(col) - (len(rp) - 1)
 
 
 def cpu_oracle_time(cfg, w, budget_s=20.0):
@@ -297,10 +358,7 @@ def cpu_oracle_time(cfg, w, budget_s=20.0):
     reps = 0
     while True:
         for rp, col, val in mats:
-            oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
-                         sweep=oracle.SWEEP_MCGS if w["sweep"] == "mcgs" else oracle.SWEEP_JACOBI,
-                         color=color)
-            edges += len(col) - (len(rp) - 1)
+            edges += oracle_step(oracle, rp, col, val, w, color)
         reps += 1
         if time.perf_counter() - t0 > budget_s / 3 or reps >= 3:
             break
@@ -385,15 +443,8 @@ def run_reference(args, cfg, w):
     else:
         mats, color = make_matrix(cfg)
         sample = "full workload per step"
-    sw = oracle.SWEEP_MCGS if w["sweep"] == "mcgs" else oracle.SWEEP_JACOBI
-
     def step():
-        e = 0
-        for rp, col, val in mats:
-            oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
-                         sweep=sw, color=color)
-            e += len(col) - (len(rp) - 1)
-        return e
+        return sum(oracle_step(oracle, rp, col, val, w, color) for rp, col, val in mats)
 
     for _ in range(args.warmup):
         step()
@@ -453,20 +504,30 @@ def main():
     value, ms_per_step = whole_job(float(r["step_ms"].sum()), E, args.steps)
 
     permuted = w["sweep"] == "mcgs"
-    ab = algorithmic_bytes(n, nnz, E, r["E_s"], w["K"], w["nu"], r["ncolors"], precision, permuted)
+    adj = w.get("adjoint")
+    mixed = precision != "fp64"
+
+    def step_bytes(rr, prec):
+        if adj:
+            return adjoint_bytes(n, nnz, w["K"], w["nu"], adj, prec)
+        return algorithmic_bytes(n, nnz, E, rr["E_s"], w["K"], w["nu"], rr["ncolors"], prec,
+                                 permuted)
+
+    ab = step_bytes(r, precision)
     launches_relax = w["nu"] * r["ncolors"]
     relax_launch_ms = r["phase_ms"][1] / launches_relax
     peak, peak_kind = peaks()
     achieved = ab["relax_per_launch"] / (relax_launch_ms * 1e-3) / 1e9
     tkey = "relax/%s/K%d/%s" % (precision, w["K"], cfg)
-    traffic = recorded_traffic(tkey, source_sha("k_relax.cu", "amgd_internal.cuh"))
+    traffic = recorded_traffic(tkey, source_sha("k_relax.cu", "rowops.cuh", "amgd_internal.cuh"))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_relax (one color phase of one sweep)",
                 "peak_source": "%s hbm_gbs" % peak_kind,
                 "algorithmic_bytes_per_launch": ab["relax_per_launch"],
                 "avg_launch_us": relax_launch_ms * 1e3}
-    phases = dict(zip(["init", "relax", "distances", "strength"], r["phase_ms"].tolist()))
+    names = ["init", "relax", "distances", "backward" if adj else "strength"]
+    phases = dict(zip(names, r["phase_ms"].tolist()))
     whole = ab["total"] / (ms_per_step * 1e-3) / 1e9
 
     line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws,
@@ -484,8 +545,21 @@ def main():
             "phase_ms": phases,
             "whole_step_gbs": whole, "whole_step_hbm_frac": whole / peak,
             "roofline": roofline}
+    if adj:
+        line["config"]["checkpoint_every"] = adj
+        line["config"]["step"] = ("vector start, nu recorded sweeps, distances, reverse pass "
+                                  "of sum r^2 over kept edges (dL/dvalues, dL/domega)")
+        line["backward_phase_gbs"] = ab["backward"] / (r["phase_ms"][3] * 1e-3) / 1e9
+        line["scalars"] = {"omega_bar": r["scalars"][0], "loss": r["scalars"][1]}
 
-    launches_per_step = 1 + launches_relax + 1 + 3
+    # kernels of ours per step
+    edge_launches = 2 if mixed else 1                     # + FP64 row fixup on mixed paths
+    if adj:
+        nck = -(-w["nu"] // adj)
+        bwd_launches = 4 + (w["nu"] - nck) + 2 * w["nu"] + 2
+        launches_per_step = 1 + launches_relax + edge_launches + bwd_launches
+    else:
+        launches_per_step = 1 + launches_relax + (1 if permuted else 0) + edge_launches + 3
     line["gpu_launches"] = launches_per_step * args.steps
 
     if not args.no_side and precision != "fp64":
@@ -493,26 +567,26 @@ def main():
         r64 = run_gpu_arm(mats, color, w, "fp64", side_steps, 3, rank, flush, want_clocks=False,
                           tune_cache=args.tune_cache)
         v64, t64 = whole_job(float(r64["step_ms"].sum()), E, side_steps)
-        ab64 = algorithmic_bytes(n, nnz, E, r64["E_s"], w["K"], w["nu"], r64["ncolors"], "fp64",
-                                 permuted)
+        ab64 = step_bytes(r64, "fp64")
         rl = r64["phase_ms"][1] / launches_relax
         a64 = ab64["relax_per_launch"] / (rl * 1e-3) / 1e9
         line["fp64"] = {"value": v64, "unit": "edges/s", "ms_per_step": t64,
                         "steps": side_steps, "shapes": {"relax": list(r64["shapes"][0]),
                                                         "edge": list(r64["shapes"][1])},
-                        "phase_ms": dict(zip(["init", "relax", "distances", "strength"],
-                                             r64["phase_ms"].tolist())),
+                        "phase_ms": dict(zip(names, r64["phase_ms"].tolist())),
                         "relax_launch_us": rl * 1e3, "relax_hbm_gbs": a64,
                         "relax_hbm_frac": a64 / peak,
                         "mixed_over_fp64": value / v64}
         r64["h"].close()
 
     e2e_steps = max(3, min(args.steps, 50))
-    e = run_e2e(r["h"], mats, w, r["sweep"], e2e_steps)
+    e = run_e2e(r["h"], mats, w, r["sweep"], e2e_steps, adjoint=adj)
     v_e2e, _ = whole_job(1e3 * e["seconds"], E, 1)
     line["e2e"] = {"value": v_e2e, "unit": "edges/s", "h2d_bytes_per_step": e["h2d"],
                    "d2h_bytes_per_step": e["d2h"], "steps": e2e_steps,
-                   "api": "amgd_set_values(host) + init + relax + distances + strength(host)"}
+                   "api": ("amgd_set_values(host) + init + relax (recorded) + distances + "
+                           "amgd_backward(host dL/dvalues)") if adj else
+                          "amgd_set_values(host) + init + relax + distances + strength(host)"}
     line["clocks"] = {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} \
         if r["clocks"] else None
     if rank == 0 and not args.no_cpu:

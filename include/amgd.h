@@ -260,6 +260,62 @@ int amgd_enable_phase_timing(amgd_handle h, int enable);
 int amgd_phase_times(amgd_handle h, float *ms);
 
 /*
+ * Reverse pass.  The paper differentiates nothing; these calls give the
+ * gradient of a scalar loss on the LS values with respect to the values of A
+ * and the Jacobi weight omega, by the chain rule through the steps of §3
+ * (Jacobi sweeps on A x = 0), Eqs. (3.2), (4.1) (the LS target) and §4.1,
+ * Eq. (4.3) (the one-point fits; a_ij minimises LS_ij, so the dependence
+ * through a_ij drops out).  The start vectors are treated as constants.
+ *
+ * amgd_set_checkpointing -- every > 0: each later amgd_relax with
+ *   AMGD_SWEEP_JACOBI (on a handle without a coloring) records its
+ *   trajectory: the iterates X_0, X_every, X_2every, ... are kept in device
+ *   memory owned by the handle (ceil(nu/every) blocks of n x Kp storage
+ *   elements); amgd_backward recomputes the iterates between checkpoints
+ *   (every - 1 more blocks).  every = 0 (the default) records nothing.
+ *   Errors: ARG.
+ *
+ * amgd_backward -- reverse pass over the last recorded amgd_relax followed
+ *   by amgd_distances (nothing else that changes the vectors, values,
+ *   weights, target or precision in between).
+ *   ls_bar[nnz] (mem): dL/dLS_p per slot, caller's slot order; entries on
+ *     the diagonal and, for the residual target, in rows with one
+ *     off-diagonal (where LS is the constant 0) are ignored.
+ *     NULL: the loss is L = sum_p r_p^2 = sum_p LS_p^-2 over the slots the
+ *     last amgd_distances kept (flags held fixed) with LS_p > 0.
+ *   val_bar[nnz] (mem, written): dL/da_p for every stored value (a
+ *     diagonal value enters both A and D: both parts are summed).
+ *   omega_bar (host, may be NULL): dL/domega.
+ *   loss (host, may be NULL): L for ls_bar == NULL, NaN otherwise.
+ *   Arithmetic is that of the storage precision (FP64, or FP32 for the
+ *   FP32/BF16 storages); sums have a fixed order (deterministic results).
+ *   Synchronises when mem is AMGD_MEM_HOST or omega_bar / loss is given;
+ *   otherwise it only enqueues work and amgd_backward_scalars fetches the
+ *   two scalars later.
+ *   Errors: ARG, STATE (no recorded trajectory or no distances after it),
+ *   UNSUPPORTED (a coloring is set), CUDA.
+ *
+ * amgd_backward_scalars -- waits for the last reverse pass (eager or graph
+ *   replay) and writes dL/domega and the loss (NaN unless the built-in loss
+ *   was used); either pointer may be NULL.  Errors: ARG, STATE, CUDA.
+ *
+ * amgd_graph_capture_backward -- record one whole forward + reverse step as
+ *   the handle's CUDA graph (replaces any earlier graph; replay with
+ *   amgd_graph_launch): vector start from `seed`, nu recorded Jacobi sweeps
+ *   with weight omega (checkpoint interval as set), distances for theta,
+ *   and the reverse pass of the built-in loss with dL/dval written to the
+ *   DEVICE buffer val_bar[nnz].  Phase timing, when enabled, records the
+ *   boundaries start | vectors | sweeps | distances | reverse pass.
+ *   Errors: ARG, STATE (checkpointing off), UNSUPPORTED (coloring set), CUDA.
+ */
+int amgd_set_checkpointing(amgd_handle h, int32_t every);
+int amgd_backward(amgd_handle h, const double *ls_bar, int mem, double *val_bar,
+                  double *omega_bar, double *loss);
+int amgd_backward_scalars(amgd_handle h, double *omega_bar, double *loss);
+int amgd_graph_capture_backward(amgd_handle h, uint64_t seed, int32_t nu, double omega,
+                                double theta, double *val_bar);
+
+/*
  * amgd_strength_noalloc -- the threshold of Eq. (4.4) and the strength CSR,
  *   computed from distances the caller already holds, without allocating
  *   any memory.  The paper has no counterpart to this entry point: it exists

@@ -75,6 +75,10 @@ SIGNATURES = {
     "amgd_enable_phase_timing": (_int, [_P, _int]),
     "amgd_phase_times": (_int, [_P, _P]),
     "amgd_strength_noalloc": (_int, [_P, _P, _P, _i64, _f64, _P, _P, _i64, _P]),
+    "amgd_set_checkpointing": (_int, [_P, _i32]),
+    "amgd_backward": (_int, [_P, _P, _int, _P, _P, _P]),
+    "amgd_backward_scalars": (_int, [_P, _P, _P]),
+    "amgd_graph_capture_backward": (_int, [_P, _u64, _i32, _f64, _f64, _P]),
     "amgd_destroy": (_int, [_P]),
     "amgd_status_string": (ctypes.c_char_p, [_int]),
     "amgd_last_error": (ctypes.c_char_p, [_P]),
@@ -293,6 +297,39 @@ class Handle:
         cap = s_col.numel() if _is_torch(s_col) else len(s_col)
         self._ck(lib().amgd_strength(self.h, p_rp, p_col, cap, None, mem))
         return s_row_ptr, s_col
+
+    # -- reverse pass ---------------------------------------------------------
+    def set_checkpointing(self, every):
+        self._ck(lib().amgd_set_checkpointing(self.h, every))
+
+    def backward(self, ls_bar=None, out=None):
+        """dL/dval per slot, dL/domega and the built-in loss (ls_bar None) of
+        the last recorded relaxation + distances.  ls_bar and out: numpy
+        arrays (host) or torch tensors (device or host), nnz float64."""
+        if out is None:
+            out = np.empty(self.nnz, dtype=np.float64)
+        p_out, mem = ptr_mem(out)
+        p_in = None
+        if ls_bar is not None:
+            ls_bar = ls_bar if _is_torch(ls_bar) else _host(ls_bar, np.float64)
+            p_in, mem_in = ptr_mem(ls_bar)
+            assert mem_in == mem, "ls_bar and out must live in the same memory"
+        wb, loss = ctypes.c_double(), ctypes.c_double()
+        self._ck(lib().amgd_backward(self.h, p_in, mem, p_out, ctypes.byref(wb),
+                                     ctypes.byref(loss)))
+        return out, wb.value, loss.value
+
+    def backward_scalars(self):
+        """(dL/domega, loss) of the last reverse pass (waits for it)."""
+        wb, loss = ctypes.c_double(), ctypes.c_double()
+        self._ck(lib().amgd_backward_scalars(self.h, ctypes.byref(wb), ctypes.byref(loss)))
+        return wb.value, loss.value
+
+    def graph_capture_backward(self, seed, nu, omega, theta, val_bar):
+        """Capture forward + reverse pass (built-in loss) into the handle's
+        graph; val_bar: device float64 tensor of nnz entries."""
+        self._ck(lib().amgd_graph_capture_backward(self.h, seed, nu, omega, theta,
+                                                   ptr_mem(val_bar)[0]))
 
     def graph_capture(self, seed, nu, omega, sweep, theta, s_row_ptr, s_col):
         cap = s_col.numel() if _is_torch(s_col) else len(s_col)

@@ -69,6 +69,26 @@ struct amgd_ctx {
     cudaGraphExec_t gexec = nullptr;
     int graph_cur_after = 0;
     Shape relax_shape[3], edge_shape[3];         // per storage type
+    // reverse pass: trajectory of the last recorded Jacobi relaxation
+    int32_t ckpt_every = 0;                      // 0: amgd_relax records nothing
+    bool traj_valid = false;
+    int32_t traj_nu = 0;
+    double traj_omega = 0.0;
+    void *ckpt = nullptr;                        // X_0, X_s, X_2s, ... (storage type)
+    size_t ckpt_bytes = 0;
+    void *seg = nullptr;                         // X_{cs+1} .. X_{cs+s-1}, recomputed
+    size_t seg_bytes = 0;
+    void *adj_vec = nullptr;                     // Y, Ybar, Xbar[2]  (arithmetic type)
+    size_t adj_vec_bytes = 0;
+    void *adj_slot = nullptr;                    // gs, gt, at_b     (arithmetic type)
+    size_t adj_slot_bytes = 0;
+    double *lsb = nullptr;                       // dL/dLS per slot
+    double *adj_part = nullptr;                  // 2 x kAdjReduceBlocks partials + 2 sums
+    int32_t *at_rp = nullptr, *at_row = nullptr, *at_slot = nullptr;   // transposed pattern
+    bool last_backward_builtin = false;          // the last reverse pass used the built-in loss
+    bool graph_is_backward = false;              // the captured graph ends with a reverse pass
+    int32_t graph_traj_nu = 0;
+    double graph_traj_omega = 0.0;
     bool phase_timing = false, graph_timed = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     std::string err;
@@ -272,6 +292,7 @@ int run_init(amgd_ctx *h, uint64_t seed, cudaStream_t s)
     a.seed = seed;
     CK(h, launch_init(h->storage, a, s));
     h->have_dist = false;
+    h->traj_valid = false;
     return AMGD_OK;
 }
 
@@ -307,6 +328,72 @@ int run_relax(amgd_ctx *h, int32_t nu, double omega, int sweep, cudaStream_t s)
         h->cur = 1 - h->cur;
     }
     if (nu > 0) h->have_dist = false;
+    h->traj_valid = false;
+    return AMGD_OK;
+}
+
+// grow a device buffer to at least `bytes` (contents not kept)
+cudaError_t ensure_buf(void **p, size_t &have, size_t bytes)
+{
+    if (*p && have >= bytes) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    have = 0;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
+
+// One Jacobi sweep X_dst = X_src - omega D^{-1} A X_src with the handle's
+// relaxation shape (bit-identical to the sweeps of run_relax).
+int jacobi_step(amgd_ctx *h, const void *src, void *dst, double omega, cudaStream_t s)
+{
+    RelaxArgs a;
+    a.status = h->status;
+    a.wait_limit = h->wait_limit;
+    a.extra_tx = h->test_extra_tx;
+    a.rp = h->rp_p;
+    a.col = h->col_p;
+    a.val = h->storage == ST_FP64 ? (const void *)h->val64 : (const void *)h->val32;
+    a.diag = h->storage == ST_FP64 ? (const void *)h->diag64 : (const void *)h->diag32;
+    a.Kp = Kp_of(h->storage, h->K);
+    a.omega = omega;
+    a.xold = src;
+    a.xnew = dst;
+    a.r0 = 0;
+    a.r1 = (int32_t)h->n;
+    a.split = 0;
+    CK(h, launch_relax(h->storage, h->relax_shape[h->storage], a, s));
+    return AMGD_OK;
+}
+
+// Jacobi sweeps that keep the trajectory for amgd_backward: X_0, X_s, X_2s,
+// ... go to checkpoint slots (written by the sweeps themselves), the other
+// iterates ping-pong through the two vector buffers, and X_nu ends where
+// run_relax would leave it.
+int run_relax_recorded(amgd_ctx *h, int32_t nu, double omega, cudaStream_t s)
+{
+    const int32_t S = h->ckpt_every;
+    const size_t xb = (size_t)h->n * Kp_of(h->storage, h->K) * esize(h->storage);
+    const int32_t nck = (nu + S - 1) / S;
+    CK(h, ensure_buf(&h->ckpt, h->ckpt_bytes, (size_t)nck * xb));
+    const int c0 = h->cur;
+    auto loc = [&](int32_t m) -> void * {
+        if (m == 0) return h->x[c0];
+        if (m == nu) return h->x[(c0 + nu) & 1];
+        if (m % S == 0) return (char *)h->ckpt + (size_t)(m / S) * xb;
+        return h->x[(c0 + m) & 1];
+    };
+    if (nck > 0) CK(h, cudaMemcpyAsync(h->ckpt, h->x[c0], xb, cudaMemcpyDeviceToDevice, s));
+    for (int32_t k = 0; k < nu; ++k) {
+        const int rc = jacobi_step(h, loc(k), loc(k + 1), omega, s);
+        if (rc != AMGD_OK) return rc;
+    }
+    h->cur = (c0 + nu) & 1;
+    if (nu > 0) h->have_dist = false;
+    h->traj_valid = true;
+    h->traj_nu = nu;
+    h->traj_omega = omega;
     return AMGD_OK;
 }
 
@@ -577,6 +664,7 @@ int amgd_set_precision(amgd_handle h, int storage)
         if (rc != AMGD_OK) return rc;
     }
     h->have_dist = false;
+    h->traj_valid = false;
     return AMGD_OK;
 }
 
@@ -587,6 +675,7 @@ int amgd_set_target(amgd_handle h, int target)
         return fail(h, AMGD_ERR_ARG, "unknown target");
     h->target = target;
     h->have_dist = false;
+    h->traj_valid = false;
     return AMGD_OK;
 }
 
@@ -602,6 +691,7 @@ int amgd_set_weights(amgd_handle h, const double *w)
     }
     h->h_w = nw;
     h->have_dist = false;
+    h->traj_valid = false;
     return upload_weights(h);
 }
 
@@ -659,6 +749,7 @@ int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int 
     CK(h, cudaStreamSynchronize(h->stream));
     h->color_start = start;
     h->have_dist = false;
+    h->traj_valid = false;
     return AMGD_OK;
 }
 
@@ -685,6 +776,7 @@ int amgd_set_vectors(amgd_handle h, const double *X, int mem)
                         Kp_of(h->storage, h->K), h->stream));
     if (mem == AMGD_MEM_HOST) CK(h, cudaStreamSynchronize(h->stream));
     h->have_dist = false;
+    h->traj_valid = false;
     return AMGD_OK;
 }
 
@@ -732,6 +824,7 @@ int amgd_set_values(amgd_handle h, const double *val, int mem)
     int rc = permute_values(h);
     if (rc != AMGD_OK) return rc;
     h->have_dist = false;
+    h->traj_valid = false;
     return AMGD_OK;
 }
 
@@ -743,6 +836,8 @@ int amgd_relax(amgd_handle h, int32_t nu, double omega, int sweep_type)
         return fail(h, AMGD_ERR_ARG, "unknown sweep type");
     if (sweep_type == AMGD_SWEEP_MCGS && !h->perm)
         return fail(h, AMGD_ERR_STATE, "MCGS needs amgd_set_coloring first");
+    if (h->ckpt_every > 0 && sweep_type == AMGD_SWEEP_JACOBI && !h->perm)
+        return run_relax_recorded(h, nu, omega, h->stream);
     return run_relax(h, nu, omega, sweep_type, h->stream);
 }
 
@@ -853,11 +948,13 @@ int amgd_graph_capture(amgd_handle h, uint64_t seed, int32_t nu, double omega, i
     h->graph_cur_after = h->cur;
     h->cur = cur0;
     h->have_dist = false;
+    h->traj_valid = false;
     if (rc != AMGD_OK) { if (g) cudaGraphDestroy(g); return rc; }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
     h->graph = g;
     CK(h, cudaGraphInstantiate(&h->gexec, h->graph, 0));
     h->graph_timed = timed;
+    h->graph_is_backward = false;
     return AMGD_OK;
 }
 
@@ -1007,6 +1104,7 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
     h->edge_shape[h->storage] = best_e;
     h->cur = cur;
     h->have_dist = false;
+    h->traj_valid = false;
     if (cache_path) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
@@ -1042,6 +1140,268 @@ int amgd_graph_launch(amgd_handle h)
     CK(h, cudaGraphLaunch(h->gexec, h->stream));
     h->cur = h->graph_cur_after;
     h->have_dist = true;
+    if (h->graph_is_backward) {
+        h->traj_valid = true;
+        h->traj_nu = h->graph_traj_nu;
+        h->traj_omega = h->graph_traj_omega;
+    }
+    return AMGD_OK;
+}
+
+int amgd_set_checkpointing(amgd_handle h, int32_t every)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (every < 0) return fail(h, AMGD_ERR_ARG, "checkpoint interval < 0");
+    h->ckpt_every = every;
+    if (every == 0) h->traj_valid = false;
+    return AMGD_OK;
+}
+
+namespace {
+
+// transposed pattern of A (host counting sort, entries of a column in
+// ascending row order), built once per handle
+int ensure_transpose(amgd_ctx *h)
+{
+    if (h->at_rp) return AMGD_OK;
+    const int64_t n = h->n, nnz = h->nnz;
+    std::vector<int32_t> trp((size_t)n + 1, 0), trow((size_t)nnz), tslot((size_t)nnz);
+    for (int64_t p = 0; p < nnz; ++p) ++trp[(size_t)h->h_col[(size_t)p] + 1];
+    for (int64_t j = 0; j < n; ++j) trp[(size_t)j + 1] += trp[(size_t)j];
+    std::vector<int32_t> next(trp.begin(), trp.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t p = h->h_rp[(size_t)i]; p < h->h_rp[(size_t)i + 1]; ++p) {
+            const int32_t q = next[(size_t)h->h_col[(size_t)p]]++;
+            trow[(size_t)q] = (int32_t)i;
+            tslot[(size_t)q] = p;
+        }
+    CK(h, dalloc(&h->at_rp, (size_t)n + 1));
+    CK(h, dalloc(&h->at_row, (size_t)(nnz ? nnz : 1)));
+    CK(h, dalloc(&h->at_slot, (size_t)(nnz ? nnz : 1)));
+    CK(h, cudaMemcpy(h->at_rp, trp.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (nnz) {
+        CK(h, cudaMemcpy(h->at_row, trow.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->at_slot, tslot.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    return AMGD_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// device buffers of the reverse pass (allocated before any capture)
+int prepare_backward(amgd_ctx *h)
+{
+    const size_t cs = h->storage == ST_FP64 ? 8 : 4;
+    const size_t nk = (size_t)h->n * Kp_of(h->storage, h->K);
+    const size_t xb = nk * esize(h->storage);
+    const int32_t S = h->ckpt_every > 0 ? h->ckpt_every : 1;
+    int rc = ensure_transpose(h);
+    if (rc != AMGD_OK) return rc;
+    CK(h, ensure_buf(&h->adj_vec, h->adj_vec_bytes, 4 * nk * cs));
+    CK(h, ensure_buf(&h->adj_slot, h->adj_slot_bytes, 3 * (size_t)(h->nnz ? h->nnz : 1) * cs));
+    CK(h, ensure_buf(&h->seg, h->seg_bytes, (size_t)(S - 1) * xb));
+    if (!h->lsb) CK(h, dalloc(&h->lsb, (size_t)(h->nnz ? h->nnz : 1)));
+    if (!h->adj_part) CK(h, dalloc(&h->adj_part, (size_t)2 * kAdjReduceBlocks + 2));
+    CK(h, ensure_tmp64(h, (size_t)h->nnz));
+    return AMGD_OK;
+}
+
+// Enqueue the whole reverse pass on stream s (nothing synchronises).
+// lsb_in: device dL/dLS or NULL (built-in loss); vb: device dL/dval.
+// The two sums (loss, dL/domega) land in adj_part[2 nb], adj_part[2 nb + 1].
+int run_backward(amgd_ctx *h, const double *lsb_in, double *vb, cudaStream_t s)
+{
+    const int st = h->storage;
+    const int32_t n = (int32_t)h->n;
+    const int64_t nnz = h->nnz;
+    const int Kp = Kp_of(st, h->K);
+    const size_t cs = st == ST_FP64 ? 8 : 4;
+    const size_t nk = (size_t)n * Kp;
+    const size_t xb = nk * esize(st);
+    const int32_t S = h->ckpt_every > 0 ? h->ckpt_every : 1;
+    const int32_t nu = h->traj_nu;
+    const int nb = kAdjReduceBlocks;
+    char *vecs = (char *)h->adj_vec;
+    void *Y = vecs, *Ybar = vecs + nk * cs;
+    void *Xbar[2] = {vecs + 2 * nk * cs, vecs + 3 * nk * cs};
+    char *slots = (char *)h->adj_slot;
+    void *gs = slots, *gt = slots + nnz * cs, *at_b = slots + 2 * nnz * cs;
+
+    CK(h, launch_adj_upstream(st, h->rp_o, h->col_o, h->ls, h->flag, lsb_in, h->lsb, h->adj_part,
+                              nb, n, h->target, s));
+    CK(h, launch_adj_bvals(st, h->val_o, h->diag64_o, h->at_row, h->at_slot, at_b, nnz, s));
+
+    AdjArgs a;
+    a.rp = h->rp_o;
+    a.col = h->col_o;
+    a.val = st == ST_FP64 ? (const void *)h->val_o : (const void *)h->val32_o;
+    a.diag = st == ST_FP64 ? (const void *)h->diag64_o : (const void *)h->diag32_o;
+    a.at_rp = h->at_rp;
+    a.at_row = h->at_row;
+    a.at_slot = h->at_slot;
+    a.at_b = at_b;
+    a.x = h->x[h->cur];
+    a.w = st == ST_FP64 ? (const void *)h->w64 : (const void *)h->w32;
+    a.a = h->a;
+    a.lsb = h->lsb;
+    a.y = Y;
+    a.ybar = Ybar;
+    a.xbar_in = nullptr;
+    a.xbar_out = Xbar[0];
+    a.gs = gs;
+    a.gt = gt;
+    a.n = n;
+    a.Kp = Kp;
+    a.target = h->target;
+    a.first = 1;
+    a.omega = h->traj_omega;
+    CK(h, launch_adj_edge(st, a, s));
+    CK(h, launch_adj_xbar_nu(st, a, s));
+
+    // sweeps, last to first, one checkpoint segment at a time: the iterates
+    // between two checkpoints are recomputed by the forward kernel
+    int xc = 0;
+    const int32_t nseg = (nu + S - 1) / S;
+    for (int32_t c = nseg - 1; c >= 0; --c) {
+        const int32_t k0 = c * S, k1 = std::min(k0 + S, nu);
+        void *base = (char *)h->ckpt + (size_t)c * xb;
+        auto iterate = [&](int32_t k) -> void * {
+            return k == k0 ? base : (char *)h->seg + (size_t)(k - k0 - 1) * xb;
+        };
+        for (int32_t k = k0; k + 1 < k1; ++k) {
+            const int rc = jacobi_step(h, iterate(k), iterate(k + 1), h->traj_omega, s);
+            if (rc != AMGD_OK) return rc;
+        }
+        for (int32_t k = k1 - 1; k >= k0; --k) {
+            a.x = iterate(k);
+            a.xbar_in = Xbar[xc];
+            a.xbar_out = Xbar[1 - xc];
+            a.first = k == nu - 1;
+            CK(h, launch_adj_gram(st, a, s));
+            CK(h, launch_adj_spmm_t(st, a, s));
+            xc = 1 - xc;
+        }
+    }
+    CK(h, launch_adj_finish(st, a, nu > 0, h->val_o, h->diag64_o, h->diag_slot, vb,
+                            h->adj_part + nb, nb, s));
+    CK(h, launch_adj_reduce(h->adj_part, nb, 2, h->adj_part + 2 * nb, s));
+    return AMGD_OK;
+}
+
+int backward_checks(amgd_ctx *h)
+{
+    if (h->perm)
+        return fail(h, AMGD_ERR_UNSUPPORTED, "the reverse pass covers Jacobi sweeps without a coloring");
+    if (!h->traj_valid)
+        return fail(h, AMGD_ERR_STATE, "no recorded trajectory: amgd_set_checkpointing, then a Jacobi amgd_relax");
+    if (!h->have_dist) return fail(h, AMGD_ERR_STATE, "amgd_distances must run after amgd_relax");
+    return AMGD_OK;
+}
+
+}  // namespace
+
+int amgd_backward(amgd_handle h, const double *ls_bar, int mem, double *val_bar,
+                  double *omega_bar, double *loss)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
+    if (!val_bar && h->nnz) return fail(h, AMGD_ERR_ARG, "val_bar is NULL");
+    int rc = backward_checks(h);
+    if (rc != AMGD_OK) return rc;
+    if ((rc = prepare_backward(h)) != AMGD_OK) return rc;
+    cudaStream_t s = h->stream;
+    const int64_t nnz = h->nnz;
+    const double *lsb_in = ls_bar;
+    double *vb = val_bar;
+    if (mem == AMGD_MEM_HOST) {
+        // one staging buffer serves both: dL/dLS is consumed by the first
+        // kernel, dL/dval written by the last
+        if (ls_bar)
+            CK(h, cudaMemcpyAsync(h->tmp64, ls_bar, nnz * sizeof(double), cudaMemcpyHostToDevice, s));
+        lsb_in = ls_bar ? h->tmp64 : nullptr;
+        vb = h->tmp64;
+    }
+    if ((rc = run_backward(h, lsb_in, vb, s)) != AMGD_OK) return rc;
+    if (mem == AMGD_MEM_HOST && nnz)
+        CK(h, cudaMemcpyAsync(val_bar, vb, nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+    h->last_backward_builtin = ls_bar == nullptr;
+    if (omega_bar || loss || mem == AMGD_MEM_HOST) return amgd_backward_scalars(h, omega_bar, loss);
+    return AMGD_OK;
+}
+
+int amgd_backward_scalars(amgd_handle h, double *omega_bar, double *loss)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (!h->adj_part) return fail(h, AMGD_ERR_STATE, "no reverse pass has run");
+    double sums[2] = {0.0, 0.0};
+    CK(h, cudaMemcpyAsync(sums, h->adj_part + 2 * kAdjReduceBlocks, 2 * sizeof(double),
+                          cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (loss) *loss = h->last_backward_builtin ? sums[0] : NAN;
+    if (omega_bar) *omega_bar = sums[1];
+    return poll_status(h);
+}
+
+int amgd_graph_capture_backward(amgd_handle h, uint64_t seed, int32_t nu, double omega,
+                                double theta, double *val_bar)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (nu < 0 || !std::isfinite(omega)) return fail(h, AMGD_ERR_ARG, "nu < 0 or omega not finite");
+    if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(h, AMGD_ERR_ARG, "theta must be finite and >= 0");
+    if (!val_bar && h->nnz) return fail(h, AMGD_ERR_ARG, "val_bar is NULL");
+    if (h->perm)
+        return fail(h, AMGD_ERR_UNSUPPORTED, "the reverse pass covers Jacobi sweeps without a coloring");
+    if (h->ckpt_every <= 0) return fail(h, AMGD_ERR_STATE, "amgd_set_checkpointing must come first");
+    // every buffer the captured work touches exists before the capture
+    {
+        const size_t xb = (size_t)h->n * Kp_of(h->storage, h->K) * esize(h->storage);
+        const int32_t nck = (nu + h->ckpt_every - 1) / h->ckpt_every;
+        CK(h, ensure_buf(&h->ckpt, h->ckpt_bytes, (size_t)nck * xb));
+        const int rc = prepare_backward(h);
+        if (rc != AMGD_OK) return rc;
+    }
+    if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    CK(h, cudaStreamSynchronize(h->stream));
+    const int cur0 = h->cur;
+    h->cur = 0;
+    if (h->phase_timing && !h->ev[0])
+        for (auto &e : h->ev) CK(h, cudaEventCreate(&e));
+    const bool timed = h->phase_timing;
+    auto mark = [&](int k) {
+        return timed ? cudaEventRecordWithFlags(h->ev[k], h->cap_stream, cudaEventRecordExternal)
+                     : cudaSuccess;
+    };
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = AMGD_OK;
+    cudaError_t me = mark(0);
+    if (me == cudaSuccess) rc = run_init(h, seed, h->cap_stream);
+    if (me == cudaSuccess && rc == AMGD_OK) me = mark(1);
+    if (me == cudaSuccess && rc == AMGD_OK) rc = run_relax_recorded(h, nu, omega, h->cap_stream);
+    if (me == cudaSuccess && rc == AMGD_OK) me = mark(2);
+    if (me == cudaSuccess && rc == AMGD_OK) rc = run_edge(h, theta, h->cap_stream);
+    if (me == cudaSuccess && rc == AMGD_OK) me = mark(3);
+    if (me == cudaSuccess && rc == AMGD_OK) rc = run_backward(h, nullptr, val_bar, h->cap_stream);
+    if (me == cudaSuccess && rc == AMGD_OK) me = mark(4);
+    if (me != cudaSuccess && rc == AMGD_OK) rc = cuda_fail(h, me, "cudaEventRecordWithFlags (capture)");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    h->graph_cur_after = h->cur;
+    h->cur = cur0;
+    h->have_dist = false;
+    h->traj_valid = false;
+    if (rc != AMGD_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    h->graph = g;
+    CK(h, cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    h->graph_timed = timed;
+    h->graph_is_backward = true;
+    h->graph_traj_nu = nu;
+    h->graph_traj_omega = omega;
+    h->last_backward_builtin = true;
     return AMGD_OK;
 }
 
@@ -1065,7 +1425,8 @@ int amgd_destroy(amgd_handle h)
                     h->defer_count, h->defer_list,
                     h->val32, h->x[0], h->x[1],
                     h->w64, h->w32, h->a, h->ls, h->flag, h->count, h->tile, h->s_rp_tmp,
-                    h->s_col_tmp, h->tmp64};
+                    h->s_col_tmp, h->tmp64, h->ckpt, h->seg, h->adj_vec, h->adj_slot, h->lsb,
+                    h->adj_part, h->at_rp, h->at_row, h->at_slot};
     for (void *p : ptrs) dfree(p);
     delete h;
     return AMGD_OK;

@@ -206,6 +206,57 @@ cudaError_t launch_strength(const int32_t *count, const int32_t *rp_orig, const 
                             const uint8_t *flag, int32_t n, int32_t *tile_sum,
                             int64_t *s_row_ptr, int32_t *s_col, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// reverse pass (Jacobi sweeps); every array in the caller's numbering, vector
+// blocks n x Kp row-major, "C" = arithmetic type of the storage (double for
+// FP64 storage, float otherwise)
+// ---------------------------------------------------------------------------
+struct AdjArgs {
+    const int32_t *rp, *col;          // CSR pattern of A
+    const void *val, *diag;           // values and diagonal, C
+    const int32_t *at_rp;             // transpose: column j owns entries [at_rp[j], at_rp[j+1])
+    const int32_t *at_row, *at_slot;  // row i and slot p of each entry (rows ascending)
+    const void *at_b;                 // b_q = a(i,j) / a_ii per entry, C
+    const void *x;                    // storage type: X_nu (edge stages) or X_k (sweeps)
+    const void *w;                    // LS weights, Kp, C
+    const void *a;                    // forward fit coefficients per slot, C
+    const double *lsb;                // dL/dLS per slot (0 where no gradient flows)
+    void *y, *ybar;                   // target Y and its adjoint, C
+    const void *xbar_in;              // C
+    void *xbar_out;                   // C
+    void *gs, *gt;                    // per-slot sums <Xbar_{k+1,i}, X_k,j> (sweeps) and
+                                      // <Ybar_i, X_nu,j> (target), C
+    int32_t n, Kp, target, first;
+    double omega;
+};
+
+// dL/dLS per slot from an upstream gradient (ls_bar) or the built-in loss
+// sum r^2 = LS^-2 over kept slots with LS > 0; per-block loss partials
+cudaError_t launch_adj_upstream(int storage, const int32_t *rp, const int32_t *col,
+                                const void *ls, const uint8_t *flag, const double *ls_bar,
+                                double *lsb, double *partial, int32_t nblocks, int32_t n,
+                                int32_t target, cudaStream_t s);
+// b_q = val[at_slot[q]] / a_ii, i = at_row[q], for every transposed entry (C)
+cudaError_t launch_adj_bvals(int storage, const double *val64, const double *diag64,
+                             const int32_t *at_row, const int32_t *at_slot, void *at_b,
+                             int64_t nnz, cudaStream_t s);
+// Y, Ybar and (residual target) gt from the fits
+cudaError_t launch_adj_edge(int storage, const AdjArgs &a, cudaStream_t s);
+// Xbar_nu = direct part of the fits + the target's adjoint, per column
+cudaError_t launch_adj_xbar_nu(int storage, const AdjArgs &a, cudaStream_t s);
+// gs (+)= <Xbar_{k+1,i}, X_k,col_p>
+cudaError_t launch_adj_gram(int storage, const AdjArgs &a, cudaStream_t s);
+// Xbar_k = Xbar_{k+1} - omega (D^{-1} A)^T Xbar_{k+1}
+cudaError_t launch_adj_spmm_t(int storage, const AdjArgs &a, cudaStream_t s);
+// dL/dval (FP64, caller slots) from gs, gt; per-block partials of dL/domega
+cudaError_t launch_adj_finish(int storage, const AdjArgs &a, bool have_gs, const double *val64,
+                              const double *diag64, const int32_t *diag_slot, double *val_bar,
+                              double *partial, int32_t nblocks, cudaStream_t s);
+// out[c] = sum of partial[c * nblocks .. (c+1) * nblocks) in a fixed order, c < nsums
+cudaError_t launch_adj_reduce(const double *partial, int32_t nblocks, int32_t nsums, double *out,
+                              cudaStream_t s);
+constexpr int kAdjReduceBlocks = 608;   // 4 per SM
+
 // message returned by amgd_last_error(NULL) on the calling host thread
 void set_thread_error(const std::string &msg);
 
