@@ -476,6 +476,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-side", action="store_true", help="skip the FP64 side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--scale", type=int, default=None,
+                    help="shrink the workload for profiling captures (grid side; for the "
+                         "graph batch: the first SCALE matrices); never for reported numbers")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file (a matching entry skips the tuning launches)")
     args = ap.parse_args()
@@ -493,7 +496,7 @@ def main():
     from paper_1106_5990_gb300 import amgd
     amgd.lib()
     precision = args.precision or w["precision"]
-    mats, color = make_matrix(cfg)
+    mats, color = make_matrix(cfg, scale=args.scale)
     n = sum(len(m[0]) - 1 for m in mats)
     nnz = sum(len(m[1]) for m in mats)
     E = nnz - n
@@ -545,6 +548,9 @@ def main():
             "phase_ms": phases,
             "whole_step_gbs": whole, "whole_step_hbm_frac": whole / peak,
             "roofline": roofline}
+    if args.scale:
+        line["config"]["scale"] = args.scale
+        line["config"]["workload"] += " -- SHRUNK by --scale for profiling, not the workload"
     if adj:
         line["config"]["checkpoint_every"] = adj
         line["config"]["step"] = ("vector start, nu recorded sweeps, distances, reverse pass "

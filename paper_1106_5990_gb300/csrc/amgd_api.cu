@@ -85,6 +85,8 @@ struct amgd_ctx {
     double *lsb = nullptr;                       // dL/dLS per slot
     double *adj_part = nullptr;                  // 2 x kAdjReduceBlocks partials + 2 sums
     int32_t *at_rp = nullptr, *at_row = nullptr, *at_slot = nullptr;   // transposed pattern
+    int32_t *edge_tiles = nullptr;               // row tiles of the edge pass
+    int32_t n_edge_tiles = 0;
     bool last_backward_builtin = false;          // the last reverse pass used the built-in loss
     bool graph_is_backward = false;              // the captured graph ends with a reverse pass
     int32_t graph_traj_nu = 0;
@@ -423,6 +425,8 @@ int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
     a.count_out = h->count;
     a.defer_count = h->defer_count;
     a.defer_list = h->defer_list;
+    a.tiles = h->edge_tiles;
+    a.ntiles = h->n_edge_tiles;
     a.n = (int32_t)h->n;
     a.Kp = Kp_of(h->storage, h->K);
     a.target = h->target;
@@ -543,6 +547,24 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
     if (const char *e = getenv("AMGD_TEST_STAGING_EXTRA_TX")) h->test_extra_tx = (uint32_t)atoi(e);
     if (const char *e = getenv("AMGD_TEST_WAIT_LIMIT")) h->wait_limit = atoll(e);
     if (n) TRY(cudaMemcpy(h->diag_slot, h->h_diag_slot.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    {
+        // row tiles of the edge pass (caller order)
+        std::vector<int32_t> tiles(1, 0);
+        int64_t rows = 0, slots = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t len = h->h_rp[(size_t)i + 1] - h->h_rp[(size_t)i];
+            if (rows > 0 && (rows == kEdgeTileRows || slots + len > kEdgeTileSlots)) {
+                tiles.push_back((int32_t)i);
+                rows = slots = 0;
+            }
+            ++rows;
+            slots += len;
+        }
+        if (n > 0) tiles.push_back((int32_t)n);
+        h->n_edge_tiles = (int32_t)tiles.size() - 1;
+        TRY(dalloc(&h->edge_tiles, tiles.size()));
+        TRY(cudaMemcpy(h->edge_tiles, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     h->rp_p = h->rp_o;
     h->col_p = h->col_o;
     h->val64 = h->val_o;
@@ -963,7 +985,7 @@ int amgd_set_kernel_shape(amgd_handle h, int kernel, int G, int NV, int U, int s
     if (!h) return AMGD_ERR_ARG;
     const Shape sh{G, NV, U, staged};
     if ((kernel != AMGD_KERNEL_RELAX && kernel != AMGD_KERNEL_EDGE) || !shape_ok(h->storage, h->K, sh) ||
-        (kernel == AMGD_KERNEL_EDGE && staged) ||
+        (kernel == AMGD_KERNEL_EDGE && staged > 1) ||
         (kernel == AMGD_KERNEL_RELAX && !relax_shape_available(h->storage, sh)))
         return fail(h, AMGD_ERR_ARG, "invalid kernel shape for this storage and K");
     (kernel == AMGD_KERNEL_RELAX ? h->relax_shape : h->edge_shape)[h->storage] = sh;
@@ -1094,12 +1116,19 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
             const int prc = poll_status(h);
             if (prc != AMGD_OK) { h->relax_shape[h->storage] = keep_r; return prc; }
         }
-        if (c.stage) continue;               // the edge pass has no staged variant
-        h->edge_shape[h->storage] = c;
-        rc = time_ms(h, [&]() { return run_edge(h, 0.5, h->stream); }, 5, ms);
-        if (rc != AMGD_OK) { h->edge_shape[h->storage] = keep_e; return rc; }
-        if (ms < te) { te = ms; best_e = c; }
     }
+    // edge pass: stage 0 row kernel, stage 1 tile kernel
+    for (int stage : {0, 1})
+        for (int NV : {1, 2, 4})
+            for (int U : {4, 8}) {
+                const Shape c{P / NV, NV, U, stage};
+                if (P % NV != 0 || !shape_ok(h->storage, h->K, c)) continue;
+                float ms = 0.f;
+                h->edge_shape[h->storage] = c;
+                const int rc = time_ms(h, [&]() { return run_edge(h, 0.5, h->stream); }, 5, ms);
+                if (rc != AMGD_OK) { h->edge_shape[h->storage] = keep_e; return rc; }
+                if (ms < te) { te = ms; best_e = c; }
+            }
     h->relax_shape[h->storage] = best_r;
     h->edge_shape[h->storage] = best_e;
     h->cur = cur;
@@ -1426,7 +1455,7 @@ int amgd_destroy(amgd_handle h)
                     h->val32, h->x[0], h->x[1],
                     h->w64, h->w32, h->a, h->ls, h->flag, h->count, h->tile, h->s_rp_tmp,
                     h->s_col_tmp, h->tmp64, h->ckpt, h->seg, h->adj_vec, h->adj_slot, h->lsb,
-                    h->adj_part, h->at_rp, h->at_row, h->at_slot};
+                    h->adj_part, h->at_rp, h->at_row, h->at_slot, h->edge_tiles};
     for (void *p : ptrs) dfree(p);
     delete h;
     return AMGD_OK;

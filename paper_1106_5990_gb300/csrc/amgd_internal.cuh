@@ -45,6 +45,10 @@ template <> struct Store<double> {
     __device__ __forceinline__ static void store(double *p, const C (&x)[V]) {
         *reinterpret_cast<double2 *>(p) = make_double2(x[0], x[1]);
     }
+    __device__ __forceinline__ static uint4 pack(const C (&x)[V]) {
+        return make_uint4((uint32_t)__double2loint(x[0]), (uint32_t)__double2hiint(x[0]),
+                          (uint32_t)__double2loint(x[1]), (uint32_t)__double2hiint(x[1]));
+    }
 };
 
 template <> struct Store<float> {
@@ -66,6 +70,10 @@ template <> struct Store<float> {
     }
     __device__ __forceinline__ static void store(float *p, const C (&x)[V]) {
         *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+    __device__ __forceinline__ static uint4 pack(const C (&x)[V]) {
+        return make_uint4(__float_as_uint(x[0]), __float_as_uint(x[1]), __float_as_uint(x[2]),
+                          __float_as_uint(x[3]));
     }
 };
 
@@ -92,13 +100,16 @@ template <> struct Store<__nv_bfloat16> {
         }
     }
     __device__ __forceinline__ static void store(__nv_bfloat16 *p, const C (&x)[V]) {
+        *reinterpret_cast<uint4 *>(p) = pack(x);
+    }
+    __device__ __forceinline__ static uint4 pack(const C (&x)[V]) {
         uint32_t w[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * k], x[2 * k + 1]);
             w[k] = (uint32_t)__bfloat16_as_ushort(h.x) | ((uint32_t)__bfloat16_as_ushort(h.y) << 16);
         }
-        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+        return make_uint4(w[0], w[1], w[2], w[3]);
     }
 };
 
@@ -151,9 +162,17 @@ struct EdgeArgs {                // everything in the caller's numbering
     int32_t *count_out;          // per row
     uint32_t *defer_count;       // rows appended to defer_list (mixed paths)
     int32_t *defer_list;         // rows to redo in FP64 (capacity n)
+    const int32_t *tiles;        // ntiles + 1 first rows of the row tiles
+    int32_t ntiles;
     int32_t n, Kp, target;       // target: 0 residual, 1 plain
     double theta;
 };
+
+// row tiles of the edge pass: consecutive rows, at most kEdgeTileRows rows and
+// kEdgeTileSlots stored entries per tile (a row with more entries is a tile
+// of its own)
+constexpr int kEdgeTileRows = 256;
+constexpr int kEdgeTileSlots = 4096;
 
 struct InitArgs {
     void *x;                   // n x Kp, permuted rows

@@ -1,28 +1,31 @@
-// k_edge.cuh -- fused per-row pass: LS target, one-point least-squares fit
-// for every stored off-diagonal, row-relative threshold and strength flags.
+// k_edge.cuh -- fused pass over the stored entries: LS target, one-point
+// least-squares fit for every stored off-diagonal, row-relative threshold
+// and strength flags.
 //
-// For row i (G lanes, NV vectors of V components per lane, as in k_relax.cu):
+// For row i and its stored entries p = (i, j):
 //   1. y_i = x_i - (1/a_ii) sum_p a(i,col_p) x(col_p)     (Eqs. (3.2), (4.1):
 //      the residual-corrected target, one local Jacobi step; same rounding
 //      as the relaxation sweep with omega = 1), or y_i = x_i (Eq. (3.1)).
-//   2. for every off-diagonal slot p = (i,j) (§4.1, Eq. (4.3)):
-//        S_xx = sum_k w_k x_jk^2, S_yx = sum_k w_k y_ik x_jk   (lane partial
-//        sums, then an xor-shuffle reduction inside the G lanes)
+//   2. for every off-diagonal (§4.1, Eq. (4.3)):
+//        S_xx = sum_k w_k x_jk^2, S_yx = sum_k w_k y_ik x_jk
 //        a_ij = S_yx / S_xx (0 if S_xx = 0)
 //        LS_ij = sum_k w_k (y_ik - a_ij x_jk)^2   (second pass over the K
 //        components, each residual one fused multiply-add: no cancellation
 //        of S_yy - a S_yx; an error in a_ij enters LS only to second order)
 //      A residual-target row with one off-diagonal has y_i proportional to
 //      x_j exactly: a = -a_ij/a_ii, LS = 0.
-//      Mixed precisions (FP32 arithmetic on FP32/BF16 vectors): an edge with
-//      LS < 1e-4 S_yy is recomputed in FP64, with y_i rebuilt from the FP64
-//      values of A, so cancellation never decides a distance.
+//      Mixed precisions (FP32 arithmetic on FP32/BF16 vectors): a row with
+//      an edge of LS < 1e-4 S_yy is recomputed in FP64 (k_edge_fixup), with
+//      y_i rebuilt from the FP64 values of A, so cancellation never decides
+//      a distance.
 //   3. m_i = min_p LS_ip; slot p is strong iff LS_p = 0 or theta LS_p < m_i
 //      (§4.2, Eq. (4.4), r = 1/LS); per-row strong count.
 // The pass runs on the caller's numbering (a row-permuted vector block is
-// copied back first), so every output lands where the caller expects it and
-// a warp's outputs form one contiguous run.  Neighbour rows are gathered U
-// at a time with all loads in flight, as in k_relax.cu.
+// copied back first), so every output lands where the caller expects it.
+// Two kernels compute the same thing (the edge shape's stage selects one;
+// the autotuner times both): k_edge_rows, G lanes per row through all
+// steps; k_edge_tiles, rows cut into tiles with one thread per stored entry
+// for the fits.
 #pragma once
 #include <type_traits>
 
@@ -106,6 +109,11 @@ __device__ __forceinline__ void residual_add(C a, const C (&x)[V], const C (&y)[
     }
 }
 
+// ---------------------------------------------------------------------------
+// Row kernel (edge shape stage 0).  G lanes own one row through all three
+// steps: the target from the row's gathers, then the fits with the row's
+// neighbours gathered again (mostly L1/L2 hits), K-component sums reduced
+// across the G lanes with shuffles, then the flags.
 // Per-warp output staging: a warp owns 32/G consecutive rows of the caller's
 // numbering, i.e. one contiguous run of CSR slots.  a, LS and the flags of
 // that run are collected in shared memory and written out with coalesced
@@ -134,7 +142,7 @@ constexpr int edge_smem_bytes()
 #endif
 
 template <class TS, int G, int NV, int U, bool UW>
-__global__ void AMGD_EDGE_BOUNDS k_edge(EdgeArgs A)
+__global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
 {
     using S = Store<TS>;
     using C = typename S::C;
@@ -232,19 +240,25 @@ __global__ void AMGD_EDGE_BOUNDS k_edge(EdgeArgs A)
                     a_ = -(C)__ldg(val + p) / diag;
                     ls_ = C(0);
                 } else {
-                    C xj[NV][V];
+                    // x_j is unpacked from the gathered bits once per use, so only one
+                    // 16-byte piece of it is live in registers at a time
                     PieceSums<C, V, UW> ps;
 #pragma unroll
                     for (int t = 0; t < NV; ++t) {
-                        S::unpack(raw[u][t], xj[t]);
-                        ps.add(xj[t], y[t], w[t]);
+                        C xj[V];
+                        S::unpack(raw[u][t], xj);
+                        ps.add(xj, y[t], w[t]);
                     }
                     const C sxx = group_sum<G>(ps.sxx(), gmask);
                     const C syx = group_sum<G>(ps.syx(), gmask);
                     a_ = (sxx == C(0)) ? C(0) : divide(syx, sxx);
                     C res = C(0);
 #pragma unroll
-                    for (int t = 0; t < NV; ++t) residual_add<C, V, UW>(a_, xj[t], y[t], w[t], res);
+                    for (int t = 0; t < NV; ++t) {
+                        C xj[V];
+                        S::unpack(raw[u][t], xj);
+                        residual_add<C, V, UW>(a_, xj, y[t], w[t], res);
+                    }
                     ls_ = group_sum<G>(res, gmask);
                     if constexpr (kMixed) defer = defer || ls_ < C(1e-4) * syy;
                 }
@@ -283,6 +297,209 @@ __global__ void AMGD_EDGE_BOUNDS k_edge(EdgeArgs A)
             ls_out[wbase + q] = ls_s[q];
             A.flag_out[wbase + q] = fl_s[q];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile kernel (edge shape stage 1).  A block owns one tile of consecutive caller rows (at most
+// kEdgeTileRows rows and kEdgeTileSlots stored entries; a longer row is a
+// tile of its own), i.e. one contiguous run of CSR slots:
+//   A. targets: G lanes per row form y_i (the same row sums and rounding as
+//      the sweeps) into shared memory, plus S_yy per row on the mixed paths;
+//   B. fits: one thread per stored entry gathers x_j once, reads y_i from
+//      shared memory and forms S_xx, S_yx, a_ij and the residual sum LS_ij
+//      over all K components itself -- no cross-lane reductions, whole-warp
+//      use for the per-edge scalar work, coalesced a/LS writes; the row
+//      minimum of LS is an atomic minimum on the (non-negative) bit patterns
+//      in shared memory, which is order independent;
+//   C. flags and per-row counts from the row minima.
+// ---------------------------------------------------------------------------
+template <class C> struct MinBits;
+template <> struct MinBits<float> {
+    using T = unsigned int;
+    static constexpr T kInf = 0x7f800000u;
+    __device__ __forceinline__ static T bits(float v) { return __float_as_uint(v); }
+    __device__ __forceinline__ static float value(T b) { return __uint_as_float(b); }
+};
+template <> struct MinBits<double> {
+    using T = unsigned long long;
+    static constexpr T kInf = 0x7ff0000000000000ull;
+    __device__ __forceinline__ static T bits(double v) { return (T)__double_as_longlong(v); }
+    __device__ __forceinline__ static double value(T b) { return __longlong_as_double((long long)b); }
+};
+
+// shared-memory layout of one tile
+template <class TS, int KP>
+struct EdgeTileLayout {
+    using C = typename Store<TS>::C;
+    using M = typename MinBits<C>::T;
+    static constexpr int TR = kEdgeTileRows;
+    static constexpr int YS = 0;                                        // TR x KP targets
+    static constexpr int DG = YS + TR * KP * (int)sizeof(C);            // TR diagonals
+    static constexpr int SY = DG + TR * (int)sizeof(C);                 // TR S_yy
+    static constexpr int MN = (SY + TR * (int)sizeof(C) + 7) & ~7;      // TR row minima (bits)
+    static constexpr int RP = MN + TR * (int)sizeof(M);                 // TR + 1 slot offsets
+    static constexpr int CN = RP + (TR + 1) * 4;                        // TR strong counts
+    static constexpr int DF = CN + TR * 4;                              // TR defer marks
+    static constexpr int SR = DF + TR * 4;                              // slot -> local row (u8)
+    static constexpr int BYTES = SR + kEdgeTileSlots;
+};
+
+template <class TS, int G, int NV, int U, bool UW>
+__global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
+{
+    using S = Store<TS>;
+    using C = typename S::C;
+    using AV = typename S::A;
+    using MB = MinBits<C>;
+    constexpr int V = S::V;
+    constexpr int P = G * NV;           // 16-byte pieces per row
+    constexpr int KP = P * V;           // padded components per row
+    using L = EdgeTileLayout<TS, KP>;
+    constexpr bool kMixed = !std::is_same<C, double>::value;
+    constexpr int HOLD = P <= 4 ? P : 1;     // pieces of x_j kept in registers between the sums
+    extern __shared__ __align__(16) unsigned char esm[];
+    C *ys = reinterpret_cast<C *>(esm + L::YS);
+    C *dg = reinterpret_cast<C *>(esm + L::DG);
+    C *syy = reinterpret_cast<C *>(esm + L::SY);
+    typename MB::T *rmin = reinterpret_cast<typename MB::T *>(esm + L::MN);
+    int32_t *rps = reinterpret_cast<int32_t *>(esm + L::RP);
+    int32_t *cnt = reinterpret_cast<int32_t *>(esm + L::CN);
+    int32_t *dfr = reinterpret_cast<int32_t *>(esm + L::DF);
+    uint8_t *srow = esm + L::SR;
+
+    const int32_t R0 = __ldg(A.tiles + blockIdx.x), R1 = __ldg(A.tiles + blockIdx.x + 1);
+    const int nr = R1 - R0;
+    const bool single = nr == 1;                 // possibly longer than kEdgeTileSlots
+    const int32_t *__restrict__ col = A.col;
+    const AV *__restrict__ val = (const AV *)A.val;
+    const TS *__restrict__ X = (const TS *)A.x;
+    const C *__restrict__ wv = (const C *)A.w;
+
+    for (int q = threadIdx.x; q <= nr; q += kEdgeThreads) rps[q] = __ldg(A.rp + R0 + q);
+    for (int q = threadIdx.x; q < nr; q += kEdgeThreads) {
+        dg[q] = (C)__ldg((const AV *)A.diag + R0 + q);
+        rmin[q] = MB::kInf;
+        cnt[q] = 0;
+        dfr[q] = 0;
+    }
+    __syncthreads();
+    const int S0 = rps[0], S1 = rps[nr];
+
+    // ---- A. targets -----------------------------------------------------------
+    {
+        const int lane = threadIdx.x % G;
+        const unsigned gmask = (G == 32) ? 0xffffffffu
+                                         : (((1u << G) - 1u) << ((threadIdx.x % 32) / G * G));
+        for (int rl = threadIdx.x / G; rl < nr; rl += kEdgeThreads / G) {
+            const int64_t r = R0 + rl;
+            const int p0 = rps[rl], p1 = rps[rl + 1];
+            if (!single)
+                for (int p = p0 + lane; p < p1; p += G) srow[p - S0] = (uint8_t)rl;
+            C y[NV][V];
+#pragma unroll
+            for (int t = 0; t < NV; ++t) S::unpack(ldg16(X + r * KP + (t * G + lane) * V), y[t]);
+            if (A.target == 0) {
+                Acc<C, V> acc[NV];
+                row_sum<TS, G, NV, U, false>(col, val, X, X, 0, KP, lane, p0, p1, acc);
+                const C d = C(1) / dg[rl];
+#pragma unroll
+                for (int t = 0; t < NV; ++t)
+#pragma unroll
+                    for (int e = 0; e < V; ++e) y[t][e] = fma(-d, acc[t].get(e), y[t][e]);
+            }
+            C s = C(0);
+#pragma unroll
+            for (int t = 0; t < NV; ++t) {
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    ys[rl * KP + (t * G + lane) * V + e] = y[t][e];
+                    if constexpr (kMixed)
+                        s = fma(UW ? y[t][e] : wv[(t * G + lane) * V + e] * y[t][e], y[t][e], s);
+                }
+            }
+            if constexpr (kMixed) {
+                s = group_sum<G>(s, gmask);
+                if (lane == 0) syy[rl] = s;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- B. one-point fits, one stored entry per thread -------------------------
+    C *a_out = (C *)A.a_out;
+    C *ls_out = (C *)A.ls_out;
+    for (int p = S0 + threadIdx.x; p < S1; p += kEdgeThreads) {
+        const int rl = single ? 0 : srow[p - S0];
+        const int64_t r = R0 + rl;
+        const int j = __ldg(col + p);
+        C a_, ls_;
+        if (j == r) {
+            a_ = C(0);
+            ls_ = C(NAN);
+        } else if (A.target == 0 && rps[rl + 1] - rps[rl] == 2) {
+            a_ = -(C)__ldg(val + p) / dg[rl];           // y_i = -(a_ij/a_ii) x_j exactly
+            ls_ = C(0);
+        } else {
+            const TS *xj = X + (int64_t)j * KP;
+            const C *yr = ys + rl * KP;
+            uint4 hold[HOLD];
+            PieceSums<C, V, UW> ps;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                const uint4 raw = ldg16(xj + c * V);
+                if constexpr (P <= 4) hold[c] = raw;
+                C x[V], y[V], w[V];
+                S::unpack(raw, x);
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    y[e] = yr[c * V + e];
+                    w[e] = UW ? C(1) : wv[c * V + e];
+                }
+                ps.add(x, y, w);
+            }
+            const C sxx = ps.sxx(), syx = ps.syx();
+            a_ = (sxx == C(0)) ? C(0) : divide(syx, sxx);
+            C res = C(0);
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                uint4 raw;
+                if constexpr (P <= 4) raw = hold[c];
+                else raw = ldg16(xj + c * V);
+                C x[V], y[V], w[V];
+                S::unpack(raw, x);
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    y[e] = yr[c * V + e];
+                    w[e] = UW ? C(1) : wv[c * V + e];
+                }
+                residual_add<C, V, UW>(a_, x, y, w, res);
+            }
+            ls_ = res;
+            if constexpr (kMixed)
+                if (ls_ < C(1e-4) * syy[rl]) dfr[rl] = 1;    // cancellation: redo the row in FP64
+        }
+        a_out[p] = a_;
+        ls_out[p] = ls_;
+        if (j != r) atomicMin(&rmin[rl], MB::bits(ls_));
+    }
+    __syncthreads();
+
+    // ---- C. strength flags (Eq. (4.4) in LS form) and counts -------------------
+    const C theta = (C)A.theta;
+    for (int p = S0 + threadIdx.x; p < S1; p += kEdgeThreads) {
+        const int rl = single ? 0 : srow[p - S0];
+        const int j = __ldg(col + p);
+        const C l = ls_out[p];                       // written by this block in B
+        const C m = MB::value(rmin[rl]);
+        const int strong = (j != R0 + rl) && (l == C(0) || theta * l < m);
+        A.flag_out[p] = (uint8_t)strong;
+        if (strong) atomicAdd(&cnt[rl], 1);
+    }
+    __syncthreads();
+    for (int rl = threadIdx.x; rl < nr; rl += kEdgeThreads) {
+        A.count_out[R0 + rl] = cnt[rl];
+        if (kMixed && dfr[rl]) A.defer_list[atomicAdd(A.defer_count, 1u)] = R0 + rl;
     }
 }
 
@@ -380,50 +597,64 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
     }
 }
 
+template <class K>
+cudaError_t opt_in_smem(K kernel, int bytes, bool &opted)
+{
+    if (bytes <= 48 * 1024 || opted) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) opted = true;
+    return e;
+}
+
 template <class TS, int G, int NV, int U, bool UW>
-cudaError_t go(const EdgeArgs &a, cudaStream_t s)
+cudaError_t go(int stage, const EdgeArgs &a, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;
+    if (stage == 1) {
+        constexpr int KP = G * NV * Store<TS>::V;
+        if (a.Kp != KP || a.ntiles <= 0) return cudaErrorInvalidValue;
+        constexpr int smem = EdgeTileLayout<TS, KP>::BYTES;
+        static bool opted = false;
+        const cudaError_t e = opt_in_smem(k_edge_tiles<TS, G, NV, U, UW>, smem, opted);
+        if (e != cudaSuccess) return e;
+        k_edge_tiles<TS, G, NV, U, UW><<<(unsigned)a.ntiles, kEdgeThreads, smem, s>>>(a);
+        return cudaGetLastError();
+    }
     const int rows_per_block = kEdgeThreads / G;
     const unsigned grid = (unsigned)(((int64_t)a.n + rows_per_block - 1) / rows_per_block);
     constexpr int smem = edge_smem_bytes<typename Store<TS>::C, G>();
-    if constexpr (smem > 48 * 1024) {
-        static bool opted = false;
-        if (!opted) {
-            const cudaError_t e = cudaFuncSetAttribute(k_edge<TS, G, NV, U, UW>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            opted = true;
-        }
-    }
-    k_edge<TS, G, NV, U, UW><<<grid, kEdgeThreads, smem, s>>>(a);
+    static bool opted = false;
+    const cudaError_t e = opt_in_smem(k_edge_rows<TS, G, NV, U, UW>, smem, opted);
+    if (e != cudaSuccess) return e;
+    k_edge_rows<TS, G, NV, U, UW><<<grid, kEdgeThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <class TS, int G, int NV, bool UW>
-cudaError_t dispatch_u(int U, const EdgeArgs &a, cudaStream_t s)
+cudaError_t dispatch_u(int stage, int U, const EdgeArgs &a, cudaStream_t s)
 {
     switch (U) {
-    case 4: return go<TS, G, NV, 4, UW>(a, s);
-    case 8: return go<TS, G, NV, 8, UW>(a, s);
+    case 4: return go<TS, G, NV, 4, UW>(stage, a, s);
+    case 8: return go<TS, G, NV, 8, UW>(stage, a, s);
     }
     return cudaErrorInvalidValue;
 }
 
 template <class TS, int G, int NV>
-cudaError_t dispatch_w(int U, bool unit_w, const EdgeArgs &a, cudaStream_t s)
+cudaError_t dispatch_w(int stage, int U, bool unit_w, const EdgeArgs &a, cudaStream_t s)
 {
-    return unit_w ? dispatch_u<TS, G, NV, true>(U, a, s) : dispatch_u<TS, G, NV, false>(U, a, s);
+    return unit_w ? dispatch_u<TS, G, NV, true>(stage, U, a, s)
+                  : dispatch_u<TS, G, NV, false>(stage, U, a, s);
 }
 
 template <class TS, int G>
-cudaError_t dispatch_nv(int NV, int U, bool unit_w, const EdgeArgs &a, cudaStream_t s)
+cudaError_t dispatch_nv(int stage, int NV, int U, bool unit_w, const EdgeArgs &a, cudaStream_t s)
 {
     constexpr int V = Store<TS>::V;
     switch (NV) {
-    case 1: return dispatch_w<TS, G, 1>(U, unit_w, a, s);
-    case 2: if constexpr (G * 2 * V <= 64) return dispatch_w<TS, G, 2>(U, unit_w, a, s); break;
-    case 4: if constexpr (G * 4 * V <= 64) return dispatch_w<TS, G, 4>(U, unit_w, a, s); break;
+    case 1: return dispatch_w<TS, G, 1>(stage, U, unit_w, a, s);
+    case 2: if constexpr (G * 2 * V <= 64) return dispatch_w<TS, G, 2>(stage, U, unit_w, a, s); break;
+    case 4: if constexpr (G * 4 * V <= 64) return dispatch_w<TS, G, 4>(stage, U, unit_w, a, s); break;
     }
     return cudaErrorInvalidValue;
 }
@@ -433,12 +664,12 @@ cudaError_t dispatch_g(Shape sh, bool unit_w, const EdgeArgs &a, cudaStream_t s)
 {
     constexpr int V = Store<TS>::V;
     switch (sh.G) {
-    case 1: return dispatch_nv<TS, 1>(sh.NV, sh.U, unit_w, a, s);
-    case 2: return dispatch_nv<TS, 2>(sh.NV, sh.U, unit_w, a, s);
-    case 4: return dispatch_nv<TS, 4>(sh.NV, sh.U, unit_w, a, s);
-    case 8: if constexpr (8 * V <= 64) return dispatch_nv<TS, 8>(sh.NV, sh.U, unit_w, a, s); break;
-    case 16: if constexpr (16 * V <= 64) return dispatch_nv<TS, 16>(sh.NV, sh.U, unit_w, a, s); break;
-    case 32: if constexpr (32 * V <= 64) return dispatch_nv<TS, 32>(sh.NV, sh.U, unit_w, a, s); break;
+    case 1: return dispatch_nv<TS, 1>(sh.stage, sh.NV, sh.U, unit_w, a, s);
+    case 2: return dispatch_nv<TS, 2>(sh.stage, sh.NV, sh.U, unit_w, a, s);
+    case 4: return dispatch_nv<TS, 4>(sh.stage, sh.NV, sh.U, unit_w, a, s);
+    case 8: if constexpr (8 * V <= 64) return dispatch_nv<TS, 8>(sh.stage, sh.NV, sh.U, unit_w, a, s); break;
+    case 16: if constexpr (16 * V <= 64) return dispatch_nv<TS, 16>(sh.stage, sh.NV, sh.U, unit_w, a, s); break;
+    case 32: if constexpr (32 * V <= 64) return dispatch_nv<TS, 32>(sh.stage, sh.NV, sh.U, unit_w, a, s); break;
     }
     return cudaErrorInvalidValue;
 }

@@ -50,56 +50,83 @@ template <> __device__ __forceinline__ double to_double<__nv_bfloat16>(__nv_bflo
 }
 
 // The start value of a component is x = d * 2^-32 with the odd integer
-// d = 2m + 1 - 2^32, |d| < 2^32, m the component's 32-bit random integer.
-// It is produced in the storage type with integer arithmetic only -- the
-// FP64 pipe of the GPU is narrow -- and rounded to nearest even exactly once.
-template <class TS> __device__ __forceinline__ TS start_value(int64_t d);
-
-template <> __device__ __forceinline__ double start_value<double>(int64_t d)
+// d = 2m + 1 - 2^32, m the component's 32-bit random integer.  |d| < 2^32,
+// so the magnitude a = |d| fits 32 bits: a = 2(m - 2^31) + 1 for m >= 2^31
+// (d > 0), a = 2(2^31 - 1 - m) + 1 otherwise (d < 0).  The value is built
+// in the storage type with 32-bit integer work (the GPU's FP64 pipe is
+// narrow) and rounded to nearest even exactly once.
+__device__ __forceinline__ uint32_t start_magnitude(uint32_t m, bool &neg)
 {
-    if (d == 0) return 0.0;                       // |d| < 2^33: exact in FP64
-    const uint64_t sgn = d < 0 ? (1ull << 63) : 0ull;
-    const uint64_t a = d < 0 ? (uint64_t)(-d) : (uint64_t)d;
-    const int lead = 63 - __clzll((long long)a);  // 0..31
-    const uint64_t mant = (a << (52 - lead)) & ((1ull << 52) - 1ull);
-    const uint64_t expo = (uint64_t)(lead - 32 + 1023);
-    return __longlong_as_double((long long)(sgn | (expo << 52) | mant));
+    neg = (m & 0x80000000u) == 0u;
+    return neg ? (((0x7fffffffu - m) << 1) | 1u) : (((m & 0x7fffffffu) << 1) | 1u);
 }
 
-template <> __device__ __forceinline__ float start_value<float>(int64_t d)
+// round the odd integer a (1 <= a < 2^32) to P+1 significant bits (nearest,
+// ties to even) and return the IEEE fields of a * 2^-32 for a format with P
+// stored mantissa bits and exponent bias B: every value here is normal
+template <int P, int B>
+__device__ __forceinline__ uint32_t encode_fields(uint32_t a, uint32_t &mant)
 {
-    return __ll2float_rn(d) * 0x1.0p-32f;         // one rounding, exact scaling
-}
-
-template <> __device__ __forceinline__ __nv_bfloat16 start_value<__nv_bfloat16>(int64_t d)
-{
-    // round |d| to 8 significant bits (nearest, ties to even), then the value
-    // is exact in FP32 and in BF16
-    uint64_t a = d < 0 ? (uint64_t)(-d) : (uint64_t)d;
-    if (a != 0) {
-        const int lead = 63 - __clzll((long long)a);
-        if (lead > 7) {
-            const int sh = lead - 7;
-            uint64_t q = a >> sh;
-            const uint64_t rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-            if (rem > half || (rem == half && (q & 1ull))) ++q;
-            a = q << sh;
-        }
+    int lead = 31 - __clz((int)a);                 // 2^lead <= a < 2^(lead+1)
+    uint32_t q;
+    if (lead <= P) {
+        q = a << (P - lead);                       // exact
+    } else {
+        const int sh = lead - P;
+        q = a >> sh;
+        const uint32_t rem = a & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        if (rem > half || (rem == half && (q & 1u))) ++q;
+        if (q == (2u << P)) { q = 1u << P; ++lead; }   // rounded up to the next power of two
     }
-    const float f = __ull2float_rn(a) * 0x1.0p-32f;
-    return __float2bfloat16_rn(d < 0 ? -f : f);
+    mant = q - (1u << P);
+    return (uint32_t)(lead - 32 + B);             // biased exponent
 }
 
-// one thread per (row, block of 8 components): one Philox4x64-10 call
-// gives 4 x 64 bits = 8 components of 32 bits (low half first)
+// raw bits of the start value of one component in the storage type
+template <class TS> struct StartBits;
+template <> struct StartBits<double> {
+    using Raw = unsigned long long;
+    __device__ __forceinline__ static Raw get(uint32_t m) {
+        bool neg;
+        const uint32_t a = start_magnitude(m, neg);    // < 2^32: exact in FP64
+        const int lead = 31 - __clz((int)a);
+        const unsigned long long mant = ((unsigned long long)a << (52 - lead)) & ((1ull << 52) - 1ull);
+        const unsigned long long expo = (unsigned long long)(lead - 32 + 1023);
+        return (neg ? (1ull << 63) : 0ull) | (expo << 52) | mant;
+    }
+};
+template <> struct StartBits<float> {
+    using Raw = uint32_t;
+    __device__ __forceinline__ static Raw get(uint32_t m) {
+        bool neg;
+        uint32_t mant;
+        const uint32_t e = encode_fields<23, 127>(start_magnitude(m, neg), mant);
+        return (neg ? 0x80000000u : 0u) | (e << 23) | mant;
+    }
+};
+template <> struct StartBits<__nv_bfloat16> {
+    using Raw = uint32_t;                               // low 16 bits used
+    __device__ __forceinline__ static Raw get(uint32_t m) {
+        bool neg;
+        uint32_t mant;
+        const uint32_t e = encode_fields<7, 127>(start_magnitude(m, neg), mant);
+        return (neg ? 0x8000u : 0u) | (e << 7) | mant;
+    }
+};
+
+// one thread per (row, block of 8 components): one Philox4x64-10 call gives
+// 4 x 64 bits = 8 components of 32 bits (low half first).  Kp is a power of
+// two; lq = log2(max(1, Kp / 8)).  Values are assembled as raw bits with
+// integer operations and written with 16-byte stores (or per component for
+// rows shorter than 8 components).
 template <class TS>
-__global__ void k_tv_init(InitArgs A)
+__global__ void __launch_bounds__(kThreads) k_tv_init(InitArgs A, int lq)
 {
-    const int nq = (A.Kp + 7) / 8;
+    using SB = StartBits<TS>;
     const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (t >= (int64_t)A.n * nq) return;
-    const int64_t r = t / nq;
-    const int q = (int)(t % nq);
+    const int64_t r = t >> lq;
+    if (r >= A.n) return;
+    const int q = (int)(t & ((1 << lq) - 1));
     const int64_t o = A.perm ? A.perm[r] : r;
     int lo = 0, hi = A.nmat;                 // matrix b with mat_off[b] <= o < mat_off[b+1]
     while (hi - lo > 1) {
@@ -108,14 +135,39 @@ __global__ void k_tv_init(InitArgs A)
     }
     const uint64_t li = (uint64_t)(o - A.mat_off[lo]);
     const U64x4 u = philox4x64_10(li, (uint64_t)q, 0ull, 0ull, A.seed, (uint64_t)lo);
-    TS *x = (TS *)A.x + r * A.Kp;
+    typename SB::Raw v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int kappa = 8 * q + k;
-        if (kappa >= A.Kp) break;
-        const uint64_t m = (k & 1) ? (u.v[k / 2] >> 32) : (u.v[k / 2] & 0xffffffffull);
-        const int64_t d = (int64_t)(2 * m + 1) - (1ll << 32);
-        x[kappa] = kappa < A.K ? start_value<TS>(d) : from_double<TS>(0.0);
+        const uint32_t m = (k & 1) ? (uint32_t)(u.v[k / 2] >> 32) : (uint32_t)u.v[k / 2];
+        v[k] = 8 * q + k < A.K ? SB::get(m) : 0;     // padding: +0
+    }
+    TS *x = (TS *)A.x + r * A.Kp + 8 * q;
+    if (A.Kp >= 8) {
+        uint4 *x4 = reinterpret_cast<uint4 *>(x);
+        if constexpr (sizeof(TS) == 2) {
+            x4[0] = make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16),
+                               v[6] | (v[7] << 16));
+        } else if constexpr (sizeof(TS) == 4) {
+            x4[0] = make_uint4(v[0], v[1], v[2], v[3]);
+            x4[1] = make_uint4(v[4], v[5], v[6], v[7]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                x4[c] = make_uint4((uint32_t)v[2 * c], (uint32_t)(v[2 * c] >> 32),
+                                   (uint32_t)v[2 * c + 1], (uint32_t)(v[2 * c + 1] >> 32));
+        }
+    } else {
+        typename SB::Raw *xr = reinterpret_cast<typename SB::Raw *>(x);
+        if constexpr (sizeof(TS) == 2) {
+            uint16_t *x16 = reinterpret_cast<uint16_t *>(x);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < A.Kp) x16[k] = (uint16_t)v[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < A.Kp) xr[k] = v[k];
+        }
     }
 }
 
@@ -220,12 +272,15 @@ inline unsigned blocks(int64_t work) { return (unsigned)((work + kThreads - 1) /
 
 cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t s)
 {
-    const int64_t work = (int64_t)a.n * ((a.Kp + 7) / 8);
+    if (a.Kp & (a.Kp - 1)) return cudaErrorInvalidValue;     // Kp is a power of two
+    int lq = 0;
+    while ((8 << lq) < a.Kp) ++lq;
+    const int64_t work = (int64_t)a.n << lq;
     if (work == 0) return cudaSuccess;
     switch (storage) {
-    case ST_FP64: k_tv_init<double><<<blocks(work), kThreads, 0, s>>>(a); break;
-    case ST_FP32: k_tv_init<float><<<blocks(work), kThreads, 0, s>>>(a); break;
-    case ST_BF16: k_tv_init<__nv_bfloat16><<<blocks(work), kThreads, 0, s>>>(a); break;
+    case ST_FP64: k_tv_init<double><<<blocks(work), kThreads, 0, s>>>(a, lq); break;
+    case ST_FP32: k_tv_init<float><<<blocks(work), kThreads, 0, s>>>(a, lq); break;
+    case ST_BF16: k_tv_init<__nv_bfloat16><<<blocks(work), kThreads, 0, s>>>(a, lq); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

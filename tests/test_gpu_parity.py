@@ -43,10 +43,13 @@ MATRICES = {
 
 
 def gpu_build(rp, col, val, K, seed, nu, omega, theta, sweep=0, color=None, w=None,
-              target=0, precision="fp64", X0=None):
+              target=0, precision="fp64", X0=None, edge_stage=None):
     with amgd.Handle(rp, col, val, K, seed) as h:
         if precision != "fp64":
             h.set_precision(precision)
+        if edge_stage is not None:
+            G, NV, U, _ = h.kernel_shape(amgd.AMGD_KERNEL_EDGE)
+            h.set_kernel_shape(amgd.AMGD_KERNEL_EDGE, G, NV, U, edge_stage)
         if color is not None:
             h.set_coloring(color)
         if w is not None:
@@ -159,6 +162,36 @@ def test_build_fp64_mcgs_weights():
         want = oracle.build(rp, col, val, 16, 1, 8, 1.0, theta, oracle.SWEEP_MCGS, color, w=w)
         got = gpu_build(rp, col, val, 16, 1, 8, 1.0, theta, 1, color, w=w)
         compare_fp64(rp, col, val, got, want, theta, w)
+
+
+def _tile_edge_matrices():
+    """Tiles of the edge pass: ragged tile ends, rows without off-diagonals,
+    one-off-diagonal rows, and a row longer than a tile's slot capacity
+    (a tile of its own) next to short rows."""
+    yield "graph_2000", inputs.graph_laplacian(2000, 8.0, 4)
+    yield "sparse_graph_isolated", inputs.graph_laplacian(700, 0.4, 9)
+    yield "lap1d_1000", inputs.lap1d(1000)
+    import scipy.sparse as sp
+    n = 5000                       # row 17 couples to every row: 5000 entries
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        rows.append(i); cols.append(i); vals.append(4.0 if i != 17 else float(n))
+        if i != 17:
+            rows += [17, i]; cols += [i, 17]; vals += [-0.5, -0.25]
+        if i + 1 < n:
+            rows += [i, i + 1]; cols += [i + 1, i]; vals += [-1.0, -1.0]
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A.sum_duplicates()
+    A.sort_indices()
+    yield "one_long_row", (A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data)
+
+
+@pytest.mark.parametrize("K,target", [(16, 0), (8, 1), (33, 0)])
+def test_edge_tile_kernel_matches_oracle(K, target):
+    for name, (rp, col, val) in _tile_edge_matrices():
+        want = oracle.build(rp, col, val, K, 3, 3, 0.6, 0.5, mode=target)
+        got = gpu_build(rp, col, val, K, 3, 3, 0.6, 0.5, target=target, edge_stage=1)
+        compare_fp64(rp, col, val, got, want, 0.5)
 
 
 # --------------------------------------------------------------------------- edge cases
@@ -338,7 +371,8 @@ def test_kernel_shapes_agree(prec, K):
                 assert st >= 1, "direct shapes are always available"
                 continue          # staged shape beyond the shared-memory limit
             staged_ok += st
-            h.set_kernel_shape(amgd.AMGD_KERNEL_EDGE, G, NV, U)
+            # the edge pass has two kernels: rows (stage 0) and tiles (stage 1)
+            h.set_kernel_shape(amgd.AMGD_KERNEL_EDGE, G, NV, U, min(st, 1))
             assert h.kernel_shape(amgd.AMGD_KERNEL_RELAX) == (G, NV, U, st)
             h.relax(3, 1.0, amgd.AMGD_SWEEP_MCGS)
             X = h.get_vectors()
