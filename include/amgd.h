@@ -228,8 +228,10 @@ int amgd_graph_launch(amgd_handle h);
  *   use (waits bounded to about one second; a wait that runs out makes the
  *   next synchronising call return AMGD_ERR_TIMEOUT); 2 warp-pipelined, CSR
  *   slices and neighbour rows copied with cp.async two and one row groups
- *   ahead (U must be 4).  Shapes change speed
- *   only, never results.  kernel: AMGD_KERNEL_RELAX (the sweeps) or
+ *   ahead (U must be 4).  For the distance pass, staged selects 0 the row
+ *   kernel (G lanes per row) or 1 the tile kernel (one thread per stored
+ *   entry).  Shapes change speed only, never results beyond the order of
+ *   the K-term LS sums.  kernel: AMGD_KERNEL_RELAX (the sweeps) or
  *   AMGD_KERNEL_EDGE (the distance pass); the shape applies to the current
  *   storage precision.
  * amgd_autotune times every valid shape of both kernels on the handle's own

@@ -124,7 +124,8 @@ __device__ __forceinline__ uint4 ldg16(const void *p)
 // gathered per batch.  P is fixed by (storage, K); G, NV and U are free.
 struct Shape {
     int G, NV, U;
-    int stage = 0;   // 1: persistent kernel with TMA-staged CSR tiles (relax only)
+    int stage = 0;   // relaxation: 0 direct, 1 TMA-staged CSR, 2 cp.async pipelined;
+                     // edge pass: 0 row kernel, 1 tile kernel
 };
 
 // device status bits set by bounded waits that gave up

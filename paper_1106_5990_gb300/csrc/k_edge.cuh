@@ -489,10 +489,9 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
     const C theta = (C)A.theta;
     for (int p = S0 + threadIdx.x; p < S1; p += kEdgeThreads) {
         const int rl = single ? 0 : srow[p - S0];
-        const int j = __ldg(col + p);
-        const C l = ls_out[p];                       // written by this block in B
+        const C l = ls_out[p];                       // written by this block in B; NaN on the diagonal
         const C m = MB::value(rmin[rl]);
-        const int strong = (j != R0 + rl) && (l == C(0) || theta * l < m);
+        const int strong = l == C(0) || theta * l < m;   // false for the diagonal's NaN
         A.flag_out[p] = (uint8_t)strong;
         if (strong) atomicAdd(&cnt[rl], 1);
     }
