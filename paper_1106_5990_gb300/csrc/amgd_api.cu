@@ -85,6 +85,7 @@ struct amgd_ctx {
     double *lsb = nullptr;                       // dL/dLS per slot
     double *adj_part = nullptr;                  // 2 x kAdjReduceBlocks partials + 2 sums
     int32_t *at_rp = nullptr, *at_row = nullptr, *at_slot = nullptr;   // transposed pattern
+    int32_t *mirror = nullptr;                   // slot of (j, i) for slot (i, j); symmetric patterns
     int32_t *edge_tiles = nullptr;               // row tiles of the edge pass
     int32_t n_edge_tiles = 0;
     bool last_backward_builtin = false;          // the last reverse pass used the built-in loss
@@ -1212,6 +1213,24 @@ int ensure_transpose(amgd_ctx *h)
         CK(h, cudaMemcpy(h->at_row, trow.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
         CK(h, cudaMemcpy(h->at_slot, tslot.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
+    // structurally symmetric pattern with ascending columns: row j's columns
+    // are column j's rows in the same order, and slot p = (j, i) has the
+    // mirror slot (i, j); the reverse sweeps then need one kernel per sweep
+    bool sym = true;
+    for (int64_t j = 0; j < n && sym; ++j) {
+        const int32_t p0 = h->h_rp[(size_t)j], p1 = h->h_rp[(size_t)j + 1];
+        if (p1 - p0 != trp[(size_t)j + 1] - trp[(size_t)j]) { sym = false; break; }
+        for (int32_t k = 0; k < p1 - p0; ++k)
+            if (h->h_col[(size_t)(p0 + k)] != trow[(size_t)(trp[(size_t)j] + k)]) { sym = false; break; }
+    }
+    if (sym && nnz) {
+        std::vector<int32_t> mirror((size_t)nnz);
+        for (int64_t j = 0; j < n; ++j)
+            for (int32_t k = 0; k < h->h_rp[(size_t)j + 1] - h->h_rp[(size_t)j]; ++k)
+                mirror[(size_t)(h->h_rp[(size_t)j] + k)] = tslot[(size_t)(trp[(size_t)j] + k)];
+        CK(h, dalloc(&h->mirror, (size_t)nnz));
+        CK(h, cudaMemcpy(h->mirror, mirror.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     return AMGD_OK;
 }
 
@@ -1229,7 +1248,7 @@ int prepare_backward(amgd_ctx *h)
     int rc = ensure_transpose(h);
     if (rc != AMGD_OK) return rc;
     CK(h, ensure_buf(&h->adj_vec, h->adj_vec_bytes, 4 * nk * cs));
-    CK(h, ensure_buf(&h->adj_slot, h->adj_slot_bytes, 3 * (size_t)(h->nnz ? h->nnz : 1) * cs));
+    CK(h, ensure_buf(&h->adj_slot, h->adj_slot_bytes, 4 * (size_t)(h->nnz ? h->nnz : 1) * cs));
     CK(h, ensure_buf(&h->seg, h->seg_bytes, (size_t)(S - 1) * xb));
     if (!h->lsb) CK(h, dalloc(&h->lsb, (size_t)(h->nnz ? h->nnz : 1)));
     if (!h->adj_part) CK(h, dalloc(&h->adj_part, (size_t)2 * kAdjReduceBlocks + 2));
@@ -1257,10 +1276,13 @@ int run_backward(amgd_ctx *h, const double *lsb_in, double *vb, cudaStream_t s)
     void *Xbar[2] = {vecs + 2 * nk * cs, vecs + 3 * nk * cs};
     char *slots = (char *)h->adj_slot;
     void *gs = slots, *gt = slots + nnz * cs, *at_b = slots + 2 * nnz * cs;
+    void *bm = slots + 3 * nnz * cs;
 
     CK(h, launch_adj_upstream(st, h->rp_o, h->col_o, h->ls, h->flag, lsb_in, h->lsb, h->adj_part,
                               nb, n, h->target, s));
     CK(h, launch_adj_bvals(st, h->val_o, h->diag64_o, h->at_row, h->at_slot, at_b, nnz, s));
+    if (h->mirror)   // per slot (j, i): a_ij / a_ii, the mirror entry over its row's diagonal
+        CK(h, launch_adj_bvals(st, h->val_o, h->diag64_o, h->col_o, h->mirror, bm, nnz, s));
 
     AdjArgs a;
     a.rp = h->rp_o;
@@ -1271,6 +1293,7 @@ int run_backward(amgd_ctx *h, const double *lsb_in, double *vb, cudaStream_t s)
     a.at_row = h->at_row;
     a.at_slot = h->at_slot;
     a.at_b = at_b;
+    a.bm = h->mirror ? bm : nullptr;
     a.x = h->x[h->cur];
     a.w = st == ST_FP64 ? (const void *)h->w64 : (const void *)h->w32;
     a.a = h->a;
@@ -1308,8 +1331,12 @@ int run_backward(amgd_ctx *h, const double *lsb_in, double *vb, cudaStream_t s)
             a.xbar_in = Xbar[xc];
             a.xbar_out = Xbar[1 - xc];
             a.first = k == nu - 1;
-            CK(h, launch_adj_gram(st, a, s));
-            CK(h, launch_adj_spmm_t(st, a, s));
+            if (a.bm) {
+                CK(h, launch_adj_sweep_sym(st, a, s));
+            } else {
+                CK(h, launch_adj_gram(st, a, s));
+                CK(h, launch_adj_spmm_t(st, a, s));
+            }
             xc = 1 - xc;
         }
     }
@@ -1455,7 +1482,7 @@ int amgd_destroy(amgd_handle h)
                     h->val32, h->x[0], h->x[1],
                     h->w64, h->w32, h->a, h->ls, h->flag, h->count, h->tile, h->s_rp_tmp,
                     h->s_col_tmp, h->tmp64, h->ckpt, h->seg, h->adj_vec, h->adj_slot, h->lsb,
-                    h->adj_part, h->at_rp, h->at_row, h->at_slot, h->edge_tiles};
+                    h->adj_part, h->at_rp, h->at_row, h->at_slot, h->edge_tiles, h->mirror};
     for (void *p : ptrs) dfree(p);
     delete h;
     return AMGD_OK;

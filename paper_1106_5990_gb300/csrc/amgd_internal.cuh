@@ -237,6 +237,7 @@ struct AdjArgs {
     const int32_t *at_rp;             // transpose: column j owns entries [at_rp[j], at_rp[j+1])
     const int32_t *at_row, *at_slot;  // row i and slot p of each entry (rows ascending)
     const void *at_b;                 // b_q = a(i,j) / a_ii per entry, C
+    const void *bm;                   // symmetric pattern: per slot (j, i) a_ij / a_ii, C (else NULL)
     const void *x;                    // storage type: X_nu (edge stages) or X_k (sweeps)
     const void *w;                    // LS weights, Kp, C
     const void *a;                    // forward fit coefficients per slot, C
@@ -268,6 +269,8 @@ cudaError_t launch_adj_xbar_nu(int storage, const AdjArgs &a, cudaStream_t s);
 cudaError_t launch_adj_gram(int storage, const AdjArgs &a, cudaStream_t s);
 // Xbar_k = Xbar_{k+1} - omega (D^{-1} A)^T Xbar_{k+1}
 cudaError_t launch_adj_spmm_t(int storage, const AdjArgs &a, cudaStream_t s);
+// both of the above in one pass over the rows (structurally symmetric patterns)
+cudaError_t launch_adj_sweep_sym(int storage, const AdjArgs &a, cudaStream_t s);
 // dL/dval (FP64, caller slots) from gs, gt; per-block partials of dL/domega
 cudaError_t launch_adj_finish(int storage, const AdjArgs &a, bool have_gs, const double *val64,
                               const double *diag64, const int32_t *diag_slot, double *val_bar,

@@ -350,6 +350,64 @@ __global__ void __launch_bounds__(kThreads) k_spmm_t(AdjArgs A)
     stc<C, V>((C *)A.xbar_out + jr * Kp + lane * V, acc);
 }
 
+// Structurally symmetric pattern: both products of one reverse sweep in one
+// pass over row j, whose columns i are exactly the rows of column j:
+//   gs_p (+)= <Xbar_{k+1,j}, X_k,i>                    (slot p = (j, i))
+//   Xbar_k,j = Xbar_{k+1,j} - omega sum_p bm_p Xbar_{k+1,i},  bm_p = a_ij / a_ii
+// (the diagonal slot has bm = 1).  Neighbours are taken four at a time.
+template <class TS, int G>
+__global__ void __launch_bounds__(kThreads) k_sweep_sym(AdjArgs A)
+{
+    using S = Store<TS>;
+    using C = typename S::C;
+    constexpr int V = S::V;
+    constexpr int U = 4;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t r = (int64_t)blockIdx.x * (kThreads / G) + threadIdx.x / G;
+    if (r >= A.n) return;
+    const unsigned gmask = group_mask<G>();
+    const TS *__restrict__ X = (const TS *)A.x;
+    const C *__restrict__ Xb = (const C *)A.xbar_in;
+    const C *__restrict__ bm = (const C *)A.bm;
+    C *gs = (C *)A.gs;
+    const int Kp = A.Kp;
+    const C om = (C)A.omega;
+    const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
+    C xb[V], acc[V];
+    ldc<C, V>(Xb + r * Kp + lane * V, xb);
+#pragma unroll
+    for (int e = 0; e < V; ++e) acc[e] = xb[e];
+    for (int pb = p0; pb < p1; pb += U) {
+        uint4 raw[U];
+        C xbi[U][V];
+        C c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (pb + u < p1) {
+                const int64_t i = __ldg(A.col + pb + u);
+                raw[u] = ldg16(X + i * Kp + lane * V);
+                ldc<C, V>(Xb + i * Kp + lane * V, xbi[u]);
+                c[u] = om * __ldg(bm + pb + u);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (pb + u >= p1) break;
+            C xi[V];
+            S::unpack(raw[u], xi);
+            C part = C(0);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                part = fma(xb[e], xi[e], part);
+                acc[e] = fma(-c[u], xbi[u][e], acc[e]);
+            }
+            part = group_sum<G>(part, gmask);
+            if (lane == 0) gs[pb + u] = A.first ? part : gs[pb + u] + part;
+        }
+    }
+    stc<C, V>((C *)A.xbar_out + r * Kp + lane * V, acc);
+}
+
 // ---------------------------------------------------------------------------
 // row i: dL/dval_p = -(omega gs_p + gt_p) / a_ii on every slot, and on the
 // diagonal slot + (qt_i + omega qs_i) / a_ii with q_i = sum_p val_p g_p / a_ii;
@@ -433,6 +491,7 @@ AMGD_ADJ_LAUNCHER(launch_adj_edge, k_edge_bwd)
 AMGD_ADJ_LAUNCHER(launch_adj_xbar_nu, k_xbar_nu)
 AMGD_ADJ_LAUNCHER(launch_adj_gram, k_gram)
 AMGD_ADJ_LAUNCHER(launch_adj_spmm_t, k_spmm_t)
+AMGD_ADJ_LAUNCHER(launch_adj_sweep_sym, k_sweep_sym)
 
 cudaError_t launch_adj_upstream(int storage, const int32_t *rp, const int32_t *col,
                                 const void *ls, const uint8_t *flag, const double *ls_bar,
