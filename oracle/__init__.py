@@ -79,6 +79,10 @@ class Oracle:
         L.orc_adjoint_jacobi.argtypes = [i64, P, P, P, i32, P, i32, P, i32, f64, f64, P, P, P,
                                          P, P]
         L.orc_adjoint_jacobi.restype = ctypes.c_int
+        L.orc_distance_graph.argtypes = [i64, P, P, i32, P, P]
+        L.orc_distance_graph.restype = i64
+        L.orc_edge_ls_graph.argtypes = [i64, P, P, P, P, P, i32, P, i32, P, P, P, P]
+        L.orc_edge_ls_graph.restype = None
         self.L = L
         self.path = path
 
@@ -168,19 +172,53 @@ class Oracle:
         k = self.L.orc_strength_csr(n, _p(rp), _p(col), _p(flag), _p(s_rp), _p(s_col))
         return s_rp, s_col[:k]
 
+    def distance_graph(self, rp, col, d: int):
+        """(row_ptr, col) of the graph G_d of A^d (structural, ascending columns)."""
+        rp = np.ascontiguousarray(rp, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        n = len(rp) - 1
+        total = self.L.orc_distance_graph(n, _p(rp), _p(col), d, None, None)
+        if total < 0:
+            raise MemoryError("oracle distance graph: out of memory")
+        prp = np.empty(n + 1, dtype=np.int64)
+        pcol = np.empty(max(total, 1), dtype=np.int32)
+        self.L.orc_distance_graph(n, _p(rp), _p(col), d, _p(prp), _p(pcol))
+        return prp, pcol[:total]
+
+    def edge_ls_graph(self, rp, col, val, prp, pcol, X, Y, w=None, mode: int = TARGET_RESIDUAL):
+        rp, col, val = _csr(rp, col, val)
+        prp = np.ascontiguousarray(prp, dtype=np.int64)
+        pcol = np.ascontiguousarray(pcol, dtype=np.int32)
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Y = np.ascontiguousarray(Y, dtype=np.float64)
+        n, K = X.shape
+        w = np.ones(K) if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        a = np.empty(len(pcol))
+        ls = np.empty(len(pcol))
+        self.L.orc_edge_ls_graph(n, _p(rp), _p(col), _p(val), _p(prp), _p(pcol), K, _p(w), mode,
+                                 _p(X), _p(Y), _p(a), _p(ls))
+        return a, ls
+
     def build(self, rp, col, val, K: int, seed: int, nu: int, omega: float, theta: float,
               sweep: int = SWEEP_JACOBI, color=None, w=None, mode: int = TARGET_RESIDUAL,
-              X0=None, stream: int = 0):
-        """The whole path: X0 -> nu sweeps -> target -> per-edge LS -> threshold -> CSR."""
+              X0=None, stream: int = 0, d: int = 1):
+        """The whole path: X0 -> nu sweeps -> target -> per-edge LS -> threshold -> CSR.
+        d > 1: fits, threshold and strength graph over the graph G_d of A^d."""
         n = len(rp) - 1
         X = (self.tv_init(n, K, seed, stream) if X0 is None
              else np.ascontiguousarray(X0, np.float64))
         Xnu = self.relax(rp, col, val, X, nu, omega, sweep, color)
         Y = self.target(rp, col, val, Xnu, mode)
-        a, ls = self.edge_ls(rp, col, val, Xnu, Y, w, mode)
-        flag, count = self.threshold(rp, col, ls, theta)
-        s_rp, s_col = self.strength_csr(rp, col, flag)
-        return dict(X=Xnu, Y=Y, a=a, ls=ls, flag=flag, count=count, s_rp=s_rp, s_col=s_col)
+        if d == 1:
+            prp, pcol = np.asarray(rp, np.int64), np.asarray(col, np.int32)
+            a, ls = self.edge_ls(rp, col, val, Xnu, Y, w, mode)
+        else:
+            prp, pcol = self.distance_graph(rp, col, d)
+            a, ls = self.edge_ls_graph(rp, col, val, prp, pcol, Xnu, Y, w, mode)
+        flag, count = self.threshold(prp, pcol, ls, theta)
+        s_rp, s_col = self.strength_csr(prp, pcol, flag)
+        return dict(X=Xnu, Y=Y, a=a, ls=ls, flag=flag, count=count, s_rp=s_rp, s_col=s_col,
+                    prp=prp, pcol=pcol)
 
     def adjoint_jacobi(self, rp, col, val, X0, nu: int, omega: float, theta: float, w=None,
                        mode: int = TARGET_RESIDUAL, ls_bar=None):
@@ -281,9 +319,17 @@ def strength_csr(rp, col, flag):
 
 
 def build(rp, col, val, K, seed, nu, omega, theta, sweep=SWEEP_JACOBI, color=None,
-          w=None, mode=TARGET_RESIDUAL, X0=None, stream=0):
+          w=None, mode=TARGET_RESIDUAL, X0=None, stream=0, d=1):
     return default().build(rp, col, val, K, seed, nu, omega, theta, sweep, color, w, mode,
-                           X0, stream)
+                           X0, stream, d)
+
+
+def distance_graph(rp, col, d):
+    return default().distance_graph(rp, col, d)
+
+
+def edge_ls_graph(rp, col, val, prp, pcol, X, Y, w=None, mode=TARGET_RESIDUAL):
+    return default().edge_ls_graph(rp, col, val, prp, pcol, X, Y, w, mode)
 
 
 def adjoint_jacobi(rp, col, val, X0, nu, omega, theta, w=None, mode=TARGET_RESIDUAL, ls_bar=None):

@@ -23,6 +23,8 @@
  *   6. the strength graph as CSR                  (§4.2)
  *   7. (extension) the reverse pass of steps 2-5 for Jacobi sweeps: the
  *      gradient of a loss on LS with respect to A's values, omega and X0
+ *   8. search depth d > 1: the graph G_d of A^d from the graph of A, and the
+ *      fits of step 4 over its entries (§4.1, Eq. (4.2); §4.2)
  *
  * Rounding conventions (the paper fixes none): every multiply-accumulate of
  * a row sum is one fused multiply-add (C99 fma, a single rounding), sums run
@@ -452,4 +454,116 @@ done:
     free(Xs); free(Y); free(Ybar); free(Xbar); free(Xnext);
     free(a); free(ls); free(lsb); free(flag); free(count);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 8. Search depth d > 1 (§4.1, Eq. (4.2); §4.2: the strength graph M^d).  */
+/*    V_i = { j : (A^d)_ij != 0 }, taken structurally (no numerical       */
+/*    cancellation) and built from the graph of A alone, as the Remark of  */
+/*    §4.2 suggests: j is in V_i iff a walk of length d joins i and j in   */
+/*    the graph of A.  Every row of A holds its diagonal, so walks may     */
+/*    pause and V_i is the set of vertices within d steps of i (i itself   */
+/*    included).  Columns of a row are listed in ascending order.          */
+/*    out_col may be NULL (count only); returns the number of entries, or  */
+/*    -5 when memory runs out.                                             */
+/* ------------------------------------------------------------------------ */
+static int orc_cmp_i32(const void *a, const void *b)
+{
+    const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+int64_t orc_distance_graph(int64_t n, const int64_t *rp, const int32_t *col, int32_t d,
+                           int64_t *out_rp, int32_t *out_col)
+{
+    int64_t *seen = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int32_t *list = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!seen || !list) {
+        free(seen);
+        free(list);
+        return -5;
+    }
+    for (int64_t v = 0; v < n; ++v) seen[v] = -1;
+    int64_t total = 0;
+    if (out_rp) out_rp[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        /* breadth-first search from i, d levels deep */
+        int64_t len = 0, level_begin = 0;
+        seen[i] = i;
+        list[len++] = (int32_t)i;
+        for (int32_t step = 0; step < d; ++step) {
+            const int64_t level_end = len;
+            for (int64_t q = level_begin; q < level_end; ++q) {
+                const int64_t u = list[q];
+                for (int64_t p = rp[u]; p < rp[u + 1]; ++p) {
+                    const int32_t v = col[p];
+                    if (seen[v] != i) {
+                        seen[v] = i;
+                        list[len++] = v;
+                    }
+                }
+            }
+            level_begin = level_end;
+        }
+        if (out_col) {
+            qsort(list, (size_t)len, sizeof(int32_t), orc_cmp_i32);
+            memcpy(out_col + total, list, (size_t)len * sizeof(int32_t));
+        }
+        total += len;
+        if (out_rp) out_rp[i + 1] = total;
+    }
+    free(seen);
+    free(list);
+    return total;
+}
+
+/*
+ * One-point fits over the entries of a pattern P (the graph G_d) with the
+ * target of A (Eq. (4.3): y_i is built from row i of A, whatever d is).
+ * As in step 4, a residual-target row of A with exactly one off-diagonal j1
+ * has y_i = -(a_ij1 / a_ii) x_j1 exactly: the entry (i, j1) gets
+ * a = -a_ij1 / a_ii and LS = 0; every other entry of row i in P is fitted.
+ * Diagonal entries of P get a = 0, ls = NaN.  With P = A this is step 4.
+ */
+void orc_edge_ls_graph(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                       const int64_t *prp, const int32_t *pcol, int32_t K, const double *w,
+                       int32_t mode, const double *X, const double *Y, double *a, double *ls)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t off = 0, p1 = -1;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+            if (col[p] != i) {
+                ++off;
+                p1 = p;
+            }
+        double aii = orc_diag(rp, col, val, i);
+        for (int64_t q = prp[i]; q < prp[i + 1]; ++q) {
+            int64_t j = pcol[q];
+            if (j == i) {
+                a[q] = 0.0;
+                ls[q] = NAN;
+                continue;
+            }
+            if (mode == 0 && off == 1 && j == col[p1]) {
+                a[q] = -val[p1] / aii;
+                ls[q] = 0.0;
+                continue;
+            }
+            const double *y = Y + i * K;
+            const double *x = X + j * K;
+            double sxx = 0.0, syx = 0.0;
+            for (int32_t kappa = 0; kappa < K; ++kappa) {
+                sxx += w[kappa] * x[kappa] * x[kappa];
+                syx += w[kappa] * y[kappa] * x[kappa];
+            }
+            double pij = (sxx == 0.0) ? 0.0 : syx / sxx;
+            double res = 0.0;
+            for (int32_t kappa = 0; kappa < K; ++kappa) {
+                double e = y[kappa] - pij * x[kappa];
+                res += w[kappa] * e * e;
+            }
+            a[q] = pij;
+            ls[q] = res;
+        }
+    }
 }

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import test_oracle_adjoint as adj
+import test_oracle_graph as graph
 import test_oracle_pins as pins
 
 PINS = [pins.pin_philox_numpy, pins.pin_tv_init, pins.pin_jacobi_dense_power,
@@ -19,7 +20,8 @@ PINS = [pins.pin_philox_numpy, pins.pin_tv_init, pins.pin_jacobi_dense_power,
         pins.pin_target, pins.pin_ls_lstsq, pins.pin_ls_brute_force, pins.pin_ls_invariants,
         pins.pin_ls_exact_cases, pins.pin_degree_one_rows, pins.pin_threshold,
         pins.pin_strength_csr, adj.pin_adjoint_fd, adj.pin_adjoint_homogeneity,
-        adj.pin_adjoint_special_cases]
+        adj.pin_adjoint_special_cases, graph.pin_distance_graph_matrix_power,
+        graph.pin_edge_ls_graph]
 
 # (name, text to find, replacement, occurrence index)
 MUTANTS = [
@@ -67,6 +69,13 @@ MUTANTS = [
      "const double *Xc = Xs + (size_t)(s + 1) * nk;", 0),
     ("adj_loss_power", "lsb[p] = -2.0 / (ls[p] * ls[p] * ls[p]);",
      "lsb[p] = -1.0 / (ls[p] * ls[p] * ls[p]);", 0),
+    ("graph_depth_short", "for (int32_t step = 0; step < d; ++step)",
+     "for (int32_t step = 1; step < d; ++step)", 0),
+    ("graph_unsorted", "qsort(list, (size_t)len, sizeof(int32_t), orc_cmp_i32);", ";", 0),
+    ("graph_no_self", "list[len++] = (int32_t)i;", ";", 0),
+    ("graph_exact_rule_any_neighbour", "if (mode == 0 && off == 1 && j == col[p1]) {",
+     "if (mode == 0 && off == 1) {", 0),
+    ("graph_target_from_x", "const double *y = Y + i * K;", "const double *y = X + i * K;", 1),
     ("adj_weights_dropped", "Xbar[j * K + kappa] += -lsb[p] * 2.0 * w[kappa] * a[p] * e;",
      "Xbar[j * K + kappa] += -lsb[p] * 2.0 * a[p] * e;", 0),
 ]
