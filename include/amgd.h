@@ -187,6 +187,10 @@ int amgd_relax(amgd_handle h, int32_t nu, double omega, int sweep_type);
  *     ls[p]   the minimal LS functional LS_ij (NaN on the diagonal)
  *   For the residual target, a row with a single off-diagonal has
  *   y_i = -(a_ij/a_ii) x_j exactly: a = -a_ij/a_ii, LS = 0 are returned.
+ *   With a search depth d > 1 (amgd_set_search_depth) the fits, the
+ *   threshold and every per-slot output follow the entries of the graph G_d
+ *   of A^d instead of A's (nnz_p entries, see amgd_distance_pattern); the
+ *   target is still built from row i of A (Eq. (4.3)).
  *   Mixed precisions compute in FP32 with compensated sums and redo in FP64
  *   an edge whose LS is below 1e-4 * sum_k w_k y_k^2 (cancellation).
  *   Errors: ARG, CUDA.
@@ -194,10 +198,28 @@ int amgd_relax(amgd_handle h, int32_t nu, double omega, int sweep_type);
 int amgd_distances(amgd_handle h, double theta, double *a, double *dist, double *ls, int mem);
 
 /*
- * amgd_strength -- the strength graph M^1 (§4.2) from the flags of the last
+ * amgd_set_search_depth -- d = 1 (default) measures the stored entries of A;
+ *   d > 1 measures every pair (i, j) with (A^d)_ij != 0: the graph G_d of
+ *   §4.1, Eq. (4.2), and the strength graph M^d of §4.2.  The pattern is
+ *   structural (numerical cancellation in A^d is ignored) and is built from
+ *   the graph of A alone (A^d is never formed): because every row holds its
+ *   diagonal, it is every j within d steps of i, i itself included, columns
+ *   ascending.  Setting d drops computed distances and any captured graph.
+ *   1 <= d <= 16.  Errors: ARG, UNSUPPORTED (2^31 entries or more), OOM, CUDA.
+ * amgd_distance_pattern -- the current pattern: row_ptr[n+1] (int64) and
+ *   col[cap] (int32), either may be NULL; *nnz_p (may be NULL) receives its
+ *   entry count.  Synchronous.  Errors: ARG, CAPACITY (cap < nnz_p), CUDA.
+ */
+int amgd_set_search_depth(amgd_handle h, int32_t d);
+int amgd_distance_pattern(amgd_handle h, int64_t *row_ptr, int32_t *col, int64_t cap,
+                          int64_t *nnz_p, int mem);
+
+/*
+ * amgd_strength -- the strength graph M^d (§4.2) from the flags of the last
  *   amgd_distances call: s_row_ptr[n+1] (int64), s_col[cap] (int32), kept
- *   edges row by row in A's slot order.
- *   mem = AMGD_MEM_DEVICE with cap >= E: enqueued without synchronising;
+ *   edges row by row in the slot order of A (d = 1) or of G_d.
+ *   mem = AMGD_MEM_DEVICE with cap >= E_p (the off-diagonal entries of the
+ *     pattern: nnz_p - n; E for d = 1): enqueued without synchronising;
  *     the total is s_row_ptr[n] on the device; *nnz_s (may be NULL) is set
  *     after a synchronisation only if nnz_s is not NULL.
  *   otherwise the call synchronises, sets *nnz_s and returns
@@ -210,7 +232,7 @@ int amgd_strength(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap
 /*
  * amgd_graph_capture -- record one whole build (vector start from `seed`,
  *   nu sweeps, distances for theta, strength CSR into the DEVICE buffers
- *   s_row_ptr[n+1], s_col[cap >= E]) as a CUDA graph owned by the handle;
+ *   s_row_ptr[n+1], s_col[cap >= E_p]) as a CUDA graph owned by the handle;
  *   amgd_graph_launch replays it on the handle's stream.  Replaces any
  *   earlier graph.  Errors: ARG, STATE, CAPACITY (cap < E), CUDA.
  */

@@ -76,6 +76,8 @@ SIGNATURES = {
     "amgd_phase_times": (_int, [_P, _P]),
     "amgd_strength_noalloc": (_int, [_P, _P, _P, _i64, _f64, _P, _P, _i64, _P]),
     "amgd_set_checkpointing": (_int, [_P, _i32]),
+    "amgd_set_search_depth": (_int, [_P, _i32]),
+    "amgd_distance_pattern": (_int, [_P, _P, _P, _i64, _P, _int]),
     "amgd_backward": (_int, [_P, _P, _int, _P, _P, _P]),
     "amgd_backward_scalars": (_int, [_P, _P, _P]),
     "amgd_graph_capture_backward": (_int, [_P, _u64, _i32, _f64, _f64, _P]),
@@ -192,6 +194,7 @@ class Handle:
         check(L.amgd_sizes(self.h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(E),
                            ctypes.byref(k), ctypes.byref(nm)), self.h)
         self.n, self.nnz, self.E, self.K, self.nmat = n.value, nnz.value, E.value, k.value, nm.value
+        self.nnz_p, self.E_p = self.nnz, self.E       # entries of the fit pattern (G_d)
 
     # -- plumbing -------------------------------------------------------------
     def _ck(self, status):
@@ -268,6 +271,23 @@ class Handle:
         p, mem = ptr_mem(val)
         self._ck(lib().amgd_set_values(self.h, p, mem))
 
+    def set_search_depth(self, d):
+        """Measure the graph G_d of A^d (d >= 1); per-slot outputs then have
+        nnz_p entries in the order of distance_pattern()."""
+        self._ck(lib().amgd_set_search_depth(self.h, d))
+        nnz_p = ctypes.c_int64()
+        self._ck(lib().amgd_distance_pattern(self.h, None, None, 0, ctypes.byref(nnz_p),
+                                             AMGD_MEM_HOST))
+        self.nnz_p, self.E_p = nnz_p.value, nnz_p.value - self.n
+
+    def distance_pattern(self):
+        """(row_ptr int64, col int32) of the current fit pattern (host)."""
+        rp = np.empty(self.n + 1, dtype=np.int64)
+        col = np.empty(max(self.nnz_p, 1), dtype=np.int32)
+        self._ck(lib().amgd_distance_pattern(self.h, rp.ctypes.data, col.ctypes.data,
+                                             col.size, None, AMGD_MEM_HOST))
+        return rp, col[:self.nnz_p]
+
     # -- the path -------------------------------------------------------------
     def relax(self, nu, omega, sweep=AMGD_SWEEP_JACOBI):
         self._ck(lib().amgd_relax(self.h, nu, omega, sweep))
@@ -276,7 +296,7 @@ class Handle:
         """Run the edge pass; return dict of requested per-slot outputs (host numpy
         unless `out` supplies device tensors)."""
         if out is None:
-            out = {k: np.empty(self.nnz, dtype=np.float64) for k in want}
+            out = {k: np.empty(self.nnz_p, dtype=np.float64) for k in want}
         ptrs = [ptr_mem(out.get(k))[0] for k in ("a", "dist", "ls")]
         mems = {ptr_mem(v)[1] for v in out.values()} or {AMGD_MEM_HOST}
         assert len(mems) == 1
@@ -288,8 +308,8 @@ class Handle:
         nnz_s = ctypes.c_int64()
         if s_row_ptr is None:
             s_rp = np.empty(self.n + 1, dtype=np.int64)
-            s_col = np.empty(max(self.E, 1), dtype=np.int32)
-            self._ck(lib().amgd_strength(self.h, s_rp.ctypes.data, s_col.ctypes.data, self.E,
+            s_col = np.empty(max(self.E_p, 1), dtype=np.int32)
+            self._ck(lib().amgd_strength(self.h, s_rp.ctypes.data, s_col.ctypes.data, self.E_p,
                                          ctypes.byref(nnz_s), AMGD_MEM_HOST))
             return s_rp, s_col[:nnz_s.value]
         p_rp, mem = ptr_mem(s_row_ptr)

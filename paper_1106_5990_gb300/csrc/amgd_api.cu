@@ -86,8 +86,13 @@ struct amgd_ctx {
     double *adj_part = nullptr;                  // 2 x kAdjReduceBlocks partials + 2 sums
     int32_t *at_rp = nullptr, *at_row = nullptr, *at_slot = nullptr;   // transposed pattern
     int32_t *mirror = nullptr;                   // slot of (j, i) for slot (i, j); symmetric patterns
-    int32_t *edge_tiles = nullptr;               // row tiles of the edge pass
+    int32_t *edge_tiles = nullptr;               // row tiles of the edge pass (over the pattern)
     int32_t n_edge_tiles = 0;
+    // pattern of the fits, threshold and strength graph: the graph G_d of A^d
+    // (search depth d); for d = 1 these alias A's caller-order pattern
+    int32_t depth = 1;
+    int32_t *prp = nullptr, *pcol = nullptr;
+    int64_t nnz_p = 0, E_p = 0;
     bool last_backward_builtin = false;          // the last reverse pass used the built-in loss
     bool graph_is_backward = false;              // the captured graph ends with a reverse pass
     int32_t graph_traj_nu = 0;
@@ -155,6 +160,14 @@ int cuda_fail(amgd_ctx *h, cudaError_t e, const char *where)
     } while (0)
 
 // read and clear the device status word (synchronises the stream)
+// drop a captured graph whose device pointers are about to change
+void drop_graph(amgd_ctx *h)
+{
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    h->graph_timed = false;
+}
+
 int poll_status(amgd_ctx *h)
 {
     uint32_t st = 0;
@@ -426,6 +439,8 @@ int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
     a.count_out = h->count;
     a.defer_count = h->defer_count;
     a.defer_list = h->defer_list;
+    a.prp = h->prp;
+    a.pcol = h->pcol;
     a.tiles = h->edge_tiles;
     a.ntiles = h->n_edge_tiles;
     a.n = (int32_t)h->n;
@@ -446,8 +461,32 @@ int alloc_slot_outputs(amgd_ctx *h, int st)
     dfree(h->ls);
     h->a = h->ls = nullptr;
     const size_t es = st == ST_FP64 ? 8 : 4;
-    CK(h, cudaMalloc(&h->a, (h->nnz ? h->nnz : 1) * es));
-    CK(h, cudaMalloc(&h->ls, (h->nnz ? h->nnz : 1) * es));
+    CK(h, cudaMalloc(&h->a, (h->nnz_p ? h->nnz_p : 1) * es));
+    CK(h, cudaMalloc(&h->ls, (h->nnz_p ? h->nnz_p : 1) * es));
+    return AMGD_OK;
+}
+
+// row tiles of the edge pass over a caller-order pattern row pointer (host)
+int build_edge_tiles(amgd_ctx *h, const std::vector<int32_t> &prp)
+{
+    std::vector<int32_t> tiles(1, 0);
+    int64_t rows = 0, slots = 0;
+    const int64_t n = h->n;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t len = prp[(size_t)i + 1] - prp[(size_t)i];
+        if (rows > 0 && (rows == kEdgeTileRows || slots + len > kEdgeTileSlots)) {
+            tiles.push_back((int32_t)i);
+            rows = slots = 0;
+        }
+        ++rows;
+        slots += len;
+    }
+    if (n > 0) tiles.push_back((int32_t)n);
+    dfree(h->edge_tiles);
+    h->edge_tiles = nullptr;
+    h->n_edge_tiles = (int32_t)tiles.size() - 1;
+    CK(h, dalloc(&h->edge_tiles, tiles.size()));
+    CK(h, cudaMemcpy(h->edge_tiles, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     return AMGD_OK;
 }
 
@@ -548,24 +587,11 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
     if (const char *e = getenv("AMGD_TEST_STAGING_EXTRA_TX")) h->test_extra_tx = (uint32_t)atoi(e);
     if (const char *e = getenv("AMGD_TEST_WAIT_LIMIT")) h->wait_limit = atoll(e);
     if (n) TRY(cudaMemcpy(h->diag_slot, h->h_diag_slot.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
-    {
-        // row tiles of the edge pass (caller order)
-        std::vector<int32_t> tiles(1, 0);
-        int64_t rows = 0, slots = 0;
-        for (int64_t i = 0; i < n; ++i) {
-            const int64_t len = h->h_rp[(size_t)i + 1] - h->h_rp[(size_t)i];
-            if (rows > 0 && (rows == kEdgeTileRows || slots + len > kEdgeTileSlots)) {
-                tiles.push_back((int32_t)i);
-                rows = slots = 0;
-            }
-            ++rows;
-            slots += len;
-        }
-        if (n > 0) tiles.push_back((int32_t)n);
-        h->n_edge_tiles = (int32_t)tiles.size() - 1;
-        TRY(dalloc(&h->edge_tiles, tiles.size()));
-        TRY(cudaMemcpy(h->edge_tiles, tiles.data(), tiles.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    }
+    h->prp = h->rp_o;
+    h->pcol = h->col_o;
+    h->nnz_p = h->nnz;
+    h->E_p = h->E;
+    if ((rc = build_edge_tiles(h, h->h_rp)) != AMGD_OK) return bail(rc);
     h->rp_p = h->rp_o;
     h->col_p = h->col_o;
     h->val64 = h->val_o;
@@ -582,7 +608,7 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
         if (e != cudaSuccess) return bail(cuda_fail(h, e, "launch_diagonal"));
     }
     h->color_start = {0, n};
-    TRY(dalloc(&h->flag, (size_t)h->nnz + 16));   // 16-byte loads past the end
+    TRY(dalloc(&h->flag, (size_t)h->nnz_p + 16));   // 16-byte loads past the end
     TRY(dalloc(&h->defer_count, 1));
     TRY(dalloc(&h->defer_list, (size_t)n));
     TRY(dalloc(&h->count, (size_t)n));
@@ -648,6 +674,8 @@ int amgd_set_precision(amgd_handle h, int storage)
     if (storage != AMGD_FP64 && storage != AMGD_FP32 && storage != AMGD_BF16)
         return fail(h, AMGD_ERR_ARG, "unknown storage precision");
     if (storage == h->storage) return AMGD_OK;
+    CK(h, cudaStreamSynchronize(h->stream));
+    drop_graph(h);                       // vector and output buffers are reallocated
     if (storage != ST_FP64 && !h->val32) {
         CK(h, dalloc(&h->val32, (size_t)h->nnz + 4));
         CK(h, dalloc(&h->val32_o, (size_t)h->nnz + 4));
@@ -739,6 +767,8 @@ int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int 
         perm[(size_t)r] = (int32_t)i;
         inv[(size_t)i] = (int32_t)r;
     }
+    CK(h, cudaStreamSynchronize(h->stream));
+    drop_graph(h);                       // the row order of the sweeps changes
     std::vector<int32_t> rp_p((size_t)n + 1, 0), col_p((size_t)h->nnz);
     for (int64_t r = 0; r < n; ++r) {
         const int32_t o = perm[(size_t)r];
@@ -839,11 +869,9 @@ int amgd_set_values(amgd_handle h, const double *val, int mem)
     CK(h, cudaStreamSynchronize(h->stream));
     if (err & 1u) return fail(h, AMGD_ERR_CSR, "non-finite value");
     if (err & 2u) return fail(h, AMGD_ERR_ZERO_DIAG, "zero diagonal");
-    double *old = h->val_o;
-    h->val_o = h->tmp64;
-    h->tmp64 = old;
-    h->tmp64_len = (size_t)h->nnz + 4;
-    if (!h->perm) h->val64 = h->val_o;
+    // copied in place: device pointers held by a captured graph stay valid
+    CK(h, cudaMemcpyAsync(h->val_o, h->tmp64, h->nnz * sizeof(double), cudaMemcpyDeviceToDevice,
+                          h->stream));
     int rc = permute_values(h);
     if (rc != AMGD_OK) return rc;
     h->have_dist = false;
@@ -874,16 +902,16 @@ int amgd_distances(amgd_handle h, double theta, double *a, double *dist, double 
     double *outs[3] = {a, dist, ls};
     if (mem == AMGD_MEM_DEVICE) {
         if (a || dist || ls)
-            CK(h, launch_export_slots(h->storage, h->a, h->ls, a, dist, ls, h->nnz, h->stream));
+            CK(h, launch_export_slots(h->storage, h->a, h->ls, a, dist, ls, h->nnz_p, h->stream));
         return AMGD_OK;
     }
     for (int k = 0; k < 3; ++k) {
         if (!outs[k]) continue;
-        CK(h, ensure_tmp64(h, (size_t)h->nnz));
+        CK(h, ensure_tmp64(h, (size_t)h->nnz_p));
         CK(h, launch_export_slots(h->storage, h->a, h->ls, k == 0 ? h->tmp64 : nullptr,
                                   k == 1 ? h->tmp64 : nullptr, k == 2 ? h->tmp64 : nullptr,
-                                  h->nnz, h->stream));
-        CK(h, cudaMemcpyAsync(outs[k], h->tmp64, h->nnz * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+                                  h->nnz_p, h->stream));
+        CK(h, cudaMemcpyAsync(outs[k], h->tmp64, h->nnz_p * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
     }
     return poll_status(h);
@@ -896,8 +924,8 @@ int amgd_strength(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap
     if (!h->have_dist) return fail(h, AMGD_ERR_STATE, "amgd_distances must run first");
     if (!s_row_ptr || (!s_col && cap > 0) || cap < 0) return fail(h, AMGD_ERR_ARG, "bad output buffers");
     if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
-    if (mem == AMGD_MEM_DEVICE && cap >= h->E) {
-        CK(h, launch_strength(h->count, h->rp_o, h->col_o, h->flag, (int32_t)h->n, h->tile,
+    if (mem == AMGD_MEM_DEVICE && cap >= h->E_p) {
+        CK(h, launch_strength(h->count, h->prp, h->pcol, h->flag, (int32_t)h->n, h->tile,
                               s_row_ptr, s_col, h->stream));
         if (nnz_s) {
             CK(h, cudaMemcpyAsync(nnz_s, s_row_ptr + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
@@ -906,8 +934,8 @@ int amgd_strength(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap
         return AMGD_OK;
     }
     if (!h->s_rp_tmp) CK(h, dalloc(&h->s_rp_tmp, (size_t)h->n + 1));
-    if (!h->s_col_tmp) CK(h, dalloc(&h->s_col_tmp, (size_t)(h->E > 0 ? h->E : 1)));
-    CK(h, launch_strength(h->count, h->rp_o, h->col_o, h->flag, (int32_t)h->n, h->tile,
+    if (!h->s_col_tmp) CK(h, dalloc(&h->s_col_tmp, (size_t)(h->E_p > 0 ? h->E_p : 1)));
+    CK(h, launch_strength(h->count, h->prp, h->pcol, h->flag, (int32_t)h->n, h->tile,
                           h->s_rp_tmp, h->s_col_tmp, h->stream));
     int64_t total = 0;
     CK(h, cudaMemcpyAsync(&total, h->s_rp_tmp + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
@@ -935,8 +963,8 @@ int amgd_graph_capture(amgd_handle h, uint64_t seed, int32_t nu, double omega, i
         return fail(h, AMGD_ERR_ARG, "unknown sweep type");
     if (sweep_type == AMGD_SWEEP_MCGS && !h->perm)
         return fail(h, AMGD_ERR_STATE, "MCGS needs amgd_set_coloring first");
-    if (!s_row_ptr || (!s_col && h->E > 0)) return fail(h, AMGD_ERR_ARG, "bad output buffers");
-    if (cap < h->E) return fail(h, AMGD_ERR_CAPACITY, "graph capture needs cap >= E");
+    if (!s_row_ptr || (!s_col && h->E_p > 0)) return fail(h, AMGD_ERR_ARG, "bad output buffers");
+    if (cap < h->E_p) return fail(h, AMGD_ERR_CAPACITY, "graph capture needs cap >= the pattern's off-diagonal count");
     if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
@@ -960,7 +988,7 @@ int amgd_graph_capture(amgd_handle h, uint64_t seed, int32_t nu, double omega, i
     if (me == cudaSuccess && rc == AMGD_OK) rc = run_edge(h, theta, h->cap_stream);
     if (me == cudaSuccess && rc == AMGD_OK) me = mark(3);
     if (me == cudaSuccess && rc == AMGD_OK) {
-        cudaError_t e = launch_strength(h->count, h->rp_o, h->col_o, h->flag, (int32_t)h->n,
+        cudaError_t e = launch_strength(h->count, h->prp, h->pcol, h->flag, (int32_t)h->n,
                                         h->tile, s_row_ptr, s_col, h->cap_stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "launch_strength (capture)");
     }
@@ -1178,6 +1206,109 @@ int amgd_graph_launch(amgd_handle h)
     return AMGD_OK;
 }
 
+namespace {
+
+// V_i = { j : (A^d)_ij != 0 } (§4.1, Eq. (4.2)) without forming A^d: every
+// row of A holds its diagonal, so j is in V_i exactly when the graph of A has
+// a path of at most d steps from i to j (d-level breadth-first search;
+// columns ascending).  Returns false if the pattern exceeds `limit` entries.
+bool depth_pattern(const std::vector<int32_t> &rp, const std::vector<int32_t> &col, int64_t n,
+                   int32_t d, int64_t limit, std::vector<int32_t> &prp, std::vector<int32_t> &pcol)
+{
+    std::vector<int32_t> mark((size_t)n, -1), frontier, next;
+    prp.assign((size_t)n + 1, 0);
+    pcol.clear();
+    for (int64_t i = 0; i < n; ++i) {
+        const size_t start = pcol.size();
+        mark[(size_t)i] = (int32_t)i;
+        pcol.push_back((int32_t)i);
+        frontier.assign(1, (int32_t)i);
+        for (int32_t level = 0; level < d && !frontier.empty(); ++level) {
+            next.clear();
+            for (int32_t u : frontier)
+                for (int32_t p = rp[(size_t)u]; p < rp[(size_t)u + 1]; ++p) {
+                    const int32_t v = col[(size_t)p];
+                    if (mark[(size_t)v] != (int32_t)i) {
+                        mark[(size_t)v] = (int32_t)i;
+                        pcol.push_back(v);
+                        next.push_back(v);
+                    }
+                }
+            frontier.swap(next);
+        }
+        std::sort(pcol.begin() + (std::ptrdiff_t)start, pcol.end());
+        if ((int64_t)pcol.size() > limit) return false;
+        prp[(size_t)i + 1] = (int32_t)pcol.size();
+    }
+    return true;
+}
+
+}  // namespace
+
+int amgd_set_search_depth(amgd_handle h, int32_t d)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (d < 1 || d > 16) return fail(h, AMGD_ERR_ARG, "search depth must be in 1..16");
+    if (d == h->depth) return AMGD_OK;
+    std::vector<int32_t> prp, pcol;
+    if (d > 1 && !depth_pattern(h->h_rp, h->h_col, h->n, d, ((int64_t)1 << 31) - 64, prp, pcol))
+        return fail(h, AMGD_ERR_UNSUPPORTED, "the graph of A^d has 2^31 entries or more");
+    CK(h, cudaStreamSynchronize(h->stream));
+    drop_graph(h);
+    if (h->depth > 1) {
+        dfree(h->prp);
+        dfree(h->pcol);
+    }
+    h->prp = h->rp_o;
+    h->pcol = h->col_o;
+    h->nnz_p = h->nnz;
+    h->depth = 1;
+    if (d > 1) {
+        const int64_t nnz_p = (int64_t)pcol.size();
+        int32_t *dp = nullptr, *dc = nullptr;
+        CK(h, dalloc(&dp, (size_t)h->n + 1 + 4));
+        cudaError_t e = dalloc(&dc, (size_t)nnz_p + 16);
+        if (e != cudaSuccess) { dfree(dp); return cuda_fail(h, e, "cudaMalloc(pattern)"); }
+        CK(h, cudaMemcpy(dp, prp.data(), (h->n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(dc, pcol.data(), nnz_p * sizeof(int32_t), cudaMemcpyHostToDevice));
+        h->prp = dp;
+        h->pcol = dc;
+        h->nnz_p = nnz_p;
+        h->depth = d;
+    }
+    h->E_p = h->nnz_p - h->n;
+    int rc = build_edge_tiles(h, d > 1 ? prp : h->h_rp);
+    if (rc != AMGD_OK) return rc;
+    if ((rc = alloc_slot_outputs(h, h->storage)) != AMGD_OK) return rc;
+    dfree(h->flag);
+    h->flag = nullptr;
+    CK(h, dalloc(&h->flag, (size_t)h->nnz_p + 16));
+    dfree(h->s_col_tmp);
+    h->s_col_tmp = nullptr;
+    h->have_dist = false;
+    h->traj_valid = false;
+    return AMGD_OK;
+}
+
+int amgd_distance_pattern(amgd_handle h, int64_t *row_ptr, int32_t *col, int64_t cap,
+                          int64_t *nnz_p, int mem)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
+    if (nnz_p) *nnz_p = h->nnz_p;
+    if (col && cap < h->nnz_p) return fail(h, AMGD_ERR_CAPACITY, "col needs the pattern's entry count");
+    const cudaMemcpyKind k = mem == AMGD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (row_ptr) {
+        std::vector<int32_t> r32((size_t)h->n + 1);
+        CK(h, cudaMemcpy(r32.data(), h->prp, (h->n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        std::vector<int64_t> r64(r32.begin(), r32.end());
+        CK(h, cudaMemcpy(row_ptr, r64.data(), (h->n + 1) * sizeof(int64_t),
+                         mem == AMGD_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice));
+    }
+    if (col && h->nnz_p) CK(h, cudaMemcpy(col, h->pcol, h->nnz_p * sizeof(int32_t), k));
+    return AMGD_OK;
+}
+
 int amgd_set_checkpointing(amgd_handle h, int32_t every)
 {
     if (!h) return AMGD_ERR_ARG;
@@ -1348,6 +1479,8 @@ int run_backward(amgd_ctx *h, const double *lsb_in, double *vb, cudaStream_t s)
 
 int backward_checks(amgd_ctx *h)
 {
+    if (h->depth != 1)
+        return fail(h, AMGD_ERR_UNSUPPORTED, "the reverse pass covers search depth 1");
     if (h->perm)
         return fail(h, AMGD_ERR_UNSUPPORTED, "the reverse pass covers Jacobi sweeps without a coloring");
     if (!h->traj_valid)
@@ -1407,8 +1540,9 @@ int amgd_graph_capture_backward(amgd_handle h, uint64_t seed, int32_t nu, double
     if (nu < 0 || !std::isfinite(omega)) return fail(h, AMGD_ERR_ARG, "nu < 0 or omega not finite");
     if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(h, AMGD_ERR_ARG, "theta must be finite and >= 0");
     if (!val_bar && h->nnz) return fail(h, AMGD_ERR_ARG, "val_bar is NULL");
-    if (h->perm)
-        return fail(h, AMGD_ERR_UNSUPPORTED, "the reverse pass covers Jacobi sweeps without a coloring");
+    if (h->perm || h->depth != 1)
+        return fail(h, AMGD_ERR_UNSUPPORTED,
+                    "the reverse pass covers Jacobi sweeps without a coloring at search depth 1");
     if (h->ckpt_every <= 0) return fail(h, AMGD_ERR_STATE, "amgd_set_checkpointing must come first");
     // every buffer the captured work touches exists before the capture
     {
@@ -1475,6 +1609,10 @@ int amgd_destroy(amgd_handle h)
         dfree(h->rp_p);
         dfree(h->col_p);
         dfree(h->val64);
+    }
+    if (h->depth > 1) {
+        dfree(h->prp);
+        dfree(h->pcol);
     }
     void *ptrs[] = {h->rp_o, h->col_o, h->val_o, h->mat_off, h->diag_slot, h->err_word, h->status,
                     h->diag64, h->diag32, h->val32_o, h->diag64_o, h->diag32_o, h->x_caller,

@@ -151,7 +151,9 @@ struct RelaxArgs {
 };
 
 struct EdgeArgs {                // everything in the caller's numbering
-    const int32_t *rp, *col;     // CSR pattern
+    const int32_t *rp, *col;     // CSR pattern of A (targets)
+    const int32_t *prp, *pcol;   // pattern of the fits: G_d (= rp, col for d = 1); every
+                                 // per-slot output and the tiles follow this pattern
     const void *val;             // values, arithmetic type
     const void *diag;            // diagonal a_ii, arithmetic type
     const double *val64;         // values in FP64 (mixed-path fallback)

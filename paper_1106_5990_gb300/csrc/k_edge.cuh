@@ -169,7 +169,7 @@ __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
     const TS *__restrict__ X = (const TS *)A.x;
     const int Kp = A.Kp;
     const int64_t wr1 = min((int64_t)A.n, wr0 + 32 / G);
-    const int wbase = __ldg(A.rp + wr0), wend = __ldg(A.rp + wr1);
+    const int wbase = __ldg(A.prp + wr0), wend = __ldg(A.prp + wr1);
     const bool staged = wend - wbase <= kWarpSlots;
     C *a_out = (C *)A.a_out;
     C *ls_out = (C *)A.ls_out;
@@ -182,12 +182,13 @@ __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
             for (int e = 0; e < V; ++e) w[t][e] = ((const C *)A.w)[(t * G + lane) * V + e];
     }
 
-    int p0 = 0, p1 = 0;
+    int q0 = 0, q1 = 0;       // the row's entries in the pattern of the fits
     C m = C(INFINITY), diag = C(1);
     bool defer = false;       // a fit of this row cancelled in FP32: redo the row in FP64
     if (active) {
-        p0 = __ldg(A.rp + r);
-        p1 = __ldg(A.rp + r + 1);
+        const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
+        q0 = __ldg(A.prp + r);
+        q1 = __ldg(A.prp + r + 1);
         diag = (C)__ldg((const AV *)A.diag + r);
 
         // ---- 1. target --------------------------------------------------
@@ -214,13 +215,21 @@ __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
                     syy = fma(UW ? y[t][e] : w[t][e] * y[t][e], y[t][e], syy);
             syy = group_sum<G>(syy, gmask);
         }
-        const int off = p1 - p0 - 1;
+        // a residual-target row of A with one off-diagonal j1: y_i is exactly
+        // -(a_ij1 / a_ii) x_j1
+        int j1 = -1;
+        C v1 = C(0);
+        if (A.target == 0 && p1 - p0 == 2) {
+            const int pj = __ldg(col + p0) == r ? p0 + 1 : p0;
+            j1 = __ldg(col + pj);
+            v1 = (C)__ldg(val + pj);
+        }
 
         // ---- 2. one-point LS per off-diagonal -----------------------------
-        for (int pb = p0; pb < p1; pb += U) {
+        for (int pb = q0; pb < q1; pb += U) {
             int jj[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) jj[u] = (pb + u < p1) ? __ldg(col + pb + u) : -1;
+            for (int u = 0; u < U; ++u) jj[u] = (pb + u < q1) ? __ldg(A.pcol + pb + u) : -1;
             uint4 raw[U][NV];
 #pragma unroll
             for (int u = 0; u < U; ++u)
@@ -236,8 +245,8 @@ __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
                 if (jj[u] == r) {
                     a_ = C(0);
                     ls_ = C(NAN);
-                } else if (A.target == 0 && off == 1) {
-                    a_ = -(C)__ldg(val + p) / diag;
+                } else if (jj[u] == j1) {
+                    a_ = -v1 / diag;
                     ls_ = C(0);
                 } else {
                     // x_j is unpacked from the gathered bits once per use, so only one
@@ -276,8 +285,8 @@ __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
     const C theta = (C)A.theta;
     int cnt = 0;
     if (active) {
-        for (int p = p0 + lane; p < p1; p += G) {
-            const int j = __ldg(col + p);
+        for (int p = q0 + lane; p < q1; p += G) {
+            const int j = __ldg(A.pcol + p);
             const C l = staged ? ls_s[p - wbase] : ls_out[p];
             const int strong = (j != r) && (l == C(0) || theta * l < m);
             if (staged) fl_s[p - wbase] = (uint8_t)strong;
@@ -341,7 +350,9 @@ struct EdgeTileLayout {
     static constexpr int RP = MN + TR * (int)sizeof(M);                 // TR + 1 slot offsets
     static constexpr int CN = RP + (TR + 1) * 4;                        // TR strong counts
     static constexpr int DF = CN + TR * 4;                              // TR defer marks
-    static constexpr int SR = DF + TR * 4;                              // slot -> local row (u8)
+    static constexpr int J1 = DF + TR * 4;                              // TR exact-rule neighbours
+    static constexpr int V1 = (J1 + TR * 4 + 7) & ~7;                   // TR their values a_ij1
+    static constexpr int SR = V1 + TR * (int)sizeof(C);                 // slot -> local row (u8)
     static constexpr int BYTES = SR + kEdgeTileSlots;
 };
 
@@ -366,6 +377,8 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
     int32_t *rps = reinterpret_cast<int32_t *>(esm + L::RP);
     int32_t *cnt = reinterpret_cast<int32_t *>(esm + L::CN);
     int32_t *dfr = reinterpret_cast<int32_t *>(esm + L::DF);
+    int32_t *j1s = reinterpret_cast<int32_t *>(esm + L::J1);
+    C *v1s = reinterpret_cast<C *>(esm + L::V1);
     uint8_t *srow = esm + L::SR;
 
     const int32_t R0 = __ldg(A.tiles + blockIdx.x), R1 = __ldg(A.tiles + blockIdx.x + 1);
@@ -376,7 +389,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
     const TS *__restrict__ X = (const TS *)A.x;
     const C *__restrict__ wv = (const C *)A.w;
 
-    for (int q = threadIdx.x; q <= nr; q += kEdgeThreads) rps[q] = __ldg(A.rp + R0 + q);
+    for (int q = threadIdx.x; q <= nr; q += kEdgeThreads) rps[q] = __ldg(A.prp + R0 + q);
     for (int q = threadIdx.x; q < nr; q += kEdgeThreads) {
         dg[q] = (C)__ldg((const AV *)A.diag + R0 + q);
         rmin[q] = MB::kInf;
@@ -393,9 +406,22 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
                                          : (((1u << G) - 1u) << ((threadIdx.x % 32) / G * G));
         for (int rl = threadIdx.x / G; rl < nr; rl += kEdgeThreads / G) {
             const int64_t r = R0 + rl;
-            const int p0 = rps[rl], p1 = rps[rl + 1];
             if (!single)
-                for (int p = p0 + lane; p < p1; p += G) srow[p - S0] = (uint8_t)rl;
+                for (int q = rps[rl] + lane; q < rps[rl + 1]; q += G) srow[q - S0] = (uint8_t)rl;
+            const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);   // row of A
+            if (lane == 0) {
+                // a residual-target row of A with one off-diagonal j1: y_i is
+                // exactly -(a_ij1 / a_ii) x_j1
+                int j1 = -1;
+                C v1 = C(0);
+                if (A.target == 0 && p1 - p0 == 2) {
+                    const int pj = __ldg(col + p0) == r ? p0 + 1 : p0;
+                    j1 = __ldg(col + pj);
+                    v1 = (C)__ldg(val + pj);
+                }
+                j1s[rl] = j1;
+                v1s[rl] = v1;
+            }
             C y[NV][V];
 #pragma unroll
             for (int t = 0; t < NV; ++t) S::unpack(ldg16(X + r * KP + (t * G + lane) * V), y[t]);
@@ -432,13 +458,13 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
     for (int p = S0 + threadIdx.x; p < S1; p += kEdgeThreads) {
         const int rl = single ? 0 : srow[p - S0];
         const int64_t r = R0 + rl;
-        const int j = __ldg(col + p);
+        const int j = __ldg(A.pcol + p);
         C a_, ls_;
         if (j == r) {
             a_ = C(0);
             ls_ = C(NAN);
-        } else if (A.target == 0 && rps[rl + 1] - rps[rl] == 2) {
-            a_ = -(C)__ldg(val + p) / dg[rl];           // y_i = -(a_ij/a_ii) x_j exactly
+        } else if (j == j1s[rl]) {
+            a_ = -v1s[rl] / dg[rl];                     // y_i = -(a_ij/a_ii) x_j exactly
             ls_ = C(0);
         } else {
             const TS *xj = X + (int64_t)j * KP;
@@ -527,10 +553,15 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; q < count; q += warps) {
         const int64_t r = A.defer_list[q];
-        const int p0 = A.rp[r], p1 = A.rp[r + 1];
+        const int p0 = A.rp[r], p1 = A.rp[r + 1];         // row of A: target
+        const int q0 = A.prp[r], q1 = A.prp[r + 1];       // entries of the fits
         double diag = 1.0;
-        for (int p = p0; p < p1; ++p)
+        int j1 = -1;
+        double v1 = 0.0;
+        for (int p = p0; p < p1; ++p) {
             if (A.col[p] == r) diag = A.val64[p];
+            else if (A.target == 0 && p1 - p0 == 2) { j1 = A.col[p]; v1 = A.val64[p]; }
+        }
         const double d = 1.0 / diag;
         double y[2], w[2];
         for (int h = 0; h < 2; ++h) {
@@ -542,18 +573,17 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
                 for (int p = p0; p < p1; ++p) acc = fma(A.val64[p], elem64(X + (int64_t)A.col[p] * Kp + k), acc);
             y[h] = (A.target == 0) ? fma(-d, acc, xi) : xi;
         }
-        const int off = p1 - p0 - 1;
         double m = INFINITY;
         C *a_out = (C *)A.a_out;
         C *ls_out = (C *)A.ls_out;
-        for (int p = p0; p < p1; ++p) {
-            const int64_t j = A.col[p];
+        for (int p = q0; p < q1; ++p) {
+            const int64_t j = A.pcol[p];
             double a64, ls64;
             if (j == r) {
                 a64 = 0.0;
                 ls64 = NAN;
-            } else if (A.target == 0 && off == 1) {
-                a64 = -A.val64[p] / diag;
+            } else if (j == j1) {
+                a64 = -v1 / diag;
                 ls64 = 0.0;
             } else {
                 double xj[2], sxx = 0.0, syx = 0.0;
@@ -584,9 +614,9 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
         }
         __syncwarp();
         int cnt = 0;
-        for (int p = p0 + lane; p < p1; p += 32) {
+        for (int p = q0 + lane; p < q1; p += 32) {
             const double l = (double)ls_out[p];
-            const int strong = (A.col[p] != r) && (l == 0.0 || A.theta * l < m);
+            const int strong = (A.pcol[p] != r) && (l == 0.0 || A.theta * l < m);
             A.flag_out[p] = (uint8_t)strong;
             cnt += strong;
         }
