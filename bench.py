@@ -287,9 +287,12 @@ def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_cloc
 
 
 def run_e2e(h, mats, w, sweep, steps, adjoint=None):
-    """Through the public API with host buffers: per step the matrix values
-    are copied from pinned host memory (amgd_set_values) and the strength CSR
-    is read back to pinned host memory (amgd_strength, host mode)."""
+    """Through the public API with host buffers.  Per step: the matrix values
+    are copied from pinned host memory (amgd_set_values: staged, checked,
+    written in place), the build captured by run_gpu_arm is replayed
+    (amgd_graph_launch) and the strength CSR is read back to pinned host
+    memory (amgd_strength, host mode).  With a reverse pass: set_values, the
+    eager calls and dL/dvalues written to pinned host memory (amgd_backward)."""
     import ctypes
     import torch
     from paper_1106_5990_gb300 import amgd
@@ -308,12 +311,14 @@ def run_e2e(h, mats, w, sweep, steps, adjoint=None):
     for _ in range(steps):
         t0 = time.perf_counter()
         h.set_values(val_h)
-        h.init_vectors(w["seed"])
-        h.relax(w["nu"], w["omega"], sweep)
-        amgd.check(L.amgd_distances(h.h, w["theta"], None, None, None, amgd.AMGD_MEM_DEVICE), h.h)
         if adjoint:
+            h.init_vectors(w["seed"])
+            h.relax(w["nu"], w["omega"], sweep)
+            amgd.check(L.amgd_distances(h.h, w["theta"], None, None, None, amgd.AMGD_MEM_DEVICE),
+                       h.h)
             h.backward(out=vb_h)                 # dL/dvalues to pinned host memory
         else:
+            h.graph_launch()
             amgd.check(L.amgd_strength(h.h, s_rp.data_ptr(), s_col.data_ptr(), s_col.numel(),
                                        ctypes.byref(nnz_s), amgd.AMGD_MEM_HOST), h.h)
         times.append(time.perf_counter() - t0)
@@ -592,7 +597,8 @@ def main():
                    "d2h_bytes_per_step": e["d2h"], "steps": e2e_steps,
                    "api": ("amgd_set_values(host) + init + relax (recorded) + distances + "
                            "amgd_backward(host dL/dvalues)") if adj else
-                          "amgd_set_values(host) + init + relax + distances + strength(host)"}
+                          "amgd_set_values(host) + amgd_graph_launch (captured build) + "
+                          "amgd_strength(host)"}
     line["clocks"] = {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} \
         if r["clocks"] else None
     if rank == 0 and not args.no_cpu:

@@ -37,6 +37,7 @@ struct amgd_ctx {
     uint32_t test_extra_tx = 0;                  // test hook, see amgd_create
     // device: row-permuted matrix (aliases of the caller arrays without coloring)
     int32_t *rp_p = nullptr, *col_p = nullptr, *perm = nullptr;
+    int32_t *slot_perm = nullptr;                // permuted slot of every caller slot
     double *val64 = nullptr;
     float *val32 = nullptr;
     double *diag64 = nullptr;                    // permuted diagonal
@@ -265,33 +266,19 @@ int upload_weights(amgd_ctx *h)
     return AMGD_OK;
 }
 
-// (re)build the FP64 and FP32 permuted value arrays from h->val_o, and the
-// permuted diagonal
-int permute_values_only(amgd_ctx *h);
-int permute_values(amgd_ctx *h)
+// Values from src (caller order; NULL: h->val_o itself) into every copy the
+// kernels read -- the caller FP64 array, the FP32 copies and, with a
+// coloring, the row-permuted arrays -- in one coalesced pass, then the
+// diagonals in caller and permuted order.
+int permute_values(amgd_ctx *h, const double *src = nullptr)
 {
-    const int rc = permute_values_only(h);
-    if (rc != AMGD_OK) return rc;
-    CK(h, launch_diagonal(h->rp_p, h->col_p, h->val64, h->diag64, h->diag32, (int32_t)h->n, h->stream));
-    CK(h, launch_diagonal(h->rp_o, h->col_o, h->val_o, h->diag64_o, h->diag32_o, (int32_t)h->n, h->stream));
-    if (h->val32_o && h->val32_o != h->val32)
-        CK(h, launch_permute_values(h->val_o, h->rp_o, nullptr, h->rp_o, nullptr, h->val32_o,
-                                    (int32_t)h->n, h->stream));
-    return AMGD_OK;
-}
-
-int permute_values_only(amgd_ctx *h)
-{
-    if (h->perm) {
-        CK(h, launch_permute_values(h->val_o, h->rp_o, h->perm, h->rp_p, h->val64, h->val32,
-                                    (int32_t)h->n, h->stream));
-    } else {
-        if (h->val64 != h->val_o)
-            CK(h, cudaMemcpyAsync(h->val64, h->val_o, h->nnz * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-        if (h->val32)
-            CK(h, launch_permute_values(h->val_o, h->rp_o, nullptr, h->rp_o, nullptr, h->val32,
-                                        (int32_t)h->n, h->stream));
-    }
+    const bool in_place = src == nullptr;
+    float *v32o = (h->val32_o && h->val32_o != h->val32) ? h->val32_o : nullptr;
+    double *vp64 = h->perm ? h->val64 : nullptr;        // without a coloring val64 is val_o
+    CK(h, launch_scatter_values(in_place ? h->val_o : src, h->nnz, h->perm ? h->slot_perm : nullptr,
+                                in_place ? nullptr : h->val_o, v32o, vp64, h->val32, h->stream));
+    CK(h, launch_diag_values(h->val_o, h->diag_slot, h->perm, (int32_t)h->n, h->diag64_o,
+                             h->diag32_o, h->diag64, h->diag32, h->stream));
     return AMGD_OK;
 }
 
@@ -795,6 +782,17 @@ int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int 
     CK(h, cudaMemcpy(h->perm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->rp_p, rp_p.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->col_p, col_p.data(), h->nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    {
+        std::vector<int32_t> sp((size_t)h->nnz);
+        for (int64_t r = 0; r < n; ++r) {
+            const int32_t o = perm[(size_t)r];
+            for (int32_t k = 0; k < h->h_rp[(size_t)o + 1] - h->h_rp[(size_t)o]; ++k)
+                sp[(size_t)(h->h_rp[(size_t)o] + k)] = rp_p[(size_t)r] + k;
+        }
+        if (!h->slot_perm) CK(h, dalloc(&h->slot_perm, (size_t)(h->nnz ? h->nnz : 1)));
+        if (h->nnz)
+            CK(h, cudaMemcpy(h->slot_perm, sp.data(), h->nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     int rc = permute_values(h);
     if (rc != AMGD_OK) return rc;
     CK(h, launch_import(h->storage, h->tmp64, h->x[h->cur], h->perm, (int32_t)n, h->K,
@@ -869,10 +867,8 @@ int amgd_set_values(amgd_handle h, const double *val, int mem)
     CK(h, cudaStreamSynchronize(h->stream));
     if (err & 1u) return fail(h, AMGD_ERR_CSR, "non-finite value");
     if (err & 2u) return fail(h, AMGD_ERR_ZERO_DIAG, "zero diagonal");
-    // copied in place: device pointers held by a captured graph stay valid
-    CK(h, cudaMemcpyAsync(h->val_o, h->tmp64, h->nnz * sizeof(double), cudaMemcpyDeviceToDevice,
-                          h->stream));
-    int rc = permute_values(h);
+    // written in place: device pointers held by a captured graph stay valid
+    int rc = permute_values(h, h->tmp64);
     if (rc != AMGD_OK) return rc;
     h->have_dist = false;
     h->traj_valid = false;
@@ -1609,6 +1605,7 @@ int amgd_destroy(amgd_handle h)
         dfree(h->rp_p);
         dfree(h->col_p);
         dfree(h->val64);
+        dfree(h->slot_perm);
     }
     if (h->depth > 1) {
         dfree(h->prp);

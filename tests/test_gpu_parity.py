@@ -307,6 +307,39 @@ def test_graph_capture_equals_stepwise():
         assert np.array_equal(g_col[:g_rp[-1]], s_col)
 
 
+def test_graph_replay_after_set_values():
+    """amgd_set_values writes the new values in place, so a captured build
+    replayed afterwards uses them (FP64 against the oracle on the new
+    values, host and device sources, colored and plain handles)."""
+    import torch
+    N = 48
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
+    rng = np.random.default_rng(3)
+    val2 = val * rng.uniform(0.8, 1.25, len(val))
+    color = inputs.red_black(N)
+    for colored in (False, True):
+        sweep = amgd.AMGD_SWEEP_MCGS if colored else amgd.AMGD_SWEEP_JACOBI
+        osweep = oracle.SWEEP_MCGS if colored else oracle.SWEEP_JACOBI
+        omega = 1.0 if colored else 2.0 / 3.0
+        want = oracle.build(rp, col, val2, 16, 2, 5, omega, 0.5, osweep,
+                            color if colored else None)
+        with amgd.Handle(rp, col, val, 16, 2) as h:
+            if colored:
+                h.set_coloring(color)
+            d_rp = torch.empty(N * N + 1, dtype=torch.int64, device="cuda")
+            d_col = torch.empty(h.E, dtype=torch.int32, device="cuda")
+            h.graph_capture(2, 5, omega, sweep, 0.5, d_rp, d_col)
+            h.graph_launch()
+            for src in (val2, torch.from_numpy(val2).cuda()):
+                h.set_values(src)
+                h.graph_launch()
+                torch.cuda.synchronize()
+                s_rp = d_rp.cpu().numpy()
+                got = dict(X=h.get_vectors(), s_rp=s_rp, s_col=d_col[: s_rp[-1]].cpu().numpy())
+                got.update(h.distances(0.5))     # same vectors: the graph's distances
+                compare_fp64(rp, col, val2, got, want, 0.5)
+
+
 # --------------------------------------------------------------------------- API states
 def test_state_errors_and_roundtrips():
     rp, col, val = inputs.poisson2d_5pt(20)
