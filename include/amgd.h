@@ -244,7 +244,8 @@ int amgd_graph_launch(amgd_handle h);
  * Kernel shapes and the autotuner.  A row of test vectors is P = Kp/V
  *   sixteen-byte vectors (V = 2, 4, 8 elements for FP64, FP32, BF16); a
  *   shape spreads them over G lanes with NV vectors per lane (G*NV = P,
- *   NV in {1,2,4}) and gathers U nonzeros per batch (U in {4,8}).  For the
+ *   NV in {1,2,4}) and gathers U nonzeros per batch (U in {4,8}; the
+ *   distance pass also takes U = 2).  For the
  *   relaxation, staged selects the kernel: 0 direct; 1 persistent, each
  *   tile's CSR slice copied into shared memory with TMA bulk copies ahead of
  *   use (waits bounded to about one second; a wait that runs out makes the

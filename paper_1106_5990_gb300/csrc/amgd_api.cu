@@ -127,7 +127,7 @@ bool shape_ok(int st, int K, Shape sh)
 {
     const int P = P_of(st, K);
     if (sh.NV != 1 && sh.NV != 2 && sh.NV != 4) return false;
-    if (sh.U != 4 && sh.U != 8) return false;
+    if (sh.U != 2 && sh.U != 4 && sh.U != 8) return false;     // U = 2: edge pass only
     if (sh.G < 1 || sh.G > 32 || (sh.G & (sh.G - 1))) return false;
     if (sh.stage < 0 || sh.stage > 2) return false;
     return sh.G * sh.NV == P;
@@ -1106,7 +1106,8 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
                 if (line.compare(0, key.size(), key) == 0 && line.size() > key.size() &&
                     line[key.size()] == ';' && parse_shape(line, "relax", r) &&
                     parse_shape(line, "edge", e) && shape_ok(h->storage, h->K, r) &&
-                    shape_ok(h->storage, h->K, e))
+                    shape_ok(h->storage, h->K, e) && e.stage <= 1 &&
+                    relax_shape_available(h->storage, r))
                     found = true;       // the last matching line wins
             }
             fclose(f);
@@ -1145,7 +1146,7 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
     // edge pass: stage 0 row kernel, stage 1 tile kernel
     for (int stage : {0, 1})
         for (int NV : {1, 2, 4})
-            for (int U : {4, 8}) {
+            for (int U : {2, 4, 8}) {
                 const Shape c{P / NV, NV, U, stage};
                 if (P % NV != 0 || !shape_ok(h->storage, h->K, c)) continue;
                 float ms = 0.f;

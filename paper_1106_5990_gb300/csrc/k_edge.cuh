@@ -663,6 +663,7 @@ template <class TS, int G, int NV, bool UW>
 cudaError_t dispatch_u(int stage, int U, const EdgeArgs &a, cudaStream_t s)
 {
     switch (U) {
+    case 2: return go<TS, G, NV, 2, UW>(stage, a, s);
     case 4: return go<TS, G, NV, 4, UW>(stage, a, s);
     case 8: return go<TS, G, NV, 8, UW>(stage, a, s);
     }

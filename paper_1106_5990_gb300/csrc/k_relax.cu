@@ -623,6 +623,7 @@ int pipe_smem(int G, int NV)
 
 bool relax_shape_available(int storage, Shape sh)
 {
+    if (sh.U != 4 && sh.U != 8) return false;   // the sweeps gather 4 or 8 entries per batch
     if (!sh.stage) return true;
     if (sh.stage == 2 && (sh.U != 4 || sh.G < 2)) return false;   // no batch size; RG <= 16
     int b = 0;

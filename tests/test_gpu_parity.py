@@ -425,6 +425,31 @@ def test_kernel_shapes_agree(prec, K):
             h.set_kernel_shape(amgd.AMGD_KERNEL_RELAX, 3, 1, 4)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_edge_batch_of_two(prec):
+    """The distance pass also compiles a gather batch of 2 (both kernels):
+    same distances as the default shape (FP64 against the oracle)."""
+    rp, col, val = inputs.aniso2d_9pt(40, 1e-3, math.pi / 6)
+    want = oracle.build(rp, col, val, 16, 4, 3, 0.7, 0.5)
+    for stage in (0, 1):
+        with amgd.Handle(rp, col, val, 16, 4) as h:
+            h.set_precision(prec)
+            G, NV, _, _ = h.kernel_shape(amgd.AMGD_KERNEL_EDGE)
+            h.set_kernel_shape(amgd.AMGD_KERNEL_EDGE, G, NV, 2, stage)
+            with pytest.raises(amgd.AmgdError):
+                h.set_kernel_shape(amgd.AMGD_KERNEL_RELAX, G, NV, 2, 0)
+            h.relax(3, 0.7)
+            X = h.get_vectors()
+            out = h.distances(0.5)
+            s_rp, s_col = h.strength()
+        if prec == "fp64":
+            compare_fp64(rp, col, val, dict(X=X, s_rp=s_rp, s_col=s_col, **out), want, 0.5)
+        else:
+            off = ~np.isnan(want["ls"])
+            rel = np.abs(out["ls"][off] - want["ls"][off]) / want["ls"][off]
+            assert np.median(rel) <= 5e-3
+
+
 def test_autotune_and_cache(tmp_path):
     N = 64
     rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
