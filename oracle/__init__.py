@@ -83,6 +83,8 @@ class Oracle:
         L.orc_distance_graph.restype = i64
         L.orc_edge_ls_graph.argtypes = [i64, P, P, P, P, P, i32, P, i32, P, P, P, P]
         L.orc_edge_ls_graph.restype = None
+        L.orc_ls_interp.argtypes = [i64, i32, P, P, P, P, P, P, i32, f64, P, P, P, P, i64]
+        L.orc_ls_interp.restype = i64
         self.L = L
         self.path = path
 
@@ -198,6 +200,28 @@ class Oracle:
         self.L.orc_edge_ls_graph(n, _p(rp), _p(col), _p(val), _p(prp), _p(pcol), K, _p(w), mode,
                                  _p(X), _p(Y), _p(a), _p(ls))
         return a, ls
+
+    def ls_interp(self, X, Y, prp, pcol, coarse, caliber: int, gamma: float = 1.5, w=None):
+        """Least-squares interpolation (§4.3): P as (p_rp, p_col, p_val) and
+        the chosen LS per row, from vectors X, targets Y, the neighbourhood
+        pattern (prp, pcol) and the coarse mask."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Y = np.ascontiguousarray(Y, dtype=np.float64)
+        prp = np.ascontiguousarray(prp, dtype=np.int64)
+        pcol = np.ascontiguousarray(pcol, dtype=np.int32)
+        coarse = np.ascontiguousarray(coarse, dtype=np.uint8)
+        n, K = X.shape
+        w = np.ones(K) if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        cap = n * max(caliber, 1)
+        p_rp = np.empty(n + 1, dtype=np.int64)
+        p_col = np.empty(max(cap, 1), dtype=np.int32)
+        p_val = np.empty(max(cap, 1), dtype=np.float64)
+        ls = np.empty(n, dtype=np.float64)
+        total = self.L.orc_ls_interp(n, K, _p(w), _p(X), _p(Y), _p(prp), _p(pcol), _p(coarse),
+                                     caliber, gamma, _p(p_rp), _p(p_col), _p(p_val), _p(ls), cap)
+        if total < 0:
+            raise MemoryError("oracle interpolation: out of memory or capacity")
+        return p_rp, p_col[:total], p_val[:total], ls
 
     def build(self, rp, col, val, K: int, seed: int, nu: int, omega: float, theta: float,
               sweep: int = SWEEP_JACOBI, color=None, w=None, mode: int = TARGET_RESIDUAL,
@@ -322,6 +346,10 @@ def build(rp, col, val, K, seed, nu, omega, theta, sweep=SWEEP_JACOBI, color=Non
           w=None, mode=TARGET_RESIDUAL, X0=None, stream=0, d=1):
     return default().build(rp, col, val, K, seed, nu, omega, theta, sweep, color, w, mode,
                            X0, stream, d)
+
+
+def ls_interp(X, Y, prp, pcol, coarse, caliber, gamma=1.5, w=None):
+    return default().ls_interp(X, Y, prp, pcol, coarse, caliber, gamma, w)
 
 
 def distance_graph(rp, col, d):

@@ -25,6 +25,8 @@
  *      gradient of a loss on LS with respect to A's values, omega and X0
  *   8. search depth d > 1: the graph G_d of A^d from the graph of A, and the
  *      fits of step 4 over its entries (§4.1, Eq. (4.2); §4.2)
+ *   9. (extension) least-squares interpolation of a given caliber over sets
+ *      of coarse points, with the size penalty gamma (§4.3)
  *
  * Rounding conventions (the paper fixes none): every multiply-accumulate of
  * a row sum is one fused multiply-add (C99 fma, a single rounding), sums run
@@ -566,4 +568,160 @@ void orc_edge_ls_graph(int64_t n, const int64_t *rp, const int32_t *col, const d
             ls[q] = res;
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* 9. Least-squares interpolation (§4.3; the functional of Eqs. (3.1),     */
+/*    (3.2) with a set W of coarse points).  For a fine row i (coarse[i] =  */
+/*    0) the candidates are the coarse points of V_i in the pattern prp /  */
+/*    pcol (the graph G_{d_LS}); every subset W of at most c candidates is */
+/*    fitted: p_W solves the weighted normal equations                     */
+/*      sum_b G_ab p_b = b_a,  G_ab = sum_k w x_a x_b,  b_a = sum_k w y x_a  */
+/*    (Gaussian elimination with partial pivoting; a pivot below 1e-13 of  */
+/*    the largest diagonal entry marks the set singular and it is skipped),*/
+/*    and LS_W = sum_k w (y_i - sum_{a in W} p_a x_a)^2.  For each size m   */
+/*    the first set (lexicographic over the ascending candidate list) with */
+/*    the smallest LS_W is kept.  Sizes are then compared with the penalty  */
+/*    of §4.3 on LS normalised by S_yy = sum_k w y_i^2: starting from the   */
+/*    empty set (normalised LS 1), size m replaces the current size m' <  m */
+/*    when LS_m / S_yy < (LS_m' / S_yy)^(gamma (m - m')).  (S_yy = 0 keeps   */
+/*    the empty set.)  A coarse row interpolates itself: (i, 1).            */
+/*    Outputs: P as CSR (p_rp[n+1], p_col, p_val; columns ascending) and   */
+/*    the chosen LS per row (0 for coarse rows).  Returns the entry count, */
+/*    -7 when it exceeds cap (p_rp still written), -5 when out of memory.  */
+/* ------------------------------------------------------------------------ */
+static int orc_solve_small(int m, double *G, double *b, double *p)
+{
+    /* G (m x m, row-major) p = b, partial pivoting; G and b are destroyed */
+    double dmax = 0.0;
+    for (int a = 0; a < m; ++a)
+        if (fabs(G[a * m + a]) > dmax) dmax = fabs(G[a * m + a]);
+    for (int k = 0; k < m; ++k) {
+        int piv = k;
+        for (int a = k + 1; a < m; ++a)
+            if (fabs(G[a * m + k]) > fabs(G[piv * m + k])) piv = a;
+        if (!(fabs(G[piv * m + k]) > 1e-13 * dmax)) return -1;
+        if (piv != k) {
+            for (int c2 = 0; c2 < m; ++c2) {
+                double t = G[k * m + c2];
+                G[k * m + c2] = G[piv * m + c2];
+                G[piv * m + c2] = t;
+            }
+            double t = b[k];
+            b[k] = b[piv];
+            b[piv] = t;
+        }
+        for (int a = k + 1; a < m; ++a) {
+            double f = G[a * m + k] / G[k * m + k];
+            for (int c2 = k; c2 < m; ++c2) G[a * m + c2] -= f * G[k * m + c2];
+            b[a] -= f * b[k];
+        }
+    }
+    for (int k = m - 1; k >= 0; --k) {
+        double s = b[k];
+        for (int c2 = k + 1; c2 < m; ++c2) s -= G[k * m + c2] * p[c2];
+        p[k] = s / G[k * m + k];
+    }
+    return 0;
+}
+
+int64_t orc_ls_interp(int64_t n, int32_t K, const double *w, const double *X, const double *Y,
+                      const int64_t *prp, const int32_t *pcol, const uint8_t *coarse, int32_t c,
+                      double gamma, int64_t *p_rp, int32_t *p_col, double *p_val, double *ls_out,
+                      int64_t cap)
+{
+    enum { MAXC = 8 };
+    if (c > MAXC) c = MAXC;
+    int64_t total = 0;
+    int64_t maxcand = 1;
+    for (int64_t i = 0; i < n; ++i)
+        if (prp[i + 1] - prp[i] > maxcand) maxcand = prp[i + 1] - prp[i];
+    int32_t *cand = (int32_t *)malloc((size_t)maxcand * sizeof(int32_t));
+    if (!cand) return -5;
+    p_rp[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t bestset[MAXC + 1][MAXC];
+        double bestp[MAXC + 1][MAXC];
+        double bestls[MAXC + 1];
+        int have[MAXC + 1];
+        int chosen = 0;
+        if (coarse[i]) {
+            if (total < cap) {
+                p_col[total] = (int32_t)i;
+                p_val[total] = 1.0;
+            }
+            ++total;
+            p_rp[i + 1] = total;
+            if (ls_out) ls_out[i] = 0.0;
+            continue;
+        }
+        const double *y = Y + i * K;
+        int nc = 0;
+        for (int64_t q = prp[i]; q < prp[i + 1]; ++q)
+            if (coarse[pcol[q]]) cand[nc++] = pcol[q];
+        double syy = 0.0;
+        for (int32_t k = 0; k < K; ++k) syy += w[k] * y[k] * y[k];
+        for (int m = 0; m <= c; ++m) have[m] = 0;
+        have[0] = 1;
+        bestls[0] = syy;
+        for (int m = 1; m <= c && m <= nc; ++m) {
+            int idx[MAXC];
+            for (int a = 0; a < m; ++a) idx[a] = a;
+            for (;;) {
+                double G[MAXC * MAXC], b[MAXC], p[MAXC];
+                for (int a = 0; a < m; ++a) {
+                    const double *xa = X + (int64_t)cand[idx[a]] * K;
+                    double s = 0.0;
+                    for (int32_t k = 0; k < K; ++k) s += w[k] * y[k] * xa[k];
+                    b[a] = s;
+                    for (int bb = 0; bb < m; ++bb) {
+                        const double *xb = X + (int64_t)cand[idx[bb]] * K;
+                        double g = 0.0;
+                        for (int32_t k = 0; k < K; ++k) g += w[k] * xa[k] * xb[k];
+                        G[a * m + bb] = g;
+                    }
+                }
+                if (orc_solve_small(m, G, b, p) == 0) {
+                    double res = 0.0;
+                    for (int32_t k = 0; k < K; ++k) {
+                        double e = y[k];
+                        for (int a = 0; a < m; ++a) e -= p[a] * X[(int64_t)cand[idx[a]] * K + k];
+                        res += w[k] * e * e;
+                    }
+                    if (!have[m] || res < bestls[m]) {
+                        have[m] = 1;
+                        bestls[m] = res;
+                        for (int a = 0; a < m; ++a) {
+                            bestset[m][a] = cand[idx[a]];
+                            bestp[m][a] = p[a];
+                        }
+                    }
+                }
+                /* next combination in lexicographic order */
+                int a = m - 1;
+                while (a >= 0 && idx[a] == nc - m + a) --a;
+                if (a < 0) break;
+                ++idx[a];
+                for (int bb = a + 1; bb < m; ++bb) idx[bb] = idx[bb - 1] + 1;
+            }
+        }
+        if (syy > 0.0) {
+            for (int m = 1; m <= c; ++m) {
+                if (!have[m]) continue;
+                double cur = bestls[chosen] / syy;
+                if (bestls[m] / syy < pow(cur, gamma * (double)(m - chosen))) chosen = m;
+            }
+        }
+        for (int a = 0; a < chosen; ++a) {
+            if (total < cap) {
+                p_col[total] = bestset[chosen][a];
+                p_val[total] = bestp[chosen][a];
+            }
+            ++total;
+        }
+        p_rp[i + 1] = total;
+        if (ls_out) ls_out[i] = bestls[chosen];
+    }
+    free(cand);
+    return total > cap ? -7 : total;
 }

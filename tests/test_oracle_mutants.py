@@ -13,6 +13,7 @@ import pytest
 import oracle
 import test_oracle_adjoint as adj
 import test_oracle_graph as graph
+import test_oracle_interp as interp
 import test_oracle_pins as pins
 
 PINS = [pins.pin_philox_numpy, pins.pin_tv_init, pins.pin_jacobi_dense_power,
@@ -21,7 +22,8 @@ PINS = [pins.pin_philox_numpy, pins.pin_tv_init, pins.pin_jacobi_dense_power,
         pins.pin_ls_exact_cases, pins.pin_degree_one_rows, pins.pin_threshold,
         pins.pin_strength_csr, adj.pin_adjoint_fd, adj.pin_adjoint_homogeneity,
         adj.pin_adjoint_special_cases, graph.pin_distance_graph_matrix_power,
-        graph.pin_edge_ls_graph]
+        graph.pin_edge_ls_graph, interp.pin_interp_brute_force, interp.pin_interp_single_point,
+        interp.pin_interp_monotone_and_exact]
 
 # (name, text to find, replacement, occurrence index)
 MUTANTS = [
@@ -76,6 +78,15 @@ MUTANTS = [
     ("graph_exact_rule_any_neighbour", "if (mode == 0 && off == 1 && j == col[p1]) {",
      "if (mode == 0 && off == 1) {", 0),
     ("graph_target_from_x", "const double *y = Y + i * K;", "const double *y = X + i * K;", 1),
+    ("interp_penalty_absolute", "pow(cur, gamma * (double)(m - chosen))",
+     "pow(cur, gamma * (double)m)", 0),
+    ("interp_not_normalised", "if (bestls[m] / syy < pow(cur,", "if (bestls[m] < pow(cur,", 0),
+    ("interp_ties_last", "if (!have[m] || res < bestls[m]) {", "if (!have[m] || res <= bestls[m]) {", 0),
+    ("interp_residual_sign", "for (int a = 0; a < m; ++a) e -= p[a] * X[", "for (int a = 0; a < m; ++a) e += p[a] * X[", 0),
+    ("interp_gram_unweighted", "for (int32_t k = 0; k < K; ++k) g += w[k] * xa[k] * xb[k];",
+     "for (int32_t k = 0; k < K; ++k) g += xa[k] * xb[k];", 0),
+    ("interp_fine_candidates", "if (coarse[pcol[q]]) cand[nc++] = pcol[q];",
+     "if (pcol[q] != i) cand[nc++] = pcol[q];", 0),
     ("adj_weights_dropped", "Xbar[j * K + kappa] += -lsb[p] * 2.0 * w[kappa] * a[p] * e;",
      "Xbar[j * K + kappa] += -lsb[p] * 2.0 * a[p] * e;", 0),
 ]
