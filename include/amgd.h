@@ -285,6 +285,36 @@ int amgd_enable_phase_timing(amgd_handle h, int enable);
 int amgd_phase_times(amgd_handle h, float *ms);
 
 /*
+ * amgd_ls_interpolation -- least-squares interpolation of caliber c (§4.3;
+ *   the functional of Eq. (3.1), or of Eq. (3.2) for the residual target,
+ *   over a set W of coarse points), from the current vectors (after
+ *   amgd_relax) and the current target and weights.
+ *   coarse[n] (coarse_mem): 1 for a coarse point, 0 for a fine point.
+ *   For a fine row i the candidates are the coarse points among the entries
+ *   of row i of the current pattern (A for search depth 1, the graph G_d of
+ *   A^d after amgd_set_search_depth(d): the d_LS-ring of Eq. (4.5)); at most
+ *   32 per row.  Every subset W with |W| <= c is fitted (weighted normal
+ *   equations, Gaussian elimination with partial pivoting; a set whose
+ *   pivot falls below 1e-13 of the largest diagonal entry is skipped) and
+ *   scored by LS_W = sum_k w_k (y_ik - sum_{j in W} p_j x_jk)^2; the first
+ *   set in lexicographic order with the smallest LS is kept for each size.
+ *   Sizes then compete with the penalty of §4.3 on LS / S_yy (S_yy =
+ *   sum_k w_k y_ik^2): starting from the empty set (1), size m replaces the
+ *   current size m' < m when LS_m / S_yy < (LS_m' / S_yy)^(gamma (m - m')).
+ *   A coarse row interpolates itself (weight 1).  Computed in FP64 from the
+ *   vectors widened exactly, with the rounding order of the definition.
+ *   Outputs (mem): p_row_ptr[n+1] (int64); p_col[cap] (int32, ascending per
+ *   row) and p_val[cap] (double) -- both NULL to query the size; ls[n] (may
+ *   be NULL): the chosen LS per row (0 for coarse rows).  *nnz_p (may be
+ *   NULL): the entry count.  1 <= c <= 4, gamma >= 0.  Synchronous.
+ *   Errors: ARG, CAPACITY (cap too small; p_row_ptr still written),
+ *   UNSUPPORTED (a row with more than 32 candidates, K > 64), CUDA.
+ */
+int amgd_ls_interpolation(amgd_handle h, const uint8_t *coarse, int coarse_mem, int32_t caliber,
+                          double gamma, int64_t *p_row_ptr, int32_t *p_col, double *p_val,
+                          int64_t cap, int64_t *nnz_p, double *ls, int mem);
+
+/*
  * Reverse pass.  The paper differentiates nothing; these calls give the
  * gradient of a scalar loss on the LS values with respect to the values of A
  * and the Jacobi weight omega, by the chain rule through the steps of §3

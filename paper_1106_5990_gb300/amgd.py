@@ -77,6 +77,7 @@ SIGNATURES = {
     "amgd_strength_noalloc": (_int, [_P, _P, _P, _i64, _f64, _P, _P, _i64, _P]),
     "amgd_set_checkpointing": (_int, [_P, _i32]),
     "amgd_set_search_depth": (_int, [_P, _i32]),
+    "amgd_ls_interpolation": (_int, [_P, _P, _int, _i32, _f64, _P, _P, _P, _i64, _P, _P, _int]),
     "amgd_distance_pattern": (_int, [_P, _P, _P, _i64, _P, _int]),
     "amgd_backward": (_int, [_P, _P, _int, _P, _P, _P]),
     "amgd_backward_scalars": (_int, [_P, _P, _P]),
@@ -317,6 +318,21 @@ class Handle:
         cap = s_col.numel() if _is_torch(s_col) else len(s_col)
         self._ck(lib().amgd_strength(self.h, p_rp, p_col, cap, None, mem))
         return s_row_ptr, s_col
+
+    def ls_interpolation(self, coarse, caliber, gamma=1.5):
+        """Least-squares interpolation (host numpy): (p_row_ptr, p_col, p_val, ls)."""
+        c = coarse if _is_torch(coarse) else _host(coarse, np.uint8)
+        pc, cmem = ptr_mem(c)
+        p_rp = np.empty(self.n + 1, dtype=np.int64)
+        ls = np.empty(self.n, dtype=np.float64)
+        cap = self.n * caliber
+        p_col = np.empty(max(cap, 1), dtype=np.int32)
+        p_val = np.empty(max(cap, 1), dtype=np.float64)
+        nnz = ctypes.c_int64()
+        self._ck(lib().amgd_ls_interpolation(self.h, pc, cmem, caliber, gamma, p_rp.ctypes.data,
+                                             p_col.ctypes.data, p_val.ctypes.data, cap,
+                                             ctypes.byref(nnz), ls.ctypes.data, AMGD_MEM_HOST))
+        return p_rp, p_col[:nnz.value], p_val[:nnz.value], ls
 
     # -- reverse pass ---------------------------------------------------------
     def set_checkpointing(self, every):

@@ -87,6 +87,13 @@ struct amgd_ctx {
     double *adj_part = nullptr;                  // 2 x kAdjReduceBlocks partials + 2 sums
     int32_t *at_rp = nullptr, *at_row = nullptr, *at_slot = nullptr;   // transposed pattern
     int32_t *mirror = nullptr;                   // slot of (j, i) for slot (i, j); symmetric patterns
+    // least-squares interpolation working buffers
+    uint8_t *ip_coarse = nullptr;
+    int32_t *ip_sel_col = nullptr, *ip_cnt = nullptr;
+    double *ip_sel_val = nullptr, *ip_ls = nullptr;
+    int64_t *ip_rp = nullptr;
+    void *ip_out = nullptr;
+    size_t ip_out_bytes = 0;
     int32_t *edge_tiles = nullptr;               // row tiles of the edge pass (over the pattern)
     int32_t n_edge_tiles = 0;
     // pattern of the fits, threshold and strength graph: the graph G_d of A^d
@@ -1306,6 +1313,93 @@ int amgd_distance_pattern(amgd_handle h, int64_t *row_ptr, int32_t *col, int64_t
     return AMGD_OK;
 }
 
+int amgd_ls_interpolation(amgd_handle h, const uint8_t *coarse, int coarse_mem, int32_t caliber,
+                          double gamma, int64_t *p_row_ptr, int32_t *p_col, double *p_val,
+                          int64_t cap, int64_t *nnz_p, double *ls, int mem)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (caliber < 1 || caliber > kInterpMaxCaliber) return fail(h, AMGD_ERR_ARG, "caliber must be in 1..4");
+    if (!(gamma >= 0.0) || !std::isfinite(gamma)) return fail(h, AMGD_ERR_ARG, "gamma must be finite and >= 0");
+    if (h->K > 64) return fail(h, AMGD_ERR_UNSUPPORTED, "interpolation needs K <= 64");
+    if ((!coarse && h->n) || !p_row_ptr) return fail(h, AMGD_ERR_ARG, "NULL coarse mask or row_ptr");
+    if ((coarse_mem != AMGD_MEM_HOST && coarse_mem != AMGD_MEM_DEVICE) ||
+        (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE))
+        return fail(h, AMGD_ERR_ARG, "bad mem");
+    cudaStream_t s = h->stream;
+    const int64_t n = h->n;
+    // working buffers (kept by the handle)
+    if (!h->ip_coarse) {
+        CK(h, dalloc(&h->ip_coarse, (size_t)n + 16));
+        CK(h, dalloc(&h->ip_sel_col, (size_t)n * kInterpMaxCaliber + 1));
+        CK(h, dalloc(&h->ip_sel_val, (size_t)n * kInterpMaxCaliber + 1));
+        CK(h, dalloc(&h->ip_cnt, (size_t)n + 8));
+        CK(h, dalloc(&h->ip_ls, (size_t)n + 1));
+        CK(h, dalloc(&h->ip_rp, (size_t)n + 1));
+    }
+    CK(h, cudaMemcpyAsync(h->ip_coarse, coarse, (size_t)n,
+                          coarse_mem == AMGD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemsetAsync(h->ip_cnt, 0, ((size_t)n + 8) * sizeof(int32_t), s));
+    const void *xc = h->x[h->cur];
+    if (h->perm) {
+        if (!h->x_caller) return fail(h, AMGD_ERR_STATE, "caller-order vector buffer missing");
+        CK(h, launch_unpermute(h->storage, h->x[h->cur], h->x_caller, h->perm, (int32_t)n,
+                               Kp_of(h->storage, h->K), s));
+        xc = h->x_caller;
+    }
+    InterpArgs a;
+    a.rp = h->rp_o;
+    a.col = h->col_o;
+    a.val64 = h->val_o;
+    a.prp = h->prp;
+    a.pcol = h->pcol;
+    a.coarse = h->ip_coarse;
+    a.x = xc;
+    a.w64 = h->w64;
+    a.sel_col = h->ip_sel_col;
+    a.sel_val = h->ip_sel_val;
+    a.cnt = h->ip_cnt;
+    a.ls = h->ip_ls;
+    a.err = h->err_word;
+    a.n = (int32_t)n;
+    a.K = h->K;
+    a.Kp = Kp_of(h->storage, h->K);
+    a.target = h->target;
+    a.caliber = caliber;
+    a.gamma = gamma;
+    CK(h, cudaMemsetAsync(h->err_word, 0, sizeof(uint32_t), s));
+    CK(h, launch_ls_interp(h->storage, a, s));
+    CK(h, launch_row_ptr(h->ip_cnt, (int32_t)n, h->tile, h->ip_rp, s));
+    uint32_t err = 0;
+    int64_t total = 0;
+    CK(h, cudaMemcpyAsync(&err, h->err_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaMemcpyAsync(&total, h->ip_rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (err & 1u)
+        return fail(h, AMGD_ERR_UNSUPPORTED, "a fine row has more than 32 coarse candidates");
+    if (nnz_p) *nnz_p = total;
+    if ((p_col || p_val) && cap < total)
+        return fail(h, AMGD_ERR_CAPACITY, "P needs " + std::to_string(total) + " entries");
+    const cudaMemcpyKind k = mem == AMGD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(h, cudaMemcpyAsync(p_row_ptr, h->ip_rp, (n + 1) * sizeof(int64_t), k, s));
+    if (ls) CK(h, cudaMemcpyAsync(ls, h->ip_ls, n * sizeof(double), k, s));
+    if (p_col && p_val && total > 0) {
+        int32_t *dc = p_col;
+        double *dv = p_val;
+        if (mem == AMGD_MEM_HOST) {
+            CK(h, ensure_buf(&h->ip_out, h->ip_out_bytes, (size_t)total * (sizeof(int32_t) + sizeof(double))));
+            dv = (double *)h->ip_out;
+            dc = (int32_t *)(dv + total);
+        }
+        CK(h, launch_interp_fill(h->ip_rp, h->ip_sel_col, h->ip_sel_val, (int32_t)n, dc, dv, s));
+        if (mem == AMGD_MEM_HOST) {
+            CK(h, cudaMemcpyAsync(p_col, dc, total * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            CK(h, cudaMemcpyAsync(p_val, dv, total * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+    }
+    CK(h, cudaStreamSynchronize(s));
+    return poll_status(h);
+}
+
 int amgd_set_checkpointing(amgd_handle h, int32_t every)
 {
     if (!h) return AMGD_ERR_ARG;
@@ -1618,7 +1712,9 @@ int amgd_destroy(amgd_handle h)
                     h->val32, h->x[0], h->x[1],
                     h->w64, h->w32, h->a, h->ls, h->flag, h->count, h->tile, h->s_rp_tmp,
                     h->s_col_tmp, h->tmp64, h->ckpt, h->seg, h->adj_vec, h->adj_slot, h->lsb,
-                    h->adj_part, h->at_rp, h->at_row, h->at_slot, h->edge_tiles, h->mirror};
+                    h->adj_part, h->at_rp, h->at_row, h->at_slot, h->edge_tiles, h->mirror,
+                    h->ip_coarse, h->ip_sel_col, h->ip_cnt, h->ip_sel_val, h->ip_ls, h->ip_rp,
+                    h->ip_out};
     for (void *p : ptrs) dfree(p);
     delete h;
     return AMGD_OK;

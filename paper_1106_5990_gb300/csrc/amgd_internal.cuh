@@ -294,6 +294,35 @@ cudaError_t launch_adj_reduce(const double *partial, int32_t nblocks, int32_t ns
                               cudaStream_t s);
 constexpr int kAdjReduceBlocks = 608;   // 4 per SM
 
+// row_ptr[n+1] (int64) = exclusive scan of count[n] (int32, 16-byte aligned,
+// padded to a multiple of 4); tile_sum holds n / kTileRows + 2 entries
+cudaError_t launch_row_ptr(const int32_t *count, int32_t n, int32_t *tile_sum, int64_t *row_ptr,
+                           cudaStream_t s);
+
+// least-squares interpolation (k_interp.cu)
+constexpr int kInterpMaxCaliber = 4;
+constexpr int kInterpMaxCand = 32;
+struct InterpArgs {
+    const int32_t *rp, *col;        // A (targets), caller order
+    const double *val64;            // A's values (FP64)
+    const int32_t *prp, *pcol;      // neighbourhood pattern (candidates: its coarse entries)
+    const uint8_t *coarse;          // n, 1 = coarse
+    const void *x;                  // vectors, caller order, storage type, row stride Kp
+    const double *w64;              // weights (FP64, Kp)
+    int32_t *sel_col;               // n x kInterpMaxCaliber chosen columns
+    double *sel_val;                // n x kInterpMaxCaliber weights
+    int32_t *cnt;                   // n chosen sizes (coarse rows: 1)
+    double *ls;                     // n chosen LS
+    uint32_t *err;                  // bit 1: a row had more than kInterpMaxCand candidates
+    int32_t n, K, Kp, target, caliber;
+    double gamma;
+};
+cudaError_t launch_ls_interp(int storage, const InterpArgs &a, cudaStream_t s);
+// P as CSR from the fixed-stride selections and row_ptr
+cudaError_t launch_interp_fill(const int64_t *row_ptr, const int32_t *sel_col,
+                               const double *sel_val, int32_t n, int32_t *p_col, double *p_val,
+                               cudaStream_t s);
+
 // message returned by amgd_last_error(NULL) on the calling host thread
 void set_thread_error(const std::string &msg);
 

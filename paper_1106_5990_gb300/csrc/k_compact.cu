@@ -153,7 +153,48 @@ k_compact(const int32_t *__restrict__ count, const int32_t *__restrict__ rp,
     }
 }
 
+// row pointers only (first half of k_compact)
+__global__ void __launch_bounds__(kCompactThreads)
+k_row_ptr(const int32_t *__restrict__ count, int32_t n, const int32_t *__restrict__ tile_off,
+          int64_t *__restrict__ row_ptr)
+{
+    __shared__ int sm[33];
+    const int64_t row0 = (int64_t)blockIdx.x * kTileRows;
+    const int64_t row_end = min((int64_t)n, row0 + kTileRows);
+    const int64_t off = tile_off[blockIdx.x];
+    int c[kRowsPerThread];
+    int mine = 0;
+    const int64_t rbase = row0 + (int64_t)threadIdx.x * kRowsPerThread;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        c[k] = (rbase + k < row_end) ? count[rbase + k] : 0;
+        mine += c[k];
+    }
+    int total;
+    int run = block_exclusive_scan<kCompactThreads>(mine, total, sm);
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k) {
+        if (rbase + k < row_end) row_ptr[rbase + k] = off + run;
+        run += c[k];
+    }
+    if (row_end == n && threadIdx.x == 0) row_ptr[n] = off + total;
+}
+
 }  // namespace
+
+cudaError_t launch_row_ptr(const int32_t *count, int32_t n, int32_t *tile_sum, int64_t *row_ptr,
+                           cudaStream_t s)
+{
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
+    const int ntiles = (int)(((int64_t)n + kTileRows - 1) / kTileRows);
+    k_tile_sums<<<ntiles, kSumThreads, 0, s>>>(count, n, tile_sum);
+    k_tile_scan<<<1, 1024, 0, s>>>(tile_sum, ntiles);
+    k_row_ptr<<<ntiles, kCompactThreads, 0, s>>>(count, n, tile_sum, row_ptr);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_strength(const int32_t *count, const int32_t *rp_orig, const int32_t *col_orig,
                             const uint8_t *flag, int32_t n, int32_t *tile_sum,

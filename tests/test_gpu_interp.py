@@ -1,0 +1,81 @@
+"""Least-squares interpolation (§4.3) on the GPU against the oracle: the
+GPU evaluates every candidate set in FP64 with the rounding order of the
+definition, so on the same (stored) vectors the chosen sets, weights and LS
+values equal the oracle's bit for bit -- for every storage precision (the
+vectors are widened exactly), with and without a coloring, search depth 1
+and 2, caliber 1 to 4, gamma 1.5 and 0."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1106_5990_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+amgd = pytest.importorskip("paper_1106_5990_gb300.amgd")
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1106_5990_gb300 import _build
+    _build.build()
+
+
+def _case(name):
+    if name == "aniso5_24":
+        N = 24
+        rp, col, val = inputs.aniso2d_5pt(N, 1e-2)
+        coarse = inputs.red_black(N).astype(np.uint8) ^ 1          # red points coarse
+        return rp, col, val, coarse, inputs.red_black(N)
+    rp, col, val = inputs.random_csr(500, 3.0, 13, symmetric_pattern=True)   # <= 26 candidates at d = 2
+    coarse = (np.random.default_rng(1).random(500) < 0.35).astype(np.uint8)
+    return rp, col, val, coarse, None
+
+
+@pytest.mark.parametrize("name", ["aniso5_24", "random_500"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+@pytest.mark.parametrize("d,c,gamma", [(1, 2, 1.5), (2, 3, 1.5), (2, 4, 0.0), (2, 1, 1.5)])
+def test_interp_matches_oracle(name, prec, d, c, gamma):
+    rp, col, val, coarse, color = _case(name)
+    K = 8
+    w = np.random.default_rng(4).uniform(0.5, 2.0, K)
+    with amgd.Handle(rp, col, val, K, 9) as h:
+        h.set_precision(prec)
+        h.set_weights(w)
+        if color is not None:
+            h.set_coloring(color)
+            h.relax(3, 1.0, amgd.AMGD_SWEEP_MCGS)
+        else:
+            h.relax(3, 0.7, amgd.AMGD_SWEEP_JACOBI)
+        h.set_search_depth(d)
+        X = h.get_vectors()
+        prp, pcol = h.distance_pattern()
+        got = h.ls_interpolation(coarse, c, gamma)
+    Y = oracle.target(rp, col, val, X)
+    want = oracle.ls_interp(X, Y, prp, pcol, coarse, c, gamma, w)
+    assert np.array_equal(got[0], want[0])
+    assert np.array_equal(got[1], want[1])
+    assert np.array_equal(got[2], want[2])
+    assert np.array_equal(got[3], want[3])
+    # coarse rows interpolate themselves
+    for i in np.nonzero(coarse)[0][:50]:
+        assert got[1][got[0][i]:got[0][i + 1]].tolist() == [i]
+
+
+def test_interp_too_many_candidates():
+    rp, col, val = inputs.graph_laplacian(300, 12.0, 2)
+    with amgd.Handle(rp, col, val, 8, 1) as h:
+        h.relax(2, 0.7)
+        h.set_search_depth(3)
+        coarse = np.ones(300, dtype=np.uint8)
+        coarse[::7] = 0
+        with pytest.raises(amgd.AmgdError) as e:
+            h.ls_interpolation(coarse, 2)
+        assert e.value.status == amgd.AMGD_ERR_UNSUPPORTED
+        with pytest.raises(amgd.AmgdError) as e:
+            h.ls_interpolation(coarse, 5)
+        assert e.value.status == amgd.AMGD_ERR_ARG
