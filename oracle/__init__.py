@@ -13,6 +13,8 @@ algebraic distances measure of AMG strength of connection"):
 * residual-corrected LS target y_i = x_i - r_i / a_ii -- Eqs. (3.2), (4.1)
 * one-point LS fit and algebraic distance r_ij = 1/LS_ij -- §4.1, Eq. (4.3)
 * strength graph r_ij > theta max_k r_ik -- §4.2, Eq. (4.4)
+* least-squares interpolation of a given caliber -- §4.3
+* compatible-relaxation coarsening -- §3.2, Eqs. (3.4), (3.5); Algorithm 1
 """
 from __future__ import annotations
 
@@ -85,6 +87,9 @@ class Oracle:
         L.orc_edge_ls_graph.restype = None
         L.orc_ls_interp.argtypes = [i64, i32, P, P, P, P, P, P, i32, f64, P, P, P, P, i64]
         L.orc_ls_interp.restype = i64
+        L.orc_cr_coarsen.argtypes = [i64, P, P, P, P, P, P, i32, f64, P, i32, i32, f64, f64, f64,
+                                     i32, u64, P, P]
+        L.orc_cr_coarsen.restype = i32
         self.L = L
         self.path = path
 
@@ -223,6 +228,33 @@ class Oracle:
             raise MemoryError("oracle interpolation: out of memory or capacity")
         return p_rp, p_col[:total], p_val[:total], ls
 
+    def cr_coarsen(self, rp, col, val, prp, pcol, ls, theta: float = 0.5, nu: int = 5,
+                   omega: float = 1.0, sweep: int = SWEEP_JACOBI, color=None,
+                   delta: float = 0.7, tol: float = 0.5, max_sets: int = 20, seed: int = 0,
+                   coarse0=None):
+        """Compatible-relaxation coarsening (§3.2, §4.2, Algorithm 1): the
+        coarse mask C and the convergence estimate rho_f of every stage, from
+        A (F-relaxation), the fit pattern (prp, pcol) and its per-slot LS."""
+        rp, col, val = _csr(rp, col, val)
+        prp = np.ascontiguousarray(prp, dtype=np.int64)
+        pcol = np.ascontiguousarray(pcol, dtype=np.int32)
+        ls = np.ascontiguousarray(ls, dtype=np.float64)
+        n = len(rp) - 1
+        coarse = (np.zeros(n, dtype=np.uint8) if coarse0 is None
+                  else np.array(coarse0, dtype=np.uint8, copy=True))
+        if sweep == SWEEP_MCGS:
+            color = np.ascontiguousarray(color, dtype=np.int32)
+            ncol = int(color.max()) + 1 if n else 1
+        else:
+            color, ncol = np.zeros(max(n, 1), dtype=np.int32), 1
+        rho = np.empty(max_sets + 1, dtype=np.float64)
+        m = self.L.orc_cr_coarsen(n, _p(rp), _p(col), _p(val), _p(prp), _p(pcol), _p(ls), sweep,
+                                  omega, _p(color), ncol, nu, theta, delta, tol, max_sets,
+                                  seed, _p(coarse), _p(rho))
+        if m < 0:
+            raise MemoryError("oracle CR coarsening: out of memory")
+        return coarse, rho[:m]
+
     def build(self, rp, col, val, K: int, seed: int, nu: int, omega: float, theta: float,
               sweep: int = SWEEP_JACOBI, color=None, w=None, mode: int = TARGET_RESIDUAL,
               X0=None, stream: int = 0, d: int = 1):
@@ -350,6 +382,12 @@ def build(rp, col, val, K, seed, nu, omega, theta, sweep=SWEEP_JACOBI, color=Non
 
 def ls_interp(X, Y, prp, pcol, coarse, caliber, gamma=1.5, w=None):
     return default().ls_interp(X, Y, prp, pcol, coarse, caliber, gamma, w)
+
+
+def cr_coarsen(rp, col, val, prp, pcol, ls, theta=0.5, nu=5, omega=1.0, sweep=SWEEP_JACOBI,
+               color=None, delta=0.7, tol=0.5, max_sets=20, seed=0, coarse0=None):
+    return default().cr_coarsen(rp, col, val, prp, pcol, ls, theta, nu, omega, sweep, color,
+                                delta, tol, max_sets, seed, coarse0)
 
 
 def distance_graph(rp, col, d):

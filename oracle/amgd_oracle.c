@@ -27,6 +27,9 @@
  *      fits of step 4 over its entries (§4.1, Eq. (4.2); §4.2)
  *   9. (extension) least-squares interpolation of a given caliber over sets
  *      of coarse points, with the size penalty gamma (§4.3)
+ *  10. compatible-relaxation coarsening: F-relaxation, the convergence
+ *      estimate, candidates and independent sets of the strength graph on F
+ *      (§3.2, §4.2, Algorithm 1)
  *
  * Rounding conventions (the paper fixes none): every multiply-accumulate of
  * a row sum is one fused multiply-add (C99 fma, a single rounding), sums run
@@ -724,4 +727,189 @@ int64_t orc_ls_interp(int64_t n, int32_t K, const double *w, const double *X, co
     }
     free(cand);
     return total > cap ? -7 : total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 10. Compatible-relaxation coarsening (§3.2 Eqs. (3.4), (3.5); §4.2 Eq.   */
+/*     (4.4); Algorithm 1 with the candidate measure of the Remark after    */
+/*     it).  One stage:                                                     */
+/*     (a) nu F-relaxation sweeps of the homogeneous system from the        */
+/*         constant start u = 1 on F (Eq. (3.4)): the sweep of section 2    */
+/*         (weighted Jacobi, or multicolor Gauss-Seidel) applied to the     */
+/*         rows of F only, with u = 0 held on C, which is                   */
+/*         u_f <- (I - M_ff^{-1} A_ff) u_f;                                 */
+/*     (b) the convergence estimate of Eq. (3.5) in the max norm,           */
+/*         rho_f = (||u^nu|| / ||u^0||)^(1/nu)  (0 when F is empty);         */
+/*     (c) stop when rho_f <= delta, or when max_sets sets were added;      */
+/*     (d) candidates Z = { i in F : sigma_i = |u_i| / ||u^nu|| > tol };    */
+/*     (e) the strength graph M on F (Eq. (4.4) restricted to i, j in F,    */
+/*         the maximum over the neighbours k in F): slot (i, j) of the      */
+/*         pattern is strong iff i, j in F, j != i and LS_ij = 0 or         */
+/*         theta LS_ij < min_k LS_ik;                                       */
+/*     (f) an independent set of Z in M (edges in either direction): the   */
+/*         greedy set in decreasing priority, where the priority of i is    */
+/*         lambda_i = |{ j in Z : (j, i) strong }| (the number of           */
+/*         candidates that depend strongly on i, as in the classical first  */
+/*         pass), then a random 64-bit key (word 0 of Philox4x64-10 with    */
+/*         counter (i, stage, 1, 0) and key (seed, 0)), then the smaller    */
+/*         index;                                                           */
+/*     (g) C <- C + the set; the next stage starts again at (a).            */
+/*     coarse[n] is C_0 on entry and C on exit.  rho[] gets one estimate    */
+/*     per stage (at most max_sets + 1).  nu >= 1.  Returns the number of   */
+/*     estimates, or -5 when out of memory.                                 */
+/* ------------------------------------------------------------------------ */
+static int orc_cr_before(int32_t la, uint64_t ra, int64_t a, int32_t lb, uint64_t rb, int64_t b)
+{
+    /* 1 if vertex a comes before vertex b in the greedy order */
+    if (la != lb) return la > lb;
+    if (ra != rb) return ra > rb;
+    return a < b;
+}
+
+static const int32_t *orc_cr_lam;
+static const uint64_t *orc_cr_key;
+
+static int orc_cr_cmp(const void *pa, const void *pb)
+{
+    int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
+    if (a == b) return 0;
+    return orc_cr_before(orc_cr_lam[a], orc_cr_key[a], a, orc_cr_lam[b], orc_cr_key[b], b) ? -1 : 1;
+}
+
+int32_t orc_cr_coarsen(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                       const int64_t *prp, const int32_t *pcol, const double *ls, int32_t sweep,
+                       double omega, const int32_t *color, int32_t ncolors, int32_t nu,
+                       double theta, double delta, double tol, int32_t max_sets, uint64_t seed,
+                       uint8_t *coarse, double *rho)
+{
+    int64_t nnz_p = prp[n];
+    double *u = (double *)malloc((size_t)(n ? n : 1) * sizeof(double));
+    double *un = (double *)malloc((size_t)(n ? n : 1) * sizeof(double));
+    uint8_t *inz = (uint8_t *)malloc((size_t)(n ? n : 1));
+    uint8_t *inset = (uint8_t *)malloc((size_t)(n ? n : 1));
+    int32_t *lam = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    uint64_t *key = (uint64_t *)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+    int64_t *order = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    uint8_t *strong = (uint8_t *)malloc((size_t)(nnz_p ? nnz_p : 1));
+    int64_t *trp = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t *tsrc = (int64_t *)malloc((size_t)(nnz_p ? nnz_p : 1) * sizeof(int64_t));
+    int32_t stage = 0;
+    if (!u || !un || !inz || !inset || !lam || !key || !order || !strong || !trp || !tsrc) {
+        stage = -5;
+        goto done;
+    }
+    for (;;) {
+        /* (a) nu F-relaxation sweeps from the constant start */
+        int64_t nf = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            u[i] = coarse[i] ? 0.0 : 1.0;
+            nf += !coarse[i];
+        }
+        for (int32_t s = 0; s < nu; ++s) {
+            if (sweep == 0) {
+                for (int64_t i = 0; i < n; ++i) {
+                    if (coarse[i]) { un[i] = 0.0; continue; }
+                    double c = omega / orc_diag(rp, col, val, i);
+                    double acc = 0.0;
+                    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) acc = fma(val[p], u[col[p]], acc);
+                    un[i] = fma(-c, acc, u[i]);
+                }
+            } else {
+                memcpy(un, u, (size_t)n * sizeof(double));
+                for (int32_t cc = 0; cc < ncolors; ++cc) {
+                    for (int64_t i = 0; i < n; ++i) {
+                        if (color[i] != cc || coarse[i]) continue;
+                        double c = omega / orc_diag(rp, col, val, i);
+                        double acc = 0.0;
+                        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                            int64_t j = col[p];
+                            acc = fma(val[p], color[j] < cc ? un[j] : u[j], acc);
+                        }
+                        un[i] = fma(-c, acc, u[i]);
+                    }
+                }
+            }
+            double *t = u;
+            u = un;
+            un = t;
+        }
+        /* (b) rho_f in the max norm; ||u^0|| = 1 when F is not empty */
+        double unorm = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            if (!coarse[i] && fabs(u[i]) > unorm) unorm = fabs(u[i]);
+        double r = nf == 0 ? 0.0 : pow(unorm, 1.0 / (double)nu);
+        rho[stage] = r;
+        /* (c) */
+        if (!(r > delta) || stage >= max_sets) { ++stage; break; }
+        /* (d) candidates */
+        for (int64_t i = 0; i < n; ++i)
+            inz[i] = (uint8_t)(!coarse[i] && fabs(u[i]) / unorm > tol);
+        /* (e) strength graph on F */
+        for (int64_t i = 0; i < n; ++i) {
+            double m = INFINITY;
+            for (int64_t q = prp[i]; q < prp[i + 1]; ++q) {
+                strong[q] = 0;
+                int64_t j = pcol[q];
+                if (j != i && !coarse[j] && ls[q] < m) m = ls[q];
+            }
+            if (coarse[i]) continue;
+            for (int64_t q = prp[i]; q < prp[i + 1]; ++q) {
+                int64_t j = pcol[q];
+                if (j != i && !coarse[j] && (ls[q] == 0.0 || theta * ls[q] < m)) strong[q] = 1;
+            }
+        }
+        /* (f) priorities and the greedy independent set of Z */
+        for (int64_t i = 0; i < n; ++i) lam[i] = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (!inz[j]) continue;
+            for (int64_t q = prp[j]; q < prp[j + 1]; ++q)
+                if (strong[q] && inz[pcol[q]]) ++lam[pcol[q]];
+        }
+        {
+            const uint64_t k2[2] = {seed, 0};
+            for (int64_t i = 0; i < n; ++i) {
+                uint64_t ctr[4] = {(uint64_t)i, (uint64_t)stage, 1, 0};
+                uint64_t out[4];
+                orc_philox4x64_10(ctr, k2, out);
+                key[i] = out[0];
+            }
+        }
+        /* in-edges of the strong graph: the transpose of the strong slots */
+        for (int64_t i = 0; i <= n; ++i) trp[i] = 0;
+        for (int64_t q = 0; q < nnz_p; ++q)
+            if (strong[q]) ++trp[pcol[q] + 1];
+        for (int64_t i = 0; i < n; ++i) trp[i + 1] += trp[i];
+        {
+            int64_t *fill = order;   /* scratch: next free in-edge position per row */
+            for (int64_t i = 0; i < n; ++i) fill[i] = trp[i];
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t q = prp[i]; q < prp[i + 1]; ++q)
+                    if (strong[q]) tsrc[fill[pcol[q]]++] = i;
+        }
+        int64_t nz = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            inset[i] = 0;
+            if (inz[i]) order[nz++] = i;
+        }
+        orc_cr_lam = lam;
+        orc_cr_key = key;
+        qsort(order, (size_t)nz, sizeof(int64_t), orc_cr_cmp);
+        for (int64_t t = 0; t < nz; ++t) {
+            int64_t v = order[t];
+            int blocked = 0;
+            for (int64_t q = prp[v]; q < prp[v + 1] && !blocked; ++q)
+                if (strong[q] && inset[pcol[q]]) blocked = 1;
+            for (int64_t e = trp[v]; e < trp[v + 1] && !blocked; ++e)
+                if (inset[tsrc[e]]) blocked = 1;
+            if (!blocked) inset[v] = 1;
+        }
+        /* (g) */
+        for (int64_t i = 0; i < n; ++i)
+            if (inset[i]) coarse[i] = 1;
+        ++stage;
+    }
+done:
+    free(u); free(un); free(inz); free(inset); free(lam); free(key); free(order);
+    free(strong); free(trp); free(tsrc);
+    return stage;
 }

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import test_oracle_adjoint as adj
+import test_oracle_cr as cr
 import test_oracle_graph as graph
 import test_oracle_interp as interp
 import test_oracle_pins as pins
@@ -23,7 +24,8 @@ PINS = [pins.pin_philox_numpy, pins.pin_tv_init, pins.pin_jacobi_dense_power,
         pins.pin_strength_csr, adj.pin_adjoint_fd, adj.pin_adjoint_homogeneity,
         adj.pin_adjoint_special_cases, graph.pin_distance_graph_matrix_power,
         graph.pin_edge_ls_graph, interp.pin_interp_brute_force, interp.pin_interp_single_point,
-        interp.pin_interp_monotone_and_exact]
+        interp.pin_interp_monotone_and_exact, cr.pin_cr_stage_brute_force,
+        cr.pin_cr_spectral_limit, cr.pin_cr_special_cases]
 
 # (name, text to find, replacement, occurrence index)
 MUTANTS = [
@@ -87,6 +89,22 @@ MUTANTS = [
      "for (int32_t k = 0; k < K; ++k) g += xa[k] * xb[k];", 0),
     ("interp_fine_candidates", "if (coarse[pcol[q]]) cand[nc++] = pcol[q];",
      "if (pcol[q] != i) cand[nc++] = pcol[q];", 0),
+    ("cr_coarse_rows_relaxed", "if (coarse[i]) { un[i] = 0.0; continue; }",
+     "if (coarse[i] && 0) { un[i] = 0.0; continue; }", 0),
+    ("cr_sor_ignores_omega", "acc = fma(val[p], color[j] < cc ? un[j] : u[j], acc);\n                        }\n                        un[i] = fma(-c, acc, u[i]);",
+     "acc = fma(val[p], color[j] < cc ? un[j] : u[j], acc);\n                        }\n                        un[i] = fma(-c / omega, acc, u[i]);", 0),
+    ("cr_rho_no_root", "pow(unorm, 1.0 / (double)nu)", "unorm", 0),
+    ("cr_candidates_signed", "fabs(u[i]) / unorm > tol", "u[i] / unorm > tol", 0),
+    ("cr_min_over_all_neighbours", "if (j != i && !coarse[j] && ls[q] < m) m = ls[q];",
+     "if (j != i && ls[q] < m) m = ls[q];", 0),
+    ("cr_lambda_out_degree", "if (strong[q] && inz[pcol[q]]) ++lam[pcol[q]];",
+     "if (strong[q] && inz[pcol[q]]) ++lam[j];", 0),
+    ("cr_priority_reversed", "if (la != lb) return la > lb;", "if (la != lb) return la < lb;", 0),
+    ("cr_key_wrong_word", "key[i] = out[0];", "key[i] = out[1];", 0),
+    ("cr_key_no_stage", "uint64_t ctr[4] = {(uint64_t)i, (uint64_t)stage, 1, 0};",
+     "uint64_t ctr[4] = {(uint64_t)i, 0, 1, 0};", 0),
+    ("cr_ignores_in_edges", "if (inset[tsrc[e]]) blocked = 1;", "if (0) blocked = 1;", 0),
+    ("cr_not_restarted", "u[i] = coarse[i] ? 0.0 : 1.0;", "u[i] = coarse[i] ? 0.0 : (stage ? u[i] : 1.0);", 0),
     ("adj_weights_dropped", "Xbar[j * K + kappa] += -lsb[p] * 2.0 * w[kappa] * a[p] * e;",
      "Xbar[j * K + kappa] += -lsb[p] * 2.0 * a[p] * e;", 0),
 ]
