@@ -315,6 +315,42 @@ int amgd_ls_interpolation(amgd_handle h, const uint8_t *coarse, int coarse_mem, 
                           int64_t cap, int64_t *nnz_p, double *ls, int mem);
 
 /*
+ * amgd_cr_coarsen -- compatible-relaxation coarsening (§3.2 Eqs. (3.4),
+ *   (3.5); §4.2 Eq. (4.4); Algorithm 1 with the candidate measure of the
+ *   Remark after it).  coarse[n] (coarse_mem): C_0 on entry (nonzero =
+ *   coarse; C_0 empty is allowed), C on exit (0/1).  Each stage:
+ *   (1) nu F-relaxation sweeps of one vector from u = 1 on F, u = 0 held on
+ *       C: the sweep of amgd_relax (sweep: AMGD_SWEEP_JACOBI with weight
+ *       omega, or AMGD_SWEEP_MCGS over the coloring of amgd_set_coloring,
+ *       SOR weight omega) restricted to the rows of F, in FP64 (row sums as
+ *       fused multiply-adds in CSR order);
+ *   (2) rho_f = ||u^nu||_inf^(1/nu) (Eq. (3.5) in the max norm; 0 when F is
+ *       empty), written to rho[stage];
+ *   (3) stop when rho_f <= delta or when max_sets sets have been added;
+ *   (4) candidates Z = { i in F : |u_i| / ||u^nu||_inf > tol };
+ *   (5) the strength graph on F: slot (i, j) of the current pattern (A, or
+ *       G_d after amgd_set_search_depth) is strong iff i, j in F, j != i
+ *       and LS_ij = 0 or theta LS_ij < min over the F neighbours k of LS_ik;
+ *   (6) C gains the independent set of Z (strong slots in either direction
+ *       are edges) that the greedy order selects: more candidates j with
+ *       (j, i) strong first, then the larger key (word 0 of Philox4x64-10
+ *       with counter (i, stage, 1, 0) and key (seed, 0)), then the smaller
+ *       index.  It is computed by rounds of local maxima in that order.
+ *   ls (ls_mem): FP64 LS per slot of the current pattern (nnz of the
+ *   pattern, diagonal slots ignored), or NULL for the LS of the last
+ *   amgd_distances (widened exactly).  rho: max_sets + 1 doubles on the host
+ *   (may be NULL); *n_rho (may be NULL): the number of estimates written =
+ *   the number of stages.  nu >= 1, max_sets >= 0.  Synchronous; one host
+ *   read per stage and per batch of selection rounds.  Single-matrix
+ *   handles only.
+ *   Errors: ARG, STATE (no LS and no distances; MCGS without coloring),
+ *   UNSUPPORTED (batched handle), CUDA.
+ */
+int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double *ls, int ls_mem,
+                    int sweep, double omega, int32_t nu, double theta, double delta, double tol,
+                    int32_t max_sets, uint64_t seed, double *rho, int32_t *n_rho);
+
+/*
  * Reverse pass.  The paper differentiates nothing; these calls give the
  * gradient of a scalar loss on the LS values with respect to the values of A
  * and the Jacobi weight omega, by the chain rule through the steps of §3

@@ -79,6 +79,8 @@ SIGNATURES = {
     "amgd_set_search_depth": (_int, [_P, _i32]),
     "amgd_ls_interpolation": (_int, [_P, _P, _int, _i32, _f64, _P, _P, _P, _i64, _P, _P, _int]),
     "amgd_distance_pattern": (_int, [_P, _P, _P, _i64, _P, _int]),
+    "amgd_cr_coarsen": (_int, [_P, _P, _int, _P, _int, _int, _f64, _i32, _f64, _f64, _f64, _i32,
+                               _u64, _P, _P]),
     "amgd_backward": (_int, [_P, _P, _int, _P, _P, _P]),
     "amgd_backward_scalars": (_int, [_P, _P, _P]),
     "amgd_graph_capture_backward": (_int, [_P, _u64, _i32, _f64, _f64, _P]),
@@ -333,6 +335,24 @@ class Handle:
                                              p_col.ctypes.data, p_val.ctypes.data, cap,
                                              ctypes.byref(nnz), ls.ctypes.data, AMGD_MEM_HOST))
         return p_rp, p_col[:nnz.value], p_val[:nnz.value], ls
+
+    def cr_coarsen(self, coarse0=None, ls=None, sweep=AMGD_SWEEP_JACOBI, omega=1.0, nu=5,
+                   theta=0.5, delta=0.7, tol=0.5, max_sets=20, seed=0):
+        """Compatible-relaxation coarsening (host numpy): (coarse mask, rho per
+        stage).  ls: LS per slot of the current pattern (numpy or torch), or
+        None for the handle's last distances."""
+        c = (np.zeros(self.n, dtype=np.uint8) if coarse0 is None
+             else np.array(_host(coarse0, np.uint8), dtype=np.uint8, copy=True))
+        p_ls, ls_mem = None, AMGD_MEM_HOST
+        if ls is not None:
+            ls = ls if _is_torch(ls) else _host(ls, np.float64)
+            p_ls, ls_mem = ptr_mem(ls)
+        rho = np.empty(max_sets + 1, dtype=np.float64)
+        m = ctypes.c_int32()
+        self._ck(lib().amgd_cr_coarsen(self.h, c.ctypes.data, AMGD_MEM_HOST, p_ls, ls_mem, sweep,
+                                       omega, nu, theta, delta, tol, max_sets, seed,
+                                       rho.ctypes.data, ctypes.byref(m)))
+        return c, rho[:m.value]
 
     # -- reverse pass ---------------------------------------------------------
     def set_checkpointing(self, every):

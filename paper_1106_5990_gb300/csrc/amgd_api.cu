@@ -94,6 +94,14 @@ struct amgd_ctx {
     int64_t *ip_rp = nullptr;
     void *ip_out = nullptr;
     size_t ip_out_bytes = 0;
+    // compatible-relaxation coarsening working buffers
+    int32_t *color_o = nullptr;                  // caller-order colors (set by amgd_set_coloring)
+    double *cr_u[2] = {nullptr, nullptr};
+    uint8_t *cr_coarse = nullptr, *cr_state = nullptr, *cr_ismax = nullptr, *cr_strong = nullptr;
+    size_t cr_strong_len = 0;
+    int32_t *cr_lam = nullptr;
+    uint64_t *cr_key = nullptr;
+    unsigned long long *cr_scal = nullptr;
     int32_t *edge_tiles = nullptr;               // row tiles of the edge pass (over the pattern)
     int32_t n_edge_tiles = 0;
     // pattern of the fits, threshold and strength graph: the graph G_d of A^d
@@ -805,6 +813,8 @@ int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int 
     CK(h, launch_import(h->storage, h->tmp64, h->x[h->cur], h->perm, (int32_t)n, h->K,
                         Kp_of(h->storage, h->K), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (!h->color_o) CK(h, dalloc(&h->color_o, (size_t)n));
+    if (n) CK(h, cudaMemcpy(h->color_o, c.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
     h->color_start = start;
     h->have_dist = false;
     h->traj_valid = false;
@@ -1400,6 +1410,120 @@ int amgd_ls_interpolation(amgd_handle h, const uint8_t *coarse, int coarse_mem, 
     return poll_status(h);
 }
 
+int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double *ls, int ls_mem,
+                    int sweep, double omega, int32_t nu, double theta, double delta, double tol,
+                    int32_t max_sets, uint64_t seed, double *rho, int32_t *n_rho)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (n_rho) *n_rho = 0;
+    if (h->nmat != 1) return fail(h, AMGD_ERR_UNSUPPORTED, "coarsening needs a single-matrix handle");
+    if (nu < 1 || max_sets < 0) return fail(h, AMGD_ERR_ARG, "nu must be >= 1 and max_sets >= 0");
+    if (!std::isfinite(omega) || omega == 0.0 || !(theta >= 0.0) || !std::isfinite(theta) ||
+        !std::isfinite(delta) || !std::isfinite(tol))
+        return fail(h, AMGD_ERR_ARG, "omega, theta, delta and tol must be finite (omega != 0, theta >= 0)");
+    if (sweep != AMGD_SWEEP_JACOBI && sweep != AMGD_SWEEP_MCGS) return fail(h, AMGD_ERR_ARG, "unknown sweep type");
+    if (sweep == AMGD_SWEEP_MCGS && !h->color_o)
+        return fail(h, AMGD_ERR_STATE, "MCGS needs amgd_set_coloring first");
+    if (!coarse && h->n) return fail(h, AMGD_ERR_ARG, "NULL coarse mask");
+    if ((coarse_mem != AMGD_MEM_HOST && coarse_mem != AMGD_MEM_DEVICE) ||
+        (ls && ls_mem != AMGD_MEM_HOST && ls_mem != AMGD_MEM_DEVICE))
+        return fail(h, AMGD_ERR_ARG, "bad mem");
+    if (!ls && !h->have_dist) return fail(h, AMGD_ERR_STATE, "no LS given and amgd_distances has not run");
+    cudaStream_t s = h->stream;
+    const int64_t n = h->n;
+    if (!h->cr_u[0]) {
+        CK(h, dalloc(&h->cr_u[0], (size_t)n));
+        CK(h, dalloc(&h->cr_u[1], (size_t)n));
+        CK(h, dalloc(&h->cr_coarse, (size_t)n));
+        CK(h, dalloc(&h->cr_state, (size_t)n));
+        CK(h, dalloc(&h->cr_ismax, (size_t)n));
+        CK(h, dalloc(&h->cr_lam, (size_t)n));
+        CK(h, dalloc(&h->cr_key, (size_t)n));
+        CK(h, dalloc(&h->cr_scal, 4));
+    }
+    if (h->cr_strong_len < (size_t)h->nnz_p || !h->cr_strong) {
+        dfree(h->cr_strong);
+        h->cr_strong = nullptr;
+        h->cr_strong_len = 0;
+        CK(h, dalloc(&h->cr_strong, (size_t)h->nnz_p));
+        h->cr_strong_len = (size_t)h->nnz_p;
+    }
+    // LS per pattern slot, FP64, on the device
+    const double *d_ls = ls;
+    if (!ls || ls_mem == AMGD_MEM_HOST) {
+        CK(h, ensure_tmp64(h, (size_t)h->nnz_p));
+        if (ls)
+            CK(h, cudaMemcpyAsync(h->tmp64, ls, h->nnz_p * sizeof(double), cudaMemcpyHostToDevice, s));
+        else
+            CK(h, launch_export_slots(h->storage, h->a, h->ls, nullptr, nullptr, h->tmp64, h->nnz_p, s));
+        d_ls = h->tmp64;
+    }
+    CK(h, cudaMemcpyAsync(h->cr_coarse, coarse, (size_t)n,
+                          coarse_mem == AMGD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    CrArgs a;
+    a.rp = h->rp_o;
+    a.col = h->col_o;
+    a.val = h->val_o;
+    a.dslot = h->diag_slot;
+    a.color = h->color_o;
+    a.ncolors = (int32_t)h->color_start.size() - 1;
+    a.prp = h->prp;
+    a.pcol = h->pcol;
+    a.ls = d_ls;
+    a.coarse = h->cr_coarse;
+    a.state = h->cr_state;
+    a.ismax = h->cr_ismax;
+    a.strong = h->cr_strong;
+    a.lam = h->cr_lam;
+    a.key = h->cr_key;
+    a.scal = h->cr_scal;
+    a.n = (int32_t)n;
+    a.omega = omega;
+    a.theta = theta;
+    int32_t stage = 0;
+    unsigned long long scal[3] = {0, 0, 0};
+    for (;;) {
+        // nu F-relaxation sweeps from the constant start (Eq. (3.4))
+        CK(h, launch_cr_start(h->cr_coarse, h->cr_u[0], (int32_t)n, s));
+        int cu = 0;
+        for (int32_t it = 0; it < nu; ++it) {
+            CK(h, launch_cr_sweep(a, sweep == AMGD_SWEEP_MCGS ? 1 : 0, h->cr_u[cu], h->cr_u[cu ^ 1], s));
+            cu ^= 1;
+        }
+        // the convergence estimate of Eq. (3.5) in the max norm (||u^0|| = 1)
+        CK(h, launch_cr_norm(h->cr_u[cu], h->cr_coarse, (int32_t)n, h->cr_scal, s));
+        CK(h, cudaMemcpyAsync(scal, h->cr_scal, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(h, cudaStreamSynchronize(s));
+        double unorm;
+        std::memcpy(&unorm, &scal[0], sizeof unorm);
+        const double r = scal[1] == 0 ? 0.0 : std::pow(unorm, 1.0 / (double)nu);
+        if (rho) rho[stage] = r;
+        if (!(r > delta) || stage >= max_sets) { ++stage; break; }
+        // candidates, strength graph on F, priorities
+        CK(h, launch_cr_candidates(a, h->cr_u[cu], tol, s));
+        CK(h, launch_cr_keys((int32_t)n, stage, seed, h->cr_key, s));
+        // independent set: rounds of local maxima until no candidate is undecided;
+        // every round selects at least the first undecided point of the order
+        int64_t rounds = 0;
+        for (;;) {
+            const int32_t batch = rounds < 8 ? 4 : 8;
+            CK(h, launch_cr_mis_rounds(a, batch, s));
+            rounds += batch;
+            CK(h, cudaMemcpyAsync(&scal[2], h->cr_scal + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            CK(h, cudaStreamSynchronize(s));
+            if (scal[2] == 0) break;
+            if (rounds > n + 8) return fail(h, AMGD_ERR_CUDA, "independent-set rounds did not finish");
+        }
+        CK(h, launch_cr_add(a, s));
+        ++stage;
+    }
+    CK(h, cudaMemcpyAsync(coarse, h->cr_coarse, (size_t)n,
+                          coarse_mem == AMGD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (n_rho) *n_rho = stage;
+    return poll_status(h);
+}
+
 int amgd_set_checkpointing(amgd_handle h, int32_t every)
 {
     if (!h) return AMGD_ERR_ARG;
@@ -1714,7 +1838,8 @@ int amgd_destroy(amgd_handle h)
                     h->s_col_tmp, h->tmp64, h->ckpt, h->seg, h->adj_vec, h->adj_slot, h->lsb,
                     h->adj_part, h->at_rp, h->at_row, h->at_slot, h->edge_tiles, h->mirror,
                     h->ip_coarse, h->ip_sel_col, h->ip_cnt, h->ip_sel_val, h->ip_ls, h->ip_rp,
-                    h->ip_out};
+                    h->ip_out, h->color_o, h->cr_u[0], h->cr_u[1], h->cr_coarse, h->cr_state,
+                    h->cr_ismax, h->cr_strong, h->cr_lam, h->cr_key, h->cr_scal};
     for (void *p : ptrs) dfree(p);
     delete h;
     return AMGD_OK;

@@ -323,6 +323,38 @@ cudaError_t launch_interp_fill(const int64_t *row_ptr, const int32_t *sel_col,
                                const double *sel_val, int32_t n, int32_t *p_col, double *p_val,
                                cudaStream_t s);
 
+// compatible-relaxation coarsening (k_cr.cu; priorities in k_init.cu)
+struct CrArgs {
+    const int32_t *rp, *col;        // A, caller order
+    const double *val;              // A's values (FP64)
+    const int32_t *dslot;           // slot of each row's diagonal
+    const int32_t *color;           // caller-order colors (multicolor sweeps)
+    int32_t ncolors;
+    const int32_t *prp, *pcol;      // pattern of the strength graph (G_d)
+    const double *ls;               // LS per pattern slot (FP64)
+    uint8_t *coarse;                // n, 1 = coarse
+    uint8_t *state;                 // n: 0 out, 1 undecided candidate, 2 selected
+    uint8_t *ismax;                 // n
+    uint8_t *strong;                // pattern slots
+    int32_t *lam;                   // n
+    const uint64_t *key;            // n
+    unsigned long long *scal;       // [0] max |u| bits, [1] |F|, [2] undecided count
+    int32_t n;
+    double omega, theta;
+};
+cudaError_t launch_cr_start(const uint8_t *coarse, double *u, int32_t n, cudaStream_t s);
+// one F-relaxation sweep u -> un (sweep 0 Jacobi, 1 multicolor Gauss-Seidel)
+cudaError_t launch_cr_sweep(const CrArgs &a, int sweep, const double *u, double *un, cudaStream_t s);
+cudaError_t launch_cr_norm(const double *u, const uint8_t *coarse, int32_t n,
+                           unsigned long long *scal, cudaStream_t s);
+// candidates, strength graph on F and the priorities' lambda
+cudaError_t launch_cr_candidates(const CrArgs &a, const double *u, double tol, cudaStream_t s);
+// `rounds` rounds of local maxima, then scal[2] = undecided points left
+cudaError_t launch_cr_mis_rounds(const CrArgs &a, int32_t rounds, cudaStream_t s);
+cudaError_t launch_cr_add(const CrArgs &a, cudaStream_t s);
+// key[i] = word 0 of Philox4x64-10, counter (i, stage, 1, 0), key (seed, 0)
+cudaError_t launch_cr_keys(int32_t n, int32_t stage, uint64_t seed, uint64_t *key, cudaStream_t s);
+
 // message returned by amgd_last_error(NULL) on the calling host thread
 void set_thread_error(const std::string &msg);
 

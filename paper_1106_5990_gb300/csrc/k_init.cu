@@ -304,7 +304,23 @@ __global__ void k_diag_values(const double *__restrict__ v, const int32_t *__res
 
 inline unsigned blocks(int64_t work) { return (unsigned)((work + kThreads - 1) / kThreads); }
 
+// priority keys of the coarse-point selection: one Philox4x64-10 block per
+// point, counter (i, stage, 1, 0) (word 2 = 1 keeps them apart from the
+// test-vector draws), key (seed, 0); word 0 is the key
+__global__ void k_cr_keys(int32_t n, int32_t stage, uint64_t seed, uint64_t *__restrict__ key)
+{
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        key[i] = philox4x64_10((uint64_t)i, (uint64_t)stage, 1ull, 0ull, seed, 0ull).v[0];
+}
+
 }  // namespace
+
+cudaError_t launch_cr_keys(int32_t n, int32_t stage, uint64_t seed, uint64_t *key, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_cr_keys<<<blocks(n), kThreads, 0, s>>>(n, stage, seed, key);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init(int storage, const InitArgs &a, cudaStream_t s)
 {

@@ -22,6 +22,7 @@ import pytest
 
 import oracle
 from paper_1106_5990_gb300 import inputs
+from parity import flags_from_strength
 
 pytestmark = pytest.mark.gpu
 amgd = pytest.importorskip("paper_1106_5990_gb300.amgd")
@@ -53,6 +54,13 @@ def run_gpu(mat, K, seed, nu, omega, theta, every, prec="fp64", target=0, w=None
         return dict(X0=X0, ls=d["ls"], val_bar=vb, omega_bar=wb, loss=loss)
 
 
+def x0(mat, K, seed, batch=None):
+    """The oracle's start vectors (never the GPU's): Philox of (seed, matrix id)."""
+    if batch is None:
+        return oracle.tv_init(len(mat[0]) - 1, K, seed)
+    return np.concatenate([oracle.tv_init(len(m[0]) - 1, K, seed, b) for b, m in enumerate(batch)])
+
+
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) /
                  max(np.linalg.norm(np.asarray(b)), 1e-300))
@@ -81,7 +89,8 @@ def test_fp64_matches_oracle(case, target):
     rng = np.random.default_rng(1)
     w = rng.uniform(0.5, 2.0, K) if case == "random_600" else None
     g = run_gpu(mat, K, 7, nu, omega, 0.5, 2, target=target, w=w)
-    o = oracle.adjoint_jacobi(*mat, g["X0"], nu, omega, 0.5, w, target)
+    assert np.array_equal(g["X0"], x0(mat, K, 7))
+    o = oracle.adjoint_jacobi(*mat, x0(mat, K, 7), nu, omega, 0.5, w, target)
     check_fp64(g, o)
 
 
@@ -100,13 +109,13 @@ def test_no_sweeps_and_upstream_gradient():
     mat = inputs.random_csr(400, 5.0, 2)
     rp, col, val = mat
     g = run_gpu(mat, 8, 4, 0, 0.7, 0.5, 2)
-    o = oracle.adjoint_jacobi(rp, col, val, g["X0"], 0, 0.7, 0.5)
+    o = oracle.adjoint_jacobi(rp, col, val, x0(mat, 8, 4), 0, 0.7, 0.5)
     check_fp64(g, o)
     assert g["omega_bar"] == 0.0
     # an explicit dL/dLS, host and device
     lsb = np.random.default_rng(5).standard_normal(len(col))
     g = run_gpu(mat, 8, 4, 3, 0.7, 0.5, 2, ls_bar=lsb)
-    o = oracle.adjoint_jacobi(rp, col, val, g["X0"], 3, 0.7, 0.5, ls_bar=lsb)
+    o = oracle.adjoint_jacobi(rp, col, val, x0(mat, 8, 4), 3, 0.7, 0.5, ls_bar=lsb)
     check_fp64(g, o)
     assert math.isnan(g["loss"])
     with amgd.Handle(rp, col, val, 8, 4) as h:
@@ -130,7 +139,8 @@ def test_batch_matches_oracle():
     rp = np.concatenate([mats[0][0]] + [m[0][1:] + so[b] for b, m in enumerate(mats) if b > 0])
     col = np.concatenate([m[1] + ro[b] for b, m in enumerate(mats)])
     val = np.concatenate([m[2] for m in mats])
-    o = oracle.adjoint_jacobi(rp, col, val, g["X0"], 4, 2.0 / 3.0, 0.5)
+    assert np.array_equal(g["X0"], x0(None, 16, 6, batch=mats))
+    o = oracle.adjoint_jacobi(rp, col, val, x0(None, 16, 6, batch=mats), 4, 2.0 / 3.0, 0.5)
     check_fp64(g, o)
 
 
@@ -146,7 +156,7 @@ def test_finite_differences_of_gpu_forward():
             h.relax(nu, om)
             ls = h.distances(theta, want=("ls",))["ls"]
             s_rp, s_col = h.strength()
-            return ls, s_col
+            return ls, (s_rp, s_col)
 
         ls0, kept0 = loss(val, omega)
         vb, wb, L = h.backward()
@@ -156,19 +166,22 @@ def test_finite_differences_of_gpu_forward():
             hstep = 1e-6
             lp, kp = loss(val + hstep * d, omega)
             lm, km = loss(val - hstep * d, omega)
-            assert np.array_equal(kp, kept0) and np.array_equal(km, kept0)
-            Lp = _loss_from(rp, col, lp, h, theta)
-            Lm = _loss_from(rp, col, lm, h, theta)
+            assert np.array_equal(kp[1], kept0[1]) and np.array_equal(km[1], kept0[1])
+            Lp = _loss_from(rp, col, lp, kp)
+            Lm = _loss_from(rp, col, lm, km)
             fd = (Lp - Lm) / (2 * hstep)
             assert abs(fd - vb @ d) <= 1e-5 * abs(fd), (fd, vb @ d)
-        lp, _ = loss(val, omega + 1e-6)
-        lm, _ = loss(val, omega - 1e-6)
-        fd = (_loss_from(rp, col, lp, h, theta) - _loss_from(rp, col, lm, h, theta)) / 2e-6
+        lp, kp = loss(val, omega + 1e-6)
+        lm, km = loss(val, omega - 1e-6)
+        assert np.array_equal(kp[1], kept0[1]) and np.array_equal(km[1], kept0[1])
+        fd = (_loss_from(rp, col, lp, kp) - _loss_from(rp, col, lm, km)) / 2e-6
         assert abs(fd - wb) <= 1e-5 * abs(fd)
 
 
-def _loss_from(rp, col, ls, h, theta):
-    flag, _ = oracle.threshold(rp, col, np.where(np.isnan(ls), np.nan, ls), theta)
+def _loss_from(rp, col, ls, strength):
+    """The built-in loss from the GPU's own outputs: sum of LS^-2 over the
+    slots its strength graph keeps with LS > 0."""
+    flag = flags_from_strength(rp, col, *strength)
     keep = (flag == 1) & (ls > 0)
     return float(np.sum(1.0 / ls[keep] ** 2))
 
@@ -207,7 +220,7 @@ MIXED_BARS = {"fp32": 1e-3, "bf16": 5e-2}
 def test_mixed_against_fp64_oracle(prec):
     mat = inputs.aniso2d_5pt(48, 1e-2)
     g = run_gpu(mat, 16, 7, 10, 2.0 / 3.0, 0.5, 2, prec=prec)
-    o = oracle.adjoint_jacobi(*mat, g["X0"], 10, 2.0 / 3.0, 0.5)
+    o = oracle.adjoint_jacobi(*mat, x0(mat, 16, 7), 10, 2.0 / 3.0, 0.5)
     e_v = rel(g["val_bar"], o["val_bar"])
     e_w = abs(g["omega_bar"] - o["omega_bar"]) / abs(o["omega_bar"])
     e_l = abs(g["loss"] - o["loss"]) / o["loss"]
@@ -222,7 +235,7 @@ def test_full_size_aniso5_512(prec):
     the oracle at full size."""
     mat = inputs.aniso2d_5pt(512, 1e-2)
     g = run_gpu(mat, 16, 7, 10, 2.0 / 3.0, 0.5, 2, prec=prec)
-    o = oracle.adjoint_jacobi(*mat, g["X0"], 10, 2.0 / 3.0, 0.5)
+    o = oracle.adjoint_jacobi(*mat, x0(mat, 16, 7), 10, 2.0 / 3.0, 0.5)
     if prec == "fp64":
         check_fp64(g, o)
     else:

@@ -1,9 +1,10 @@
 """Least-squares interpolation (§4.3) on the GPU against the oracle: the
 GPU evaluates every candidate set in FP64 with the rounding order of the
-definition, so on the same (stored) vectors the chosen sets, weights and LS
-values equal the oracle's bit for bit -- for every storage precision (the
-vectors are widened exactly), with and without a coloring, search depth 1
-and 2, caliber 1 to 4, gamma 1.5 and 0."""
+definition, so on the same stored vectors (the oracle's relaxed vectors,
+rounded to the storage type on the CPU and set on the handle) the chosen
+sets, weights and LS values equal the oracle's bit for bit -- for every
+storage precision (the vectors are widened exactly), with and without a
+coloring, search depth 1 and 2, caliber 1 to 4, gamma 1.5 and 0."""
 import math
 
 import numpy as np
@@ -36,24 +37,38 @@ def _case(name):
     return rp, col, val, coarse, None
 
 
+def _stored(X, prec):
+    """X rounded to the storage type on the CPU; the values are then exact in
+    that type, so the GPU stores them unchanged."""
+    if prec == "fp64":
+        return X
+    t = torch.from_numpy(X).to(torch.bfloat16 if prec == "bf16" else torch.float32)
+    return t.to(torch.float64).numpy()
+
+
 @pytest.mark.parametrize("name", ["aniso5_24", "random_500"])
 @pytest.mark.parametrize("prec", ["fp64", "bf16"])
 @pytest.mark.parametrize("d,c,gamma", [(1, 2, 1.5), (2, 3, 1.5), (2, 4, 0.0), (2, 1, 1.5)])
 def test_interp_matches_oracle(name, prec, d, c, gamma):
     rp, col, val, coarse, color = _case(name)
-    K = 8
+    n, K = len(rp) - 1, 8
     w = np.random.default_rng(4).uniform(0.5, 2.0, K)
+    # the oracle's relaxed vectors, in the storage type; the oracle's pattern
+    X0 = oracle.tv_init(n, K, 9)
+    if color is not None:
+        X = oracle.relax(rp, col, val, X0, 3, 1.0, oracle.SWEEP_MCGS, color)
+    else:
+        X = oracle.relax(rp, col, val, X0, 3, 0.7)
+    X = _stored(X, prec)
+    prp, pcol = oracle.distance_graph(rp, col, d)
     with amgd.Handle(rp, col, val, K, 9) as h:
         h.set_precision(prec)
         h.set_weights(w)
         if color is not None:
             h.set_coloring(color)
-            h.relax(3, 1.0, amgd.AMGD_SWEEP_MCGS)
-        else:
-            h.relax(3, 0.7, amgd.AMGD_SWEEP_JACOBI)
         h.set_search_depth(d)
-        X = h.get_vectors()
-        prp, pcol = h.distance_pattern()
+        h.set_vectors(X)
+        assert np.array_equal(h.get_vectors(), X)
         got = h.ls_interpolation(coarse, c, gamma)
     Y = oracle.target(rp, col, val, X)
     want = oracle.ls_interp(X, Y, prp, pcol, coarse, c, gamma, w)
