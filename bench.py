@@ -11,7 +11,7 @@ red-black Gauss-Seidel sweeps, theta = 0.5): the mixed path (BF16 vector
 storage, FP32 arithmetic) is the headline, the FP64 path is measured beside
 it on the same matrix.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c2]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c1..c7]
                   [--precision bf16|fp32|fp64] [--impl ours|reference]
 
 Under torchrun (N > 1) every rank builds its own copy of the workload on its
@@ -65,6 +65,21 @@ WORKLOADS = {
                     "checkpoints every 2 sweeps",
                K=16, seed=7, nu=10, omega=2.0 / 3.0, sweep="jacobi", theta=0.5,
                precision="fp32", adjoint=2),
+    "c6": dict(name="rotated anisotropic diffusion 9-point, 1024x1024 grid, eps=1e-3, "
+                    "alpha=pi/6; K=16, nu=8 red-black Gauss-Seidel, theta=0.5; search depth "
+                    "d=2 (fits, threshold and strength graph over the graph of A^2, "
+                    "25-point pattern)",
+               K=16, seed=1, nu=8, omega=1.0, sweep="mcgs", theta=0.5, precision="bf16",
+               depth=2),
+    "c7": dict(name="compatible-relaxation coarsening (Algorithm 1: 5 red-black F-relaxation "
+                    "sweeps per stage, theta=0.5, delta=0.6, tol=0.5, at most 12 sets) and "
+                    "least-squares interpolation (caliber 2, gamma=1.5, neighbourhood of A) "
+                    "of the rotated anisotropic 9-point operator, 1024x1024 grid, eps=1e-3, "
+                    "alpha=pi/6; LS from K=16, nu=8 red-black Gauss-Seidel (BF16 build, "
+                    "untimed)",
+               K=16, seed=1, nu=8, omega=1.0, sweep="mcgs", theta=0.5, precision="bf16",
+               coarsen=dict(nu=5, omega=1.0, delta=0.6, tol=0.5, max_sets=12, seed=5,
+                            caliber=2, gamma=1.5)),
 }
 
 
@@ -73,7 +88,7 @@ def make_matrix(cfg: str, scale: int | None = None):
     (used for the bounded CPU samples)."""
     if cfg == "c1":
         return [inputs.poisson2d_5pt(64)], None
-    if cfg == "c2":
+    if cfg in ("c2", "c6", "c7"):
         N = scale or 1024
         return [inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)], inputs.red_black(N)
     if cfg == "c3":
@@ -97,7 +112,9 @@ def make_matrix(cfg: str, scale: int | None = None):
 SIZES = {"fp64": 8, "fp32": 4, "bf16": 2}
 
 
-def algorithmic_bytes(n, nnz, E, E_s, K, nu, ncolors, precision, permuted):
+def algorithmic_bytes(n, nnz, E, E_s, K, nu, ncolors, precision, permuted, nnz_p=None):
+    """nnz_p: stored entries of the fit pattern (the graph G_d of A^d for
+    search depth d > 1; None: A's own pattern)."""
     s_x = SIZES[precision]
     s_a = 8 if precision == "fp64" else 4
     s_c = 8 if precision == "fp64" else 4
@@ -105,8 +122,10 @@ def algorithmic_bytes(n, nnz, E, E_s, K, nu, ncolors, precision, permuted):
     reads_per_sweep = ncolors                 # every color phase reads the vectors once
     sweep = csr + (reads_per_sweep + 1) * n * K * s_x
     init = n * K * s_x
-    edge = csr + n * K * s_x + nnz * (2 * s_c + 1) + 4 * n + (8 * n if permuted else 0)
-    strength = 4 * n * 2 + nnz + 4 * E_s * 2 + 8 * (n + 1)
+    pat = 0 if nnz_p is None else nnz_p * 4 + 4 * (n + 1)     # G_d columns and row starts
+    nnz_p = nnz if nnz_p is None else nnz_p
+    edge = csr + pat + n * K * s_x + nnz_p * (2 * s_c + 1) + 4 * n + (8 * n if permuted else 0)
+    strength = 4 * n * 2 + nnz_p + 4 * E_s * 2 + 8 * (n + 1)
     return dict(init=init, sweep=sweep, relax=nu * sweep, relax_per_launch=sweep / ncolors,
                 edge=edge, strength=strength, total=init + nu * sweep + edge + strength)
 
@@ -244,10 +263,12 @@ def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_cloc
         h.set_coloring(color)
         ncolors = int(color.max()) + 1
         sweep = amgd.AMGD_SWEEP_MCGS
+    if w.get("depth", 1) > 1:
+        h.set_search_depth(w["depth"])
     shapes = h.autotune(sweep, w["omega"], tune_cache)   # kernel shapes; untimed
     h.init_vectors(w["seed"])
     d_rp = torch.empty(h.n + 1, dtype=torch.int64, device="cuda")
-    d_col = torch.empty(max(h.E, 1), dtype=torch.int32, device="cuda")
+    d_col = torch.empty(max(h.E_p, 1), dtype=torch.int32, device="cuda")
     d_vb = None
     h.enable_phase_timing(True)
     if w.get("adjoint"):
@@ -300,7 +321,7 @@ def run_e2e(h, mats, w, sweep, steps, adjoint=None):
     vals = np.concatenate([m[2] for m in mats])
     val_h = torch.from_numpy(vals).pin_memory()
     s_rp = torch.empty(h.n + 1, dtype=torch.int64).pin_memory()
-    s_col = torch.empty(max(h.E, 1), dtype=torch.int32).pin_memory()
+    s_col = torch.empty(max(h.E_p, 1), dtype=torch.int32).pin_memory()
     L = amgd.lib()
     nnz_s = ctypes.c_int64()
     vb_h = torch.empty(len(vals), dtype=torch.float64).pin_memory() if adjoint else None
@@ -337,9 +358,10 @@ def oracle_step(oracle, rp, col, val, w, color):
         X0 = oracle.tv_init(len(rp) - 1, w["K"], w["seed"])
         oracle.adjoint_jacobi(rp, col, val, X0, w["nu"], w["omega"], w["theta"])
     else:
-        oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
-                     sweep=oracle.SWEEP_MCGS if w["sweep"] == "mcgs" else oracle.SWEEP_JACOBI,
-                     color=color)
+        b = oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
+                         sweep=oracle.SWEEP_MCGS if w["sweep"] == "mcgs" else oracle.SWEEP_JACOBI,
+                         color=color, d=w.get("depth", 1))
+        return len(b["pcol"]) - (len(rp) - 1)
     return len(col) - (len(rp) - 1)
 
 
@@ -352,6 +374,9 @@ def cpu_oracle_time(cfg, w, budget_s=20.0):
     elif cfg == "c2":
         mats, color = make_matrix(cfg)
         sample = "full workload (1024x1024)"
+    elif cfg == "c6":
+        mats, color = make_matrix(cfg, scale=512)
+        sample = "512x512 sub-grid of the same operator"
     elif cfg == "c3":
         mats, color = make_matrix(cfg, scale=64)
         sample = "64^3 sub-problem of the same operator"
@@ -436,7 +461,9 @@ def run_reference(args, cfg, w):
         return 0
     import oracle
     oracle.build_lib()
-    if cfg == "c2":
+    if w.get("coarsen"):
+        return run_reference_coarsen(args, cfg, w, ws)
+    if cfg in ("c2", "c6"):
         mats, color = make_matrix(cfg, scale=256)
         sample = "256x256 sub-grid of the same operator per step"
     elif cfg == "c3":
@@ -468,6 +495,244 @@ def run_reference(args, cfg, w):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_reference_coarsen(args, cfg, w, ws):
+    """Reference arm of the coarsening workload: the oracle's CR +
+    interpolation on a 256 x 256 sub-grid per step (its build untimed)."""
+    import oracle
+    mats, color = make_matrix(cfg, scale=256)
+    rp, col, val = mats[0]
+    b = oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
+                     oracle.SWEEP_MCGS, color)
+    for _ in range(args.warmup):
+        oracle_coarsen_step(oracle, rp, col, val, w, color, b)
+    t0 = time.perf_counter()
+    rows = sum(oracle_coarsen_step(oracle, rp, col, val, w, color, b) for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = rows / dt
+    line = {"impl": "reference",
+            "metric": "rows/s of compatible-relaxation coarsening + LS interpolation",
+            "value": v, "unit": "rows/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["name"], "config": cfg},
+            "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                             "sample": "256x256 sub-grid of the same operator per step"},
+            "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# coarsening workload: compatible relaxation + least-squares interpolation
+# --------------------------------------------------------------------------
+def interp_flops(rp, col, coarse, K, caliber):
+    """FP64 operations of the exhaustive LS interpolation as its definition
+    states it, per fine row with m coarse candidates: the Gram matrix and
+    right-hand side (m(m+1)/2 + m + 1 weighted K-term sums, 3K each), and for
+    every subset of s <= caliber candidates the elimination of the s x s
+    system (2s^3/3 + 2s^2) and the weighted residual sum over K components
+    (K (2s + 3))."""
+    n = len(rp) - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    cand = (coarse[col] != 0) & (col != rows)
+    m = np.bincount(rows[cand], minlength=n)[coarse == 0]
+    total = np.sum((m * (m + 1) / 2 + m + 1) * 3 * K)
+    for s_ in range(1, caliber + 1):
+        sub = np.array([math.comb(int(v), s_) for v in range(int(m.max(initial=0)) + 1)],
+                       dtype=np.float64)
+        total += np.sum(sub[m]) * (2 * s_ ** 3 / 3 + 2 * s_ ** 2 + K * (2 * s_ + 3))
+    return float(total)
+
+
+def cr_sweep_bytes(n, nnz, ncolors):
+    """Algorithmic bytes of one F-relaxation sweep (K = 1, FP64 values): the
+    CSR once, the diagonal slot and value per row, the mask and colors once
+    per color phase, u read once per color phase and written once."""
+    return nnz * 12 + 4 * (n + 1) + 12 * n + ncolors * (5 * n + 8 * n) + 8 * n
+
+
+def run_coarsen(args, cfg, w, mats, color, precision, ws, rank, flush):
+    """One step = amgd_cr_coarsen (Algorithm 1 from the handle's distances,
+    empty C_0) + amgd_ls_interpolation of the resulting coarse set, all
+    outputs in device memory.  Unit: rows of the matrix coarsened and
+    interpolated per second."""
+    import ctypes
+    import torch
+    from paper_1106_5990_gb300 import amgd
+
+    cw = w["coarsen"]
+    rp, col, val = mats[0]
+    n, nnz = len(rp) - 1, len(col)
+    stream = torch.cuda.current_stream()
+    h = amgd.Handle(rp, col, val, w["K"], w["seed"])
+    h.set_stream(stream)
+    h.set_precision(precision)
+    h.set_coloring(color)
+    ncolors = int(color.max()) + 1
+    h.autotune(amgd.AMGD_SWEEP_MCGS, w["omega"], args.tune_cache)
+    h.init_vectors(w["seed"])
+    h.relax(w["nu"], w["omega"], amgd.AMGD_SWEEP_MCGS)
+    h.distances(w["theta"], want=())
+    L = amgd.lib()
+    DEV, HOST = amgd.AMGD_MEM_DEVICE, amgd.AMGD_MEM_HOST
+    coarse = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    cap = n * cw["caliber"]
+    p_rp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    p_col = torch.empty(cap, dtype=torch.int32, device="cuda")
+    p_val = torch.empty(cap, dtype=torch.float64, device="cuda")
+    p_ls = torch.empty(n, dtype=torch.float64, device="cuda")
+    rho = np.empty(cw["max_sets"] + 1)
+    nr = ctypes.c_int32()
+    nnz_pp = ctypes.c_int64()
+
+    def cr():
+        amgd.check(L.amgd_cr_coarsen(h.h, coarse.data_ptr(), DEV, None, HOST,
+                                     amgd.AMGD_SWEEP_MCGS, cw["omega"], cw["nu"], w["theta"],
+                                     cw["delta"], cw["tol"], cw["max_sets"], cw["seed"],
+                                     rho.ctypes.data, ctypes.byref(nr)), h.h)
+
+    def interp():
+        amgd.check(L.amgd_ls_interpolation(h.h, coarse.data_ptr(), DEV, cw["caliber"],
+                                           cw["gamma"], p_rp.data_ptr(), p_col.data_ptr(),
+                                           p_val.data_ptr(), cap, ctypes.byref(nnz_pp),
+                                           p_ls.data_ptr(), DEV), h.h)
+
+    for _ in range(args.warmup):
+        coarse.zero_()
+        cr()
+        interp()
+    torch.cuda.synchronize()
+    steps = args.steps
+    clocks = ClockSampler(torch.cuda.current_device())
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    clocks.start()
+    time.sleep(0.15)
+    _barrier()
+    torch.cuda.synchronize()
+    launches = 0
+    t_wall = time.perf_counter()
+    for k in range(steps):
+        flush.fill_(k & 0xFF)                     # evict L2 between steps (not timed)
+        coarse.zero_()
+        ev[k][0].record(stream)
+        cr()
+        ev[k][1].record(stream)
+        interp()
+        ev[k][2].record(stream)
+        # interpolation: unpermute, classify, list, row and warp kernels, 3 scan, fill
+        launches += h.cr_stats()[1] + 9
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    _barrier()
+    clk = clocks.stop()
+    cr_ms = np.array([a.elapsed_time(b) for a, b, _ in ev])
+    ip_ms = np.array([b.elapsed_time(c) for _, b, c in ev])
+    value, ms_per_step = whole_job(float((cr_ms + ip_ms).sum()), n, steps)
+    rounds, cr_launches = h.cr_stats()
+    C = coarse.cpu().numpy()
+    stages = nr.value
+    peak, peak_kind = peaks()
+    # dominant phase: its leading kernel against its bound
+    flops = interp_flops(rp, col, C, w["K"], cw["caliber"])
+    ip_mean = float(ip_ms.mean())
+    cr_mean = float(cr_ms.mean())
+    fp64_peak = 1250.0          # GB300 FP64 nominal, GFLOP/s (ALU bound of the fits)
+    if ip_mean >= cr_mean:
+        achieved = flops / (ip_mean * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s",
+                    "frac": achieved / fp64_peak, "traffic": None,
+                    "kernel": "k_ls_interp (FP64 exhaustive fits; phase incl. scan and fill)",
+                    "peak_source": "nominal FP64 rate of the GB300 (1.25 TFLOP/s)",
+                    "algorithmic_flops_per_launch": flops, "avg_launch_us": ip_mean * 1e3}
+    else:
+        sb = cr_sweep_bytes(n, nnz, ncolors)
+        sweeps = stages * cw["nu"]
+        achieved = sweeps * sb / (cr_mean * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "CR phase as a whole against its F-relaxation sweep bytes",
+                    "peak_source": "%s hbm_gbs" % peak_kind,
+                    "algorithmic_bytes_per_launch": sb, "avg_launch_us": None}
+    line = {"metric": "rows/s of compatible-relaxation coarsening + LS interpolation",
+            "value": value, "unit": "rows/s", "n_gpus": ws, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "config": cfg, "n": n, "nnz": nnz,
+                       "storage_of_build": precision, "l2": "flushed between steps (256 MiB "
+                       "write)", "coarsen": cw},
+            "phase_ms": {"cr": cr_mean, "interp": ip_mean},
+            "cr": {"stages": stages, "rho": rho[:stages].tolist(), "coarse": int(C.sum()),
+                   "selection_rounds": rounds, "kernels": cr_launches,
+                   "interp_entries": int(nnz_pp.value)},
+            "host_wall_ms_per_step": 1e3 * t_wall / steps,
+            "roofline": roofline, "gpu_launches": launches,
+            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}}
+    # end to end: the same two calls with host buffers (coarse mask in, P out)
+    e2e_steps = max(3, min(steps, 20))
+    c_h = torch.zeros(n, dtype=torch.uint8).pin_memory()
+    prp_h = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+    pcol_h = torch.empty(cap, dtype=torch.int32).pin_memory()
+    pval_h = torch.empty(cap, dtype=torch.float64).pin_memory()
+    pls_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        c_h.zero_()
+        amgd.check(L.amgd_cr_coarsen(h.h, c_h.data_ptr(), HOST, None, HOST,
+                                     amgd.AMGD_SWEEP_MCGS, cw["omega"], cw["nu"], w["theta"],
+                                     cw["delta"], cw["tol"], cw["max_sets"], cw["seed"],
+                                     rho.ctypes.data, ctypes.byref(nr)), h.h)
+        amgd.check(L.amgd_ls_interpolation(h.h, c_h.data_ptr(), HOST, cw["caliber"],
+                                           cw["gamma"], prp_h.data_ptr(), pcol_h.data_ptr(),
+                                           pval_h.data_ptr(), cap, ctypes.byref(nnz_pp),
+                                           pls_h.data_ptr(), HOST), h.h)
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    v_e2e, _ = whole_job(1e3 * t_e2e, n, 1)
+    line["e2e"] = {"value": v_e2e, "unit": "rows/s", "h2d_bytes_per_step": 2 * n,
+                   "d2h_bytes_per_step": n + 8 * (n + 1) + 12 * int(nnz_pp.value) + 8 * n,
+                   "steps": e2e_steps,
+                   "api": "amgd_cr_coarsen(host mask) + amgd_ls_interpolation(host mask, host P)"}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_coarsen_time(w)
+    h.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def oracle_coarsen_step(oracle, rp, col, val, w, color, b):
+    """CR + LS interpolation on the oracle from the oracle's own build b."""
+    cw = w["coarsen"]
+    C, _ = oracle.cr_coarsen(rp, col, val, rp, col, b["ls"], w["theta"], cw["nu"], cw["omega"],
+                             oracle.SWEEP_MCGS, color, cw["delta"], cw["tol"], cw["max_sets"],
+                             cw["seed"])
+    oracle.ls_interp(b["X"], b["Y"], rp, col, C, cw["caliber"], cw["gamma"])
+    return len(rp) - 1
+
+
+def cpu_coarsen_time(w, budget_s=20.0, N=512):
+    """The FP64 oracle (single thread) on CR + interpolation of an N x N
+    sub-grid of the same operator (its own build, untimed)."""
+    import oracle
+    mats, color = make_matrix("c7", scale=N)
+    rp, col, val = mats[0]
+    b = oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
+                     oracle.SWEEP_MCGS, color)
+    rows = 0
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        rows += oracle_coarsen_step(oracle, rp, col, val, w, color, b)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 3 or reps >= 3:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=rows / dt, unit="rows/s", cores=1, kind="oracle",
+                sample="%dx%d sub-grid of the same operator, %d repetition(s), %.1f s"
+                       % (N, N, reps, dt))
 
 
 # --------------------------------------------------------------------------
@@ -504,11 +769,15 @@ def main():
     mats, color = make_matrix(cfg, scale=args.scale)
     n = sum(len(m[0]) - 1 for m in mats)
     nnz = sum(len(m[1]) for m in mats)
-    E = nnz - n
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    if w.get("coarsen"):
+        return run_coarsen(args, cfg, w, mats, color, precision, ws, rank, flush)
 
     r = run_gpu_arm(mats, color, w, precision, args.steps, args.warmup, rank, flush,
                     tune_cache=args.tune_cache)
+    depth = w.get("depth", 1)
+    nnz_p = r["h"].nnz_p                       # entries of the fit pattern (A, or G_d)
+    E = r["h"].E_p                             # edges whose distance the step computes
     value, ms_per_step = whole_job(float(r["step_ms"].sum()), E, args.steps)
 
     permuted = w["sweep"] == "mcgs"
@@ -519,21 +788,37 @@ def main():
         if adj:
             return adjoint_bytes(n, nnz, w["K"], w["nu"], adj, prec)
         return algorithmic_bytes(n, nnz, E, rr["E_s"], w["K"], w["nu"], rr["ncolors"], prec,
-                                 permuted)
+                                 permuted, nnz_p=nnz_p if depth > 1 else None)
 
     ab = step_bytes(r, precision)
     launches_relax = w["nu"] * r["ncolors"]
     relax_launch_ms = r["phase_ms"][1] / launches_relax
     peak, peak_kind = peaks()
-    achieved = ab["relax_per_launch"] / (relax_launch_ms * 1e-3) / 1e9
-    tkey = "relax/%s/K%d/%s" % (precision, w["K"], cfg)
-    traffic = recorded_traffic(tkey, source_sha("k_relax.cu", "rowops.cuh", "amgd_internal.cuh"))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_relax (one color phase of one sweep)",
-                "peak_source": "%s hbm_gbs" % peak_kind,
-                "algorithmic_bytes_per_launch": ab["relax_per_launch"],
-                "avg_launch_us": relax_launch_ms * 1e3}
+    if depth > 1 and r["phase_ms"][2] > r["phase_ms"][1]:
+        # the distance pass over G_d dominates the step: one launch (plus the
+        # FP64 row fixup of the mixed paths, inside the same phase)
+        edge_ms = r["phase_ms"][2]
+        achieved = ab["edge"] / (edge_ms * 1e-3) / 1e9
+        tkey = "edge/%s/K%d/%s" % (precision, w["K"], cfg)
+        traffic = recorded_traffic(tkey, source_sha("k_edge.cuh", "rowops.cuh",
+                                                    "amgd_internal.cuh"))
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "kernel": "distance pass over G_%d (edge kernel + FP64 row fixup)" % depth,
+                    "peak_source": "%s hbm_gbs" % peak_kind,
+                    "algorithmic_bytes_per_launch": ab["edge"],
+                    "avg_launch_us": edge_ms * 1e3}
+    else:
+        achieved = ab["relax_per_launch"] / (relax_launch_ms * 1e-3) / 1e9
+        tkey = "relax/%s/K%d/%s" % (precision, w["K"], cfg)
+        traffic = recorded_traffic(tkey, source_sha("k_relax.cu", "rowops.cuh",
+                                                    "amgd_internal.cuh"))
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "kernel": "k_relax (one color phase of one sweep)",
+                    "peak_source": "%s hbm_gbs" % peak_kind,
+                    "algorithmic_bytes_per_launch": ab["relax_per_launch"],
+                    "avg_launch_us": relax_launch_ms * 1e3}
     names = ["init", "relax", "distances", "backward" if adj else "strength"]
     phases = dict(zip(names, r["phase_ms"].tolist()))
     whole = ab["total"] / (ms_per_step * 1e-3) / 1e9
@@ -543,6 +828,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": w["name"], "config": cfg, "n": n, "nnz": nnz, "E": E,
+                       "search_depth": depth, "nnz_pattern": nnz_p,
                        "K": w["K"], "nu": w["nu"], "sweep": w["sweep"], "theta": w["theta"],
                        "storage": precision, "l2": "flushed between steps (256 MiB write)",
                        "graph": "one CUDA graph per step",

@@ -351,6 +351,15 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
                     int32_t max_sets, uint64_t seed, double *rho, int32_t *n_rho);
 
 /*
+ * amgd_cr_stats -- counters of the last amgd_cr_coarsen on this handle:
+ *   *rounds (may be NULL) the selection rounds launched over all stages
+ *   (local-maximum rounds come in batches of 4 or 8, so this is at least the
+ *   number needed); *launches (may be NULL) the kernels it launched.
+ *   Errors: ARG.
+ */
+int amgd_cr_stats(amgd_handle h, int32_t *rounds, int64_t *launches);
+
+/*
  * Reverse pass.  The paper differentiates nothing; these calls give the
  * gradient of a scalar loss on the LS values with respect to the values of A
  * and the Jacobi weight omega, by the chain rule through the steps of §3

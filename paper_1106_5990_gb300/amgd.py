@@ -79,6 +79,7 @@ SIGNATURES = {
     "amgd_set_search_depth": (_int, [_P, _i32]),
     "amgd_ls_interpolation": (_int, [_P, _P, _int, _i32, _f64, _P, _P, _P, _i64, _P, _P, _int]),
     "amgd_distance_pattern": (_int, [_P, _P, _P, _i64, _P, _int]),
+    "amgd_cr_stats": (_int, [_P, _P, _P]),
     "amgd_cr_coarsen": (_int, [_P, _P, _int, _P, _int, _int, _f64, _i32, _f64, _f64, _f64, _i32,
                                _u64, _P, _P]),
     "amgd_backward": (_int, [_P, _P, _int, _P, _P, _P]),
@@ -353,6 +354,12 @@ class Handle:
                                        omega, nu, theta, delta, tol, max_sets, seed,
                                        rho.ctypes.data, ctypes.byref(m)))
         return c, rho[:m.value]
+
+    def cr_stats(self):
+        """(selection rounds, kernel launches) of the last cr_coarsen."""
+        r, l = ctypes.c_int32(), ctypes.c_int64()
+        self._ck(lib().amgd_cr_stats(self.h, ctypes.byref(r), ctypes.byref(l)))
+        return r.value, l.value
 
     # -- reverse pass ---------------------------------------------------------
     def set_checkpointing(self, every):

@@ -92,6 +92,8 @@ struct amgd_ctx {
     int32_t *ip_sel_col = nullptr, *ip_cnt = nullptr;
     double *ip_sel_val = nullptr, *ip_ls = nullptr;
     int64_t *ip_rp = nullptr;
+    int32_t *ip_pos = nullptr, *ip_list = nullptr, *ip_bcnt = nullptr;
+    uint8_t *ip_bkt = nullptr;
     void *ip_out = nullptr;
     size_t ip_out_bytes = 0;
     // compatible-relaxation coarsening working buffers
@@ -102,6 +104,8 @@ struct amgd_ctx {
     int32_t *cr_lam = nullptr;
     uint64_t *cr_key = nullptr;
     unsigned long long *cr_scal = nullptr;
+    int32_t cr_rounds = 0;                       // selection rounds of the last amgd_cr_coarsen
+    int64_t cr_launches = 0;                     // kernels it launched
     int32_t *edge_tiles = nullptr;               // row tiles of the edge pass (over the pattern)
     int32_t n_edge_tiles = 0;
     // pattern of the fits, threshold and strength graph: the graph G_d of A^d
@@ -1345,6 +1349,10 @@ int amgd_ls_interpolation(amgd_handle h, const uint8_t *coarse, int coarse_mem, 
         CK(h, dalloc(&h->ip_cnt, (size_t)n + 8));
         CK(h, dalloc(&h->ip_ls, (size_t)n + 1));
         CK(h, dalloc(&h->ip_rp, (size_t)n + 1));
+        CK(h, dalloc(&h->ip_pos, (size_t)n));
+        CK(h, dalloc(&h->ip_list, (size_t)n));
+        CK(h, dalloc(&h->ip_bkt, (size_t)n));
+        CK(h, dalloc(&h->ip_bcnt, (size_t)kInterpBuckets));
     }
     CK(h, cudaMemcpyAsync(h->ip_coarse, coarse, (size_t)n,
                           coarse_mem == AMGD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
@@ -1376,6 +1384,12 @@ int amgd_ls_interpolation(amgd_handle h, const uint8_t *coarse, int coarse_mem, 
     a.target = h->target;
     a.caliber = caliber;
     a.gamma = gamma;
+    a.pos = h->ip_pos;
+    a.bkt = h->ip_bkt;
+    a.list = h->ip_list;
+    a.bcnt = h->ip_bcnt;
+    a.unit_w = true;
+    for (double wk : h->h_w) a.unit_w = a.unit_w && wk == 1.0;
     CK(h, cudaMemsetAsync(h->err_word, 0, sizeof(uint32_t), s));
     CK(h, launch_ls_interp(h->storage, a, s));
     CK(h, launch_row_ptr(h->ip_cnt, (int32_t)n, h->tile, h->ip_rp, s));
@@ -1482,6 +1496,9 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
     a.theta = theta;
     int32_t stage = 0;
     unsigned long long scal[3] = {0, 0, 0};
+    const int64_t sweep_launches = sweep == AMGD_SWEEP_MCGS ? a.ncolors : 1;
+    h->cr_rounds = 0;
+    h->cr_launches = ls ? 0 : 1;                  // the LS export
     for (;;) {
         // nu F-relaxation sweeps from the constant start (Eq. (3.4))
         CK(h, launch_cr_start(h->cr_coarse, h->cr_u[0], (int32_t)n, s));
@@ -1496,6 +1513,7 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
         CK(h, cudaStreamSynchronize(s));
         double unorm;
         std::memcpy(&unorm, &scal[0], sizeof unorm);
+        h->cr_launches += 2 + nu * sweep_launches;
         const double r = scal[1] == 0 ? 0.0 : std::pow(unorm, 1.0 / (double)nu);
         if (rho) rho[stage] = r;
         if (!(r > delta) || stage >= max_sets) { ++stage; break; }
@@ -1509,12 +1527,15 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
             const int32_t batch = rounds < 8 ? 4 : 8;
             CK(h, launch_cr_mis_rounds(a, batch, s));
             rounds += batch;
+            h->cr_launches += 4 * (int64_t)batch + 1;
             CK(h, cudaMemcpyAsync(&scal[2], h->cr_scal + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             CK(h, cudaStreamSynchronize(s));
             if (scal[2] == 0) break;
             if (rounds > n + 8) return fail(h, AMGD_ERR_CUDA, "independent-set rounds did not finish");
         }
         CK(h, launch_cr_add(a, s));
+        h->cr_launches += 4;                      // candidates, strength, keys, add
+        h->cr_rounds += (int32_t)rounds;
         ++stage;
     }
     CK(h, cudaMemcpyAsync(coarse, h->cr_coarse, (size_t)n,
@@ -1522,6 +1543,14 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
     CK(h, cudaStreamSynchronize(s));
     if (n_rho) *n_rho = stage;
     return poll_status(h);
+}
+
+int amgd_cr_stats(amgd_handle h, int32_t *rounds, int64_t *launches)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (rounds) *rounds = h->cr_rounds;
+    if (launches) *launches = h->cr_launches;
+    return AMGD_OK;
 }
 
 int amgd_set_checkpointing(amgd_handle h, int32_t every)
@@ -1838,7 +1867,7 @@ int amgd_destroy(amgd_handle h)
                     h->s_col_tmp, h->tmp64, h->ckpt, h->seg, h->adj_vec, h->adj_slot, h->lsb,
                     h->adj_part, h->at_rp, h->at_row, h->at_slot, h->edge_tiles, h->mirror,
                     h->ip_coarse, h->ip_sel_col, h->ip_cnt, h->ip_sel_val, h->ip_ls, h->ip_rp,
-                    h->ip_out, h->color_o, h->cr_u[0], h->cr_u[1], h->cr_coarse, h->cr_state,
+                    h->ip_out, h->ip_pos, h->ip_list, h->ip_bcnt, h->ip_bkt, h->color_o, h->cr_u[0], h->cr_u[1], h->cr_coarse, h->cr_state,
                     h->cr_ismax, h->cr_strong, h->cr_lam, h->cr_key, h->cr_scal};
     for (void *p : ptrs) dfree(p);
     delete h;

@@ -314,9 +314,18 @@ struct InterpArgs {
     int32_t *cnt;                   // n chosen sizes (coarse rows: 1)
     double *ls;                     // n chosen LS
     uint32_t *err;                  // bit 1: a row had more than kInterpMaxCand candidates
+    int32_t *pos;                   // n: position of a fine row inside its bucket
+    uint8_t *bkt;                   // n: bucket of a fine row (candidate count, capped)
+    int32_t *list;                  // n: fine rows grouped by bucket
+    int32_t *bcnt;                  // kInterpBuckets bucket sizes (zeroed by the launcher)
     int32_t n, K, Kp, target, caliber;
     double gamma;
+    bool unit_w;                    // all weights are 1 (the products by w are exact)
 };
+// fine rows with at most kInterpRowCand candidates take the thread-per-row
+// kernel; bucket kInterpRowCand + 1 holds the rest (warp-per-row kernel)
+constexpr int kInterpRowCand = 8;
+constexpr int kInterpBuckets = kInterpRowCand + 2;
 cudaError_t launch_ls_interp(int storage, const InterpArgs &a, cudaStream_t s);
 // P as CSR from the fixed-stride selections and row_ptr
 cudaError_t launch_interp_fill(const int64_t *row_ptr, const int32_t *sel_col,

@@ -6,19 +6,24 @@
 // one only if its LS, normalised by S_yy = sum_k w_k y_ik^2, is below the
 // smaller set's normalised LS raised to gamma times the size difference).
 //
-// One warp per fine row, all in FP64 (the vectors are widened exactly):
+// All arithmetic is FP64 (the vectors are widened exactly), in the operation
+// order of the definition:
 //   * target y_i from row i of A, the same fused multiply-adds as the sweeps;
-//   * candidate vectors x_j (the coarse entries of the neighbourhood, at most
-//     32) into shared memory; Gram entries G_ab = sum_k (w_k x_ak) x_bk and
-//     b_a = sum_k (w_k y_k) x_ak, one product and one addition per term in
-//     component order (explicit roundings, no fused operations);
-//   * every subset of each size (combinatorial unranking, lexicographic
-//     order) is solved by Gaussian elimination with partial pivoting and
-//     scored by its residual sum of squares, with the same operation order;
-//     a warp reduction keeps the smallest LS per size, the first set in
-//     lexicographic order on ties.
-// Every rounding follows the documented order of the definition, so the
-// selected sets and weights are reproducible bit for bit.
+//   * Gram entries G_ab = sum_k (w_k x_ak) x_bk and b_a = sum_k (w_k y_k) x_ak,
+//     one product and one addition per term in component order (explicit
+//     roundings, no fused operations);
+//   * every subset of each size, in lexicographic order, solved by Gaussian
+//     elimination with partial pivoting and scored by its residual sum of
+//     squares; the first set in lexicographic order with the smallest LS is
+//     kept for each size.
+// Every rounding follows that order, so the selected sets and weights are
+// reproducible bit for bit, whichever kernel evaluates a row.
+//
+// FP64 issue rate is the bound (a GB300 SM retires two FP64 operations per
+// clock), so lanes must not idle: fine rows are first grouped by their
+// candidate count m; rows with m <= kInterpRowCand are evaluated one thread
+// per row (its arrays in shared memory, interleaved across the block's
+// threads), the rest one warp per row (lanes over Gram entries and subsets).
 #include <math.h>
 
 #include "amgd_internal.cuh"
@@ -33,12 +38,28 @@ constexpr int kWarpDoubles = kInterpMaxCand * kMaxK + kInterpMaxCand * kInterpMa
                              kInterpMaxCand + 2 * kMaxK + kInterpMaxCand / 2;
 constexpr int kInterpSmem = kWarps * kWarpDoubles * (int)sizeof(double);
 
+// exact widening to double.  Normal BF16/FP32 numbers are re-biased by bit
+// manipulation on the integer pipe (exponent + 1023 - 127, mantissa shifted
+// to the top of the 52-bit field); zeros, subnormals, infinities and NaNs
+// take the conversion instruction.
+__device__ __forceinline__ double widen_f32_bits(uint32_t u)
+{
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)__uint_as_float(u);
+    const uint64_t bits = ((uint64_t)(u >> 31) << 63) | ((uint64_t)(e + 896u) << 52) |
+                          ((uint64_t)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 template <class TS> __device__ __forceinline__ double widen(const TS *p, int k);
 template <> __device__ __forceinline__ double widen<double>(const double *p, int k) { return p[k]; }
-template <> __device__ __forceinline__ double widen<float>(const float *p, int k) { return (double)p[k]; }
+template <> __device__ __forceinline__ double widen<float>(const float *p, int k)
+{
+    return widen_f32_bits(__float_as_uint(p[k]));
+}
 template <> __device__ __forceinline__ double widen<__nv_bfloat16>(const __nv_bfloat16 *p, int k)
 {
-    return (double)__bfloat162float(p[k]);
+    return widen_f32_bits((uint32_t)__bfloat16_as_ushort(p[k]) << 16);
 }
 
 // C(nn, kk) for nn <= 32, kk <= 4
@@ -64,16 +85,11 @@ __device__ __forceinline__ void unrank(int m, int s, int64_t t, int *idx)
     }
 }
 
-// the subset's fit: 0 and p, res, or -1 when the normal equations are singular
-__device__ int fit_subset(int s, const int *idx, const double *G, const double *b, int m,
-                          const double *xs, const double *y, const double *w, int K, double *p,
-                          double &res)
+// Gs p = bs (s x s, row-major, copies of the subset's entries) by Gaussian
+// elimination with partial pivoting; -1 when a pivot is below 1e-13 of the
+// largest diagonal entry (singular set)
+__device__ __forceinline__ int solve_small(int s, double *Gs, double *bs, double *p)
 {
-    double Gs[kInterpMaxCaliber * kInterpMaxCaliber], bs[kInterpMaxCaliber];
-    for (int a = 0; a < s; ++a) {
-        bs[a] = b[idx[a]];
-        for (int c = 0; c < s; ++c) Gs[a * s + c] = G[idx[a] * m + idx[c]];
-    }
     double dmax = 0.0;
     for (int a = 0; a < s; ++a) dmax = fmax(dmax, fabs(Gs[a * s + a]));
     for (int k = 0; k < s; ++k) {
@@ -102,6 +118,20 @@ __device__ int fit_subset(int s, const int *idx, const double *G, const double *
         for (int c = k + 1; c < s; ++c) t = __dsub_rn(t, __dmul_rn(Gs[k * s + c], p[c]));
         p[k] = __ddiv_rn(t, Gs[k * s + k]);
     }
+    return 0;
+}
+
+// the subset's fit: 0 and p, res, or -1 when the normal equations are singular
+__device__ int fit_subset(int s, const int *idx, const double *G, const double *b, int m,
+                          const double *xs, const double *y, const double *w, int K, double *p,
+                          double &res)
+{
+    double Gs[kInterpMaxCaliber * kInterpMaxCaliber], bs[kInterpMaxCaliber];
+    for (int a = 0; a < s; ++a) {
+        bs[a] = b[idx[a]];
+        for (int c = 0; c < s; ++c) Gs[a * s + c] = G[idx[a] * m + idx[c]];
+    }
+    if (solve_small(s, Gs, bs, p) != 0) return -1;
     double r = 0.0;
     for (int k = 0; k < K; ++k) {
         double e = y[k];
@@ -128,17 +158,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_ls_interp(InterpArgs A)
     for (int k = lane; k < K; k += 32) w[k] = A.w64[k];
     __syncwarp();
 
+    // the rows of the last bucket (more than kInterpRowCand candidates)
+    int32_t lo = 0;
+    for (int q = 0; q <= kInterpRowCand; ++q) lo += A.bcnt[q];
+    const int32_t hi = lo + A.bcnt[kInterpRowCand + 1];
     const int64_t warps = (int64_t)gridDim.x * kWarps;
-    for (int64_t i = (int64_t)blockIdx.x * kWarps + wib; i < A.n; i += warps) {
-        if (A.coarse[i]) {
-            if (lane == 0) {
-                A.cnt[i] = 1;
-                A.sel_col[i * kInterpMaxCaliber] = (int32_t)i;
-                A.sel_val[i * kInterpMaxCaliber] = 1.0;
-                A.ls[i] = 0.0;
-            }
-            continue;
-        }
+    for (int64_t e = lo + (int64_t)blockIdx.x * kWarps + wib; e < hi; e += warps) {
+        const int64_t i = A.list[e];
         // target y_i (the sweeps' rounding: one FMA per entry, x - (1/a_ii) s)
         const int p0 = A.rp[i], p1 = A.rp[i + 1];
         for (int k = lane; k < K; k += 32) {
@@ -251,6 +277,198 @@ __global__ void __launch_bounds__(kWarps * 32) k_ls_interp(InterpArgs A)
     }
 }
 
+// coarse rows interpolate themselves; fine rows get their candidate count
+// (bucket min(m, kInterpRowCand + 1)) and a position inside the bucket
+__global__ void k_interp_classify(InterpArgs A)
+{
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+        if (A.coarse[i]) {
+            A.cnt[i] = 1;
+            A.sel_col[(int64_t)i * kInterpMaxCaliber] = i;
+            A.sel_val[(int64_t)i * kInterpMaxCaliber] = 1.0;
+            A.ls[i] = 0.0;
+            continue;
+        }
+        int m = 0;
+        const int q1 = A.prp[i + 1];
+        for (int q = A.prp[i]; q < q1; ++q) m += A.coarse[A.pcol[q]] != 0;
+        if (m > kInterpMaxCand) {
+            atomicOr(A.err, 1u);
+            A.cnt[i] = 0;
+            A.ls[i] = __longlong_as_double(0x7ff8000000000000ll);   // NaN
+            A.bkt[i] = 0xff;
+            continue;
+        }
+        const int b = m <= kInterpRowCand ? m : kInterpRowCand + 1;
+        A.bkt[i] = (uint8_t)b;
+        A.pos[i] = atomicAdd(&A.bcnt[b], 1);
+    }
+}
+
+// list = buckets kInterpRowCand, ..., 1, 0 (largest candidate count first, so
+// that a warp's rows carry equal work), then bucket kInterpRowCand + 1
+__global__ void k_interp_list(InterpArgs A)
+{
+    int32_t off[kInterpBuckets];
+    int32_t acc = 0;
+    for (int b = kInterpRowCand; b >= 0; --b) {
+        off[b] = acc;
+        acc += A.bcnt[b];
+    }
+    off[kInterpRowCand + 1] = acc;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+        if (A.coarse[i]) continue;
+        const uint8_t b = A.bkt[i];
+        if (b == 0xff) continue;
+        A.list[off[b] + A.pos[i]] = i;
+    }
+}
+
+// one thread per fine row with m <= kInterpRowCand candidates.  Per-thread
+// arrays live in shared memory, element e of thread t at [e * T + t] (T the
+// block size), so that a warp's accesses fall in distinct banks.
+template <class TS, bool UNIT_W>
+__global__ void __launch_bounds__(128) k_ls_interp_rows(InterpArgs A)
+{
+    extern __shared__ __align__(16) double rsm[];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int K = A.K, Kp = A.Kp, C = A.caliber;
+    constexpr int MT = kInterpRowCand;
+    double *yv = rsm + t;                        // y_k        at yv[k * T]
+    double *Gm = yv + (size_t)K * T;              // G_ab       at Gm[(a * MT + b) * T]
+    double *bv = Gm + (size_t)MT * MT * T;        // b_a        at bv[a * T]
+    int32_t *cd = reinterpret_cast<int32_t *>(rsm + (size_t)(K + MT * MT + MT) * T) + t;
+    const TS *X = (const TS *)A.x;
+    int32_t nrows = 0;
+    for (int q = 0; q <= MT; ++q) nrows += A.bcnt[q];
+    for (int32_t e = blockIdx.x * T + t; e < nrows; e += gridDim.x * T) {
+        const int32_t i = A.list[e];
+        // target: y_k = x_ik - (1/a_ii) sum_p a_ip x_{col_p,k}, one FMA per
+        // entry in CSR order (row sums accumulated in place, entry by entry)
+        const int p0 = A.rp[i], p1 = A.rp[i + 1];
+        for (int k = 0; k < K; ++k) yv[k * T] = 0.0;
+        double d = 1.0;
+        for (int p = p0; p < p1; ++p) {
+            const int j = A.col[p];
+            const double v = A.val64[p];
+            if (j == i) d = v;
+            const TS *xr = X + (int64_t)j * Kp;
+            for (int k = 0; k < K; ++k) yv[k * T] = fma(v, widen<TS>(xr, k), yv[k * T]);
+        }
+        {
+            const TS *xi = X + (int64_t)i * Kp;
+            const double c = -(1.0 / d);
+            for (int k = 0; k < K; ++k) {
+                const double xik = widen<TS>(xi, k);
+                yv[k * T] = A.target == 0 ? fma(c, yv[k * T], xik) : xik;
+            }
+        }
+        // candidates, ascending
+        int m = 0;
+        {
+            const int q1 = A.prp[i + 1];
+            for (int q = A.prp[i]; q < q1; ++q) {
+                const int j = A.pcol[q];
+                if (A.coarse[j]) cd[(m++) * T] = j;
+            }
+        }
+        // Gram matrix row by row (row a kept in registers), right-hand side, S_yy
+        for (int a = 0; a < m; ++a) {
+            double g[MT];
+#pragma unroll
+            for (int c = 0; c < MT; ++c) g[c] = 0.0;
+            double ba = 0.0;
+            const TS *xa = X + (int64_t)cd[a * T] * Kp;
+            for (int k = 0; k < K; ++k) {
+                const double xak = widen<TS>(xa, k);
+                const double wk = UNIT_W ? 1.0 : A.w64[k];
+                const double wxa = UNIT_W ? xak : __dmul_rn(wk, xak);
+                const double yk = yv[k * T];
+                const double wy = UNIT_W ? yk : __dmul_rn(wk, yk);
+                ba = __dadd_rn(ba, __dmul_rn(wy, xak));
+#pragma unroll
+                for (int c = 0; c < MT; ++c)
+                    if (c < m) g[c] = __dadd_rn(g[c], __dmul_rn(wxa, widen<TS>(X + (int64_t)cd[c * T] * Kp, k)));
+            }
+#pragma unroll
+            for (int c = 0; c < MT; ++c)
+                if (c < m) Gm[(a * MT + c) * T] = g[c];
+            bv[a * T] = ba;
+        }
+        double syy = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double yk = yv[k * T];
+            const double wy = UNIT_W ? yk : __dmul_rn(A.w64[k], yk);
+            syy = __dadd_rn(syy, __dmul_rn(wy, yk));
+        }
+        // every subset of each size in lexicographic order; first smallest LS
+        double best_ls[kInterpMaxCaliber + 1];
+        int best_idx[kInterpMaxCaliber + 1][kInterpMaxCaliber];
+        double best_p[kInterpMaxCaliber + 1][kInterpMaxCaliber];
+        bool have[kInterpMaxCaliber + 1];
+        have[0] = true;
+        best_ls[0] = syy;
+#pragma unroll
+        for (int s = 1; s <= kInterpMaxCaliber; ++s) {
+            have[s] = false;
+            if (s > C || s > m) continue;
+            int idx[kInterpMaxCaliber];
+            for (int a = 0; a < s; ++a) idx[a] = a;
+            for (;;) {
+                double Gs[kInterpMaxCaliber * kInterpMaxCaliber], bs[kInterpMaxCaliber];
+                double p[kInterpMaxCaliber];
+                for (int a = 0; a < s; ++a) {
+                    bs[a] = bv[idx[a] * T];
+                    for (int c = 0; c < s; ++c) Gs[a * s + c] = Gm[(idx[a] * MT + idx[c]) * T];
+                }
+                if (solve_small(s, Gs, bs, p) == 0) {
+                    double r = 0.0;
+                    for (int k = 0; k < K; ++k) {
+                        double ek = yv[k * T];
+                        for (int a = 0; a < s; ++a)
+                            ek = __dsub_rn(ek, __dmul_rn(p[a], widen<TS>(X + (int64_t)cd[idx[a] * T] * Kp, k)));
+                        const double we = UNIT_W ? ek : __dmul_rn(A.w64[k], ek);
+                        r = __dadd_rn(r, __dmul_rn(we, ek));
+                    }
+                    if (!have[s] || r < best_ls[s]) {
+                        have[s] = true;
+                        best_ls[s] = r;
+                        for (int a = 0; a < s; ++a) {
+                            best_idx[s][a] = idx[a];
+                            best_p[s][a] = p[a];
+                        }
+                    }
+                }
+                // next subset in lexicographic order
+                int a = s - 1;
+                while (a >= 0 && idx[a] == m - s + a) --a;
+                if (a < 0) break;
+                ++idx[a];
+                for (int c = a + 1; c < s; ++c) idx[c] = idx[c - 1] + 1;
+            }
+        }
+        int chosen = 0;
+        if (syy > 0.0) {
+#pragma unroll
+            for (int s = 1; s <= kInterpMaxCaliber; ++s) {
+                if (!have[s]) continue;
+                const double cur = best_ls[chosen] / syy;
+                if (best_ls[s] / syy < pow(cur, A.gamma * (double)(s - chosen))) chosen = s;
+            }
+        }
+        A.cnt[i] = chosen;
+        A.ls[i] = best_ls[chosen];
+#pragma unroll
+        for (int s = 1; s <= kInterpMaxCaliber; ++s) {
+            if (s != chosen) continue;
+            for (int a = 0; a < s; ++a) {
+                A.sel_col[(int64_t)i * kInterpMaxCaliber + a] = cd[best_idx[s][a] * T];
+                A.sel_val[(int64_t)i * kInterpMaxCaliber + a] = best_p[s][a];
+            }
+        }
+    }
+}
+
 __global__ void k_interp_fill(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ sel_col,
                               const double *__restrict__ sel_val, int32_t n,
                               int32_t *__restrict__ p_col, double *__restrict__ p_val)
@@ -264,38 +482,63 @@ __global__ void k_interp_fill(const int64_t *__restrict__ row_ptr, const int32_t
     }
 }
 
+template <class TS, bool UNIT_W>
+cudaError_t launch_rows_kernel(const InterpArgs &a, cudaStream_t s)
+{
+    constexpr int T = 128;
+    constexpr int MT = kInterpRowCand;
+    const size_t smem = (size_t)T * (8 * (a.K + MT * MT + MT) + 4 * MT);
+    constexpr size_t smem_max = (size_t)T * (8 * (kMaxK + MT * MT + MT) + 4 * MT);
+    static bool opted = false;
+    if (!opted) {
+        cudaError_t e = cudaFuncSetAttribute(k_ls_interp_rows<TS, UNIT_W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+        if (e != cudaSuccess) return e;
+        opted = true;
+    }
+    const int64_t want = ((int64_t)a.n + T - 1) / T;
+    const unsigned grid = (unsigned)(want < 152 * 4 ? want : 152 * 4);
+    k_ls_interp_rows<TS, UNIT_W><<<grid, T, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class TS>
+cudaError_t launch_interp_typed(const InterpArgs &a, cudaStream_t s)
+{
+    cudaError_t e = a.unit_w ? launch_rows_kernel<TS, true>(a, s) : launch_rows_kernel<TS, false>(a, s);
+    if (e != cudaSuccess) return e;
+    static bool opted = false;
+    if (!opted) {
+        e = cudaFuncSetAttribute(k_ls_interp<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kInterpSmem);
+        if (e != cudaSuccess) return e;
+        opted = true;
+    }
+    const int64_t want = ((int64_t)a.n + kWarps - 1) / kWarps;
+    const unsigned grid = (unsigned)(want < 152 * 4 ? want : 152 * 4);
+    k_ls_interp<TS><<<grid, kWarps * 32, kInterpSmem, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_ls_interp(int storage, const InterpArgs &a, cudaStream_t s)
 {
     if (a.n == 0) return cudaSuccess;
     if (a.K > kMaxK || a.caliber < 1 || a.caliber > kInterpMaxCaliber) return cudaErrorInvalidValue;
-    const int64_t want = ((int64_t)a.n + kWarps - 1) / kWarps;
-    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
-    static bool opted[3] = {false, false, false};
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(a.bcnt, 0, kInterpBuckets * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const int64_t nb = ((int64_t)a.n + 255) / 256;
+    const unsigned g = (unsigned)(nb < 152 * 16 ? nb : 152 * 16);
+    k_interp_classify<<<g, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_interp_list<<<g, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     switch (storage) {
-    case ST_FP64:
-        if (!opted[0]) e = cudaFuncSetAttribute(k_ls_interp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kInterpSmem);
-        if (e != cudaSuccess) return e;
-        opted[0] = true;
-        k_ls_interp<double><<<grid, kWarps * 32, kInterpSmem, s>>>(a);
-        break;
-    case ST_FP32:
-        if (!opted[1]) e = cudaFuncSetAttribute(k_ls_interp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kInterpSmem);
-        if (e != cudaSuccess) return e;
-        opted[1] = true;
-        k_ls_interp<float><<<grid, kWarps * 32, kInterpSmem, s>>>(a);
-        break;
-    case ST_BF16:
-        if (!opted[2]) e = cudaFuncSetAttribute(k_ls_interp<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kInterpSmem);
-        if (e != cudaSuccess) return e;
-        opted[2] = true;
-        k_ls_interp<__nv_bfloat16><<<grid, kWarps * 32, kInterpSmem, s>>>(a);
-        break;
+    case ST_FP64: return launch_interp_typed<double>(a, s);
+    case ST_FP32: return launch_interp_typed<float>(a, s);
+    case ST_BF16: return launch_interp_typed<__nv_bfloat16>(a, s);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_interp_fill(const int64_t *row_ptr, const int32_t *sel_col,

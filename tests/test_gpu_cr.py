@@ -131,8 +131,16 @@ def test_cr_full_size_aniso9_1024():
         t0 = time.perf_counter()
         Cg, rg = h.cr_coarsen(None, ls=want["ls"], sweep=amgd.AMGD_SWEEP_MCGS, **args)
         t_gpu = time.perf_counter() - t0
+        rounds, launches = h.cr_stats()
     print("CR 1024^2: %d stages, |C| = %d, rho %s; oracle %.2f s, GPU %.1f ms (host LS copy "
-          "included)" % (len(rw), Cw.sum(), np.round(rw, 3), t_or, 1e3 * t_gpu))
+          "included); %d selection rounds, %d kernels" % (len(rw), Cw.sum(), np.round(rw, 3),
+                                                        t_or, 1e3 * t_gpu, rounds, launches))
+    stages = len(rw)
+    assert rounds >= 4 * (stages - 1)
+    # per stage: start, 5 sweeps x 2 colors, norm; per added set: candidates,
+    # strength, keys, add, 4 kernels per round and one count per batch of rounds
+    lower = stages * 12 + (stages - 1) * 4 + 4 * rounds
+    assert lower < launches <= lower + rounds // 4
     assert np.array_equal(rg, rw)
     assert np.array_equal(Cg, Cw)
 

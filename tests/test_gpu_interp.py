@@ -47,7 +47,7 @@ def _stored(X, prec):
 
 
 @pytest.mark.parametrize("name", ["aniso5_24", "random_500"])
-@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 @pytest.mark.parametrize("d,c,gamma", [(1, 2, 1.5), (2, 3, 1.5), (2, 4, 0.0), (2, 1, 1.5)])
 def test_interp_matches_oracle(name, prec, d, c, gamma):
     rp, col, val, coarse, color = _case(name)
@@ -79,6 +79,30 @@ def test_interp_matches_oracle(name, prec, d, c, gamma):
     # coarse rows interpolate themselves
     for i in np.nonzero(coarse)[0][:50]:
         assert got[1][got[0][i]:got[0][i + 1]].tolist() == [i]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_interp_unit_weights_both_kernels(prec):
+    """Unit weights (the products by w are exact and skipped) on a pattern
+    whose fine rows have from 0 to more than 8 coarse candidates, so that
+    one call runs the thread-per-row and the warp-per-row kernels."""
+    rp, col, val = inputs.random_csr(1500, 2.5, 21, symmetric_pattern=True)   # m: 0 .. 25
+    n, K = len(rp) - 1, 16
+    coarse = (np.random.default_rng(3).random(n) < 0.45).astype(np.uint8)
+    X = _stored(oracle.relax(rp, col, val, oracle.tv_init(n, K, 2), 2, 0.7), prec)
+    prp, pcol = oracle.distance_graph(rp, col, 2)
+    rows = np.repeat(np.arange(n), np.diff(prp))
+    m = np.bincount(rows[coarse[pcol] == 1], minlength=n)[coarse == 0]
+    assert m.max() > 8 and m.min() == 0
+    with amgd.Handle(rp, col, val, K, 2) as h:
+        h.set_precision(prec)
+        h.set_search_depth(2)
+        h.set_vectors(X)
+        got = h.ls_interpolation(coarse, 2, 1.5)
+    Y = oracle.target(rp, col, val, X)
+    want = oracle.ls_interp(X, Y, prp, pcol, coarse, 2, 1.5)
+    for g, w_ in zip(got, want):
+        assert np.array_equal(g, w_)
 
 
 def test_interp_too_many_candidates():
