@@ -97,9 +97,9 @@ struct amgd_ctx {
     void *ip_out = nullptr;
     size_t ip_out_bytes = 0;
     // compatible-relaxation coarsening working buffers
-    int32_t *color_o = nullptr;                  // caller-order colors (set by amgd_set_coloring)
     double *cr_u[2] = {nullptr, nullptr};
     uint8_t *cr_coarse = nullptr, *cr_state = nullptr, *cr_ismax = nullptr, *cr_strong = nullptr;
+    uint8_t *cr_coarse_p = nullptr;              // coarse mask in the sweeps' row order
     size_t cr_strong_len = 0;
     int32_t *cr_lam = nullptr;
     uint64_t *cr_key = nullptr;
@@ -817,8 +817,6 @@ int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int 
     CK(h, launch_import(h->storage, h->tmp64, h->x[h->cur], h->perm, (int32_t)n, h->K,
                         Kp_of(h->storage, h->K), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    if (!h->color_o) CK(h, dalloc(&h->color_o, (size_t)n));
-    if (n) CK(h, cudaMemcpy(h->color_o, c.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
     h->color_start = start;
     h->have_dist = false;
     h->traj_valid = false;
@@ -1436,7 +1434,7 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
         !std::isfinite(delta) || !std::isfinite(tol))
         return fail(h, AMGD_ERR_ARG, "omega, theta, delta and tol must be finite (omega != 0, theta >= 0)");
     if (sweep != AMGD_SWEEP_JACOBI && sweep != AMGD_SWEEP_MCGS) return fail(h, AMGD_ERR_ARG, "unknown sweep type");
-    if (sweep == AMGD_SWEEP_MCGS && !h->color_o)
+    if (sweep == AMGD_SWEEP_MCGS && !h->perm)
         return fail(h, AMGD_ERR_STATE, "MCGS needs amgd_set_coloring first");
     if (!coarse && h->n) return fail(h, AMGD_ERR_ARG, "NULL coarse mask");
     if ((coarse_mem != AMGD_MEM_HOST && coarse_mem != AMGD_MEM_DEVICE) ||
@@ -1474,13 +1472,14 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
     }
     CK(h, cudaMemcpyAsync(h->cr_coarse, coarse, (size_t)n,
                           coarse_mem == AMGD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    if (!h->cr_coarse_p) CK(h, dalloc(&h->cr_coarse_p, (size_t)n));
     CrArgs a;
-    a.rp = h->rp_o;
-    a.col = h->col_o;
-    a.val = h->val_o;
-    a.dslot = h->diag_slot;
-    a.color = h->color_o;
-    a.ncolors = (int32_t)h->color_start.size() - 1;
+    a.rp = h->rp_p;
+    a.col = h->col_p;
+    a.val = h->val64;
+    a.diag = h->diag64;
+    a.perm = h->perm;
+    a.coarse_p = h->cr_coarse_p;
     a.prp = h->prp;
     a.pcol = h->pcol;
     a.ls = d_ls;
@@ -1496,19 +1495,21 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
     a.theta = theta;
     int32_t stage = 0;
     unsigned long long scal[3] = {0, 0, 0};
-    const int64_t sweep_launches = sweep == AMGD_SWEEP_MCGS ? a.ncolors : 1;
+    const int32_t ncolors = (int32_t)h->color_start.size() - 1;
+    const int64_t sweep_launches = sweep == AMGD_SWEEP_MCGS ? ncolors : 1;
     h->cr_rounds = 0;
     h->cr_launches = ls ? 0 : 1;                  // the LS export
     for (;;) {
         // nu F-relaxation sweeps from the constant start (Eq. (3.4))
-        CK(h, launch_cr_start(h->cr_coarse, h->cr_u[0], (int32_t)n, s));
+        CK(h, launch_cr_start(a, h->cr_u[0], s));
         int cu = 0;
         for (int32_t it = 0; it < nu; ++it) {
-            CK(h, launch_cr_sweep(a, sweep == AMGD_SWEEP_MCGS ? 1 : 0, h->cr_u[cu], h->cr_u[cu ^ 1], s));
+            CK(h, launch_cr_sweep(a, sweep == AMGD_SWEEP_MCGS, h->color_start.data(), ncolors,
+                                  h->cr_u[cu], h->cr_u[cu ^ 1], s));
             cu ^= 1;
         }
         // the convergence estimate of Eq. (3.5) in the max norm (||u^0|| = 1)
-        CK(h, launch_cr_norm(h->cr_u[cu], h->cr_coarse, (int32_t)n, h->cr_scal, s));
+        CK(h, launch_cr_norm(h->cr_u[cu], h->cr_coarse_p, (int32_t)n, h->cr_scal, s));
         CK(h, cudaMemcpyAsync(scal, h->cr_scal, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CK(h, cudaStreamSynchronize(s));
         double unorm;
@@ -1527,7 +1528,7 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
             const int32_t batch = rounds < 8 ? 4 : 8;
             CK(h, launch_cr_mis_rounds(a, batch, s));
             rounds += batch;
-            h->cr_launches += 4 * (int64_t)batch + 1;
+            h->cr_launches += 3 * (int64_t)batch + 1;
             CK(h, cudaMemcpyAsync(&scal[2], h->cr_scal + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             CK(h, cudaStreamSynchronize(s));
             if (scal[2] == 0) break;
@@ -1867,7 +1868,7 @@ int amgd_destroy(amgd_handle h)
                     h->s_col_tmp, h->tmp64, h->ckpt, h->seg, h->adj_vec, h->adj_slot, h->lsb,
                     h->adj_part, h->at_rp, h->at_row, h->at_slot, h->edge_tiles, h->mirror,
                     h->ip_coarse, h->ip_sel_col, h->ip_cnt, h->ip_sel_val, h->ip_ls, h->ip_rp,
-                    h->ip_out, h->ip_pos, h->ip_list, h->ip_bcnt, h->ip_bkt, h->color_o, h->cr_u[0], h->cr_u[1], h->cr_coarse, h->cr_state,
+                    h->ip_out, h->ip_pos, h->ip_list, h->ip_bcnt, h->ip_bkt, h->cr_u[0], h->cr_u[1], h->cr_coarse, h->cr_coarse_p, h->cr_state,
                     h->cr_ismax, h->cr_strong, h->cr_lam, h->cr_key, h->cr_scal};
     for (void *p : ptrs) dfree(p);
     delete h;

@@ -334,12 +334,12 @@ cudaError_t launch_interp_fill(const int64_t *row_ptr, const int32_t *sel_col,
 
 // compatible-relaxation coarsening (k_cr.cu; priorities in k_init.cu)
 struct CrArgs {
-    const int32_t *rp, *col;        // A, caller order
-    const double *val;              // A's values (FP64)
-    const int32_t *dslot;           // slot of each row's diagonal
-    const int32_t *color;           // caller-order colors (multicolor sweeps)
-    int32_t ncolors;
-    const int32_t *prp, *pcol;      // pattern of the strength graph (G_d)
+    const int32_t *rp, *col;        // A with rows in color order (the sweeps' layout)
+    const double *val;              // its values (FP64)
+    const double *diag;             // its diagonal
+    const int32_t *perm;            // caller row of each color-ordered row (NULL: identity)
+    uint8_t *coarse_p;              // coarse mask in color order
+    const int32_t *prp, *pcol;      // pattern of the strength graph (G_d), caller order
     const double *ls;               // LS per pattern slot (FP64)
     uint8_t *coarse;                // n, 1 = coarse
     uint8_t *state;                 // n: 0 out, 1 undecided candidate, 2 selected
@@ -351,10 +351,13 @@ struct CrArgs {
     int32_t n;
     double omega, theta;
 };
-cudaError_t launch_cr_start(const uint8_t *coarse, double *u, int32_t n, cudaStream_t s);
-// one F-relaxation sweep u -> un (sweep 0 Jacobi, 1 multicolor Gauss-Seidel)
-cudaError_t launch_cr_sweep(const CrArgs &a, int sweep, const double *u, double *un, cudaStream_t s);
-cudaError_t launch_cr_norm(const double *u, const uint8_t *coarse, int32_t n,
+// coarse_p from coarse, u = 1 on F and 0 on C (color order)
+cudaError_t launch_cr_start(const CrArgs &a, double *u, cudaStream_t s);
+// one F-relaxation sweep u -> un over color-ordered rows: Jacobi (one range
+// [0, n)) or multicolor Gauss-Seidel (one launch per color range)
+cudaError_t launch_cr_sweep(const CrArgs &a, bool mcgs, const int64_t *color_start,
+                            int32_t ncolors, const double *u, double *un, cudaStream_t s);
+cudaError_t launch_cr_norm(const double *u, const uint8_t *coarse_p, int32_t n,
                            unsigned long long *scal, cudaStream_t s);
 // candidates, strength graph on F and the priorities' lambda
 cudaError_t launch_cr_candidates(const CrArgs &a, const double *u, double tol, cudaStream_t s);

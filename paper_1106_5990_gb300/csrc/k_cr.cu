@@ -3,9 +3,11 @@
 //
 // One stage, all on the device except the scalar decision of Algorithm 1's
 // loop: F-relaxation of one vector from the constant start with the coarse
-// rows held at zero, the max norm of the result (exact: a maximum of bit
-// patterns), the candidates sigma_i = |u_i| / ||u|| > tol, the strength graph
-// restricted to F, and an independent set of the candidates.  The set is the
+// rows held at zero (on the color-ordered copy of A that the test-vector
+// sweeps use, so a color phase is one contiguous range of rows), the max norm
+// of the result (exact: a maximum of bit patterns), the candidates
+// sigma_i = |u_i| / ||u|| > tol, the strength graph restricted to F, and an
+// independent set of the candidates.  The set is the
 // greedy set in a fixed priority order (more candidates depending strongly on
 // the point first, then a Philox key, then the smaller index); it is reached
 // by rounds of local maxima, which select exactly the points the greedy order
@@ -28,46 +30,37 @@ int grid_for(int64_t n)
     return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
 }
 
-__global__ void k_cr_start(const uint8_t *__restrict__ coarse, double *__restrict__ u, int32_t n)
+// coarse mask into color order, u = 1 on F, 0 on C
+__global__ void k_cr_start(const int32_t *__restrict__ perm, const uint8_t *__restrict__ coarse,
+                           uint8_t *__restrict__ coarse_p, double *__restrict__ u, int32_t n)
 {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        u[i] = coarse[i] ? 0.0 : 1.0;
-}
-
-// weighted Jacobi on the rows of F; coarse rows stay 0 (Eq. (3.4))
-__global__ void k_cr_jacobi(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                            const double *__restrict__ val, const int32_t *__restrict__ dslot,
-                            const uint8_t *__restrict__ coarse, double omega,
-                            const double *__restrict__ u, double *__restrict__ un, int32_t n)
-{
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (coarse[i]) { un[i] = 0.0; continue; }
-        const double c = omega / val[dslot[i]];
-        double acc = 0.0;
-        const int32_t e = rp[i + 1];
-        for (int32_t p = rp[i]; p < e; ++p) acc = fma(val[p], u[col[p]], acc);
-        un[i] = fma(-c, acc, u[i]);
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const uint8_t c = coarse[perm ? perm[r] : r];
+        coarse_p[r] = c;
+        u[r] = c ? 0.0 : 1.0;
     }
 }
 
-// one color of a multicolor Gauss-Seidel sweep on the rows of F: rows of
-// smaller colors are read from un (already updated), all others from u
-__global__ void k_cr_mcgs(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                          const double *__restrict__ val, const int32_t *__restrict__ dslot,
-                          const uint8_t *__restrict__ coarse, const int32_t *__restrict__ color,
-                          int32_t cc, double omega, const double *__restrict__ u, double *un,
-                          int32_t n)
+// one F-relaxation phase over the color-ordered rows [r0, r1): weighted
+// Jacobi (r0 = 0, r1 = n, every neighbour from u), or one color of a
+// multicolor Gauss-Seidel sweep (neighbours of earlier colors -- rows below
+// r0 -- from un, all others from u).  Coarse rows stay 0 (Eq. (3.4)).
+__global__ void k_cr_sweep(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ diag,
+                           const uint8_t *__restrict__ coarse_p, int32_t r0, int32_t r1,
+                           double omega, const double *__restrict__ u, double *un)
 {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (color[i] != cc || coarse[i]) continue;
-        const double c = omega / val[dslot[i]];
+    for (int32_t r = r0 + blockIdx.x * blockDim.x + threadIdx.x; r < r1;
+         r += gridDim.x * blockDim.x) {
+        if (coarse_p[r]) { un[r] = 0.0; continue; }
+        const double c = omega / diag[r];
         double acc = 0.0;
-        const int32_t e = rp[i + 1];
-        for (int32_t p = rp[i]; p < e; ++p) {
+        const int32_t e = rp[r + 1];
+        for (int32_t p = rp[r]; p < e; ++p) {
             const int32_t j = col[p];
-            acc = fma(val[p], color[j] < cc ? un[j] : u[j], acc);
+            acc = fma(val[p], j < r0 ? un[j] : u[j], acc);
         }
-        un[i] = fma(-c, acc, u[i]);
+        un[r] = fma(-c, acc, u[r]);
     }
 }
 
@@ -102,14 +95,20 @@ __global__ void k_cr_norm(const double *__restrict__ u, const uint8_t *__restric
     }
 }
 
-// candidates (state 1) and cleared counters
-__global__ void k_cr_cand(const double *__restrict__ u, const uint8_t *__restrict__ coarse,
+// candidates (state 1, caller order) from the color-ordered u; cleared
+// counters; every candidate starts as a possible local maximum
+__global__ void k_cr_cand(const double *__restrict__ u, const uint8_t *__restrict__ coarse_p,
+                          const int32_t *__restrict__ perm,
                           const unsigned long long *__restrict__ scal, double tol,
-                          uint8_t *__restrict__ state, int32_t *__restrict__ lam, int32_t n)
+                          uint8_t *__restrict__ state, uint8_t *__restrict__ ismax,
+                          int32_t *__restrict__ lam, int32_t n)
 {
     const double unorm = __longlong_as_double((long long)scal[0]);
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        state[i] = (!coarse[i] && fabs(u[i]) / unorm > tol) ? 1 : 0;
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int32_t i = perm ? perm[r] : r;
+        const uint8_t z = (!coarse_p[r] && fabs(u[r]) / unorm > tol) ? 1 : 0;
+        state[i] = z;
+        ismax[i] = z;
         lam[i] = 0;
     }
 }
@@ -151,12 +150,6 @@ __device__ __forceinline__ bool cr_before(int32_t la, uint64_t ka, int32_t a, in
     return a < b;
 }
 
-__global__ void k_mis_init(const uint8_t *__restrict__ state, uint8_t *__restrict__ ismax, int32_t n)
-{
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        ismax[i] = state[i] == 1;
-}
-
 // of every strong pair of undecided points the later one in the order is not
 // a local maximum (each pair is seen from the row that stores the slot)
 __global__ void k_mis_compare(const int32_t *__restrict__ prp, const int32_t *__restrict__ pcol,
@@ -188,13 +181,18 @@ __global__ void k_mis_select(uint8_t *__restrict__ state, const uint8_t *__restr
 // undecided neighbours of selected points (either direction) leave the set.
 // Selected points (2) are never written: two strong neighbours are never both
 // selected, so only 1 -> 0 transitions race, and they write the same value.
+// A point that finds no selected out-neighbour re-arms its local-maximum flag
+// for the next round (if a selected in-neighbour removes it meanwhile, the
+// flag is ignored: the next rounds only read it for undecided points).
 __global__ void k_mis_remove(const int32_t *__restrict__ prp, const int32_t *__restrict__ pcol,
-                             const uint8_t *__restrict__ strong, uint8_t *state, int32_t n)
+                             const uint8_t *__restrict__ strong, uint8_t *state,
+                             uint8_t *__restrict__ ismax, int32_t n)
 {
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint8_t st = state[i];
         if (st == 0) continue;
         const int32_t e = prp[i + 1];
+        bool removed = false;
         for (int32_t q = prp[i]; q < e; ++q) {
             if (!strong[q]) continue;
             const int32_t j = pcol[q];
@@ -202,9 +200,11 @@ __global__ void k_mis_remove(const int32_t *__restrict__ prp, const int32_t *__r
                 if (state[j] == 1) state[j] = 0;
             } else if (state[j] == 2) {
                 state[i] = 0;
+                removed = true;
                 break;
             }
         }
+        if (st == 1 && !removed) ismax[i] = 1;
     }
 }
 
@@ -217,50 +217,59 @@ __global__ void k_cr_count(const uint8_t *__restrict__ state, int32_t n, unsigne
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
 }
 
-__global__ void k_cr_add(const uint8_t *__restrict__ state, uint8_t *__restrict__ coarse, int32_t n)
+__global__ void k_cr_add(const uint8_t *__restrict__ state, const int32_t *__restrict__ perm,
+                         uint8_t *__restrict__ coarse, uint8_t *__restrict__ coarse_p, int32_t n)
 {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        if (state[i] == 2) coarse[i] = 1;
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int32_t i = perm ? perm[r] : r;
+        if (state[i] == 2) {
+            coarse[i] = 1;
+            coarse_p[r] = 1;
+        }
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_cr_start(const uint8_t *coarse, double *u, int32_t n, cudaStream_t s)
+cudaError_t launch_cr_start(const CrArgs &a, double *u, cudaStream_t s)
 {
-    k_cr_start<<<grid_for(n), kThreads, 0, s>>>(coarse, u, n);
+    k_cr_start<<<grid_for(a.n), kThreads, 0, s>>>(a.perm, a.coarse, a.coarse_p, u, a.n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cr_sweep(const CrArgs &a, int sweep, const double *u, double *un, cudaStream_t s)
+cudaError_t launch_cr_sweep(const CrArgs &a, bool mcgs, const int64_t *color_start,
+                            int32_t ncolors, const double *u, double *un, cudaStream_t s)
 {
-    const int g = grid_for(a.n);
-    if (sweep == 0) {
-        k_cr_jacobi<<<g, kThreads, 0, s>>>(a.rp, a.col, a.val, a.dslot, a.coarse, a.omega, u, un, a.n);
+    if (!mcgs) {
+        k_cr_sweep<<<grid_for(a.n), kThreads, 0, s>>>(a.rp, a.col, a.val, a.diag, a.coarse_p, 0,
+                                                      a.n, a.omega, u, un);
         return cudaGetLastError();
     }
-    cudaError_t e = cudaMemcpyAsync(un, u, (size_t)a.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
-    for (int32_t cc = 0; cc < a.ncolors; ++cc) {
-        k_cr_mcgs<<<g, kThreads, 0, s>>>(a.rp, a.col, a.val, a.dslot, a.coarse, a.color, cc, a.omega,
-                                         u, un, a.n);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int32_t cc = 0; cc < ncolors; ++cc) {
+        const int32_t r0 = (int32_t)color_start[cc], r1 = (int32_t)color_start[cc + 1];
+        if (r1 <= r0) continue;
+        k_cr_sweep<<<grid_for(r1 - r0), kThreads, 0, s>>>(a.rp, a.col, a.val, a.diag, a.coarse_p,
+                                                         r0, r1, a.omega, u, un);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-cudaError_t launch_cr_norm(const double *u, const uint8_t *coarse, int32_t n,
+cudaError_t launch_cr_norm(const double *u, const uint8_t *coarse_p, int32_t n,
                            unsigned long long *scal, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(scal, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    k_cr_norm<<<grid_for(n), kThreads, 0, s>>>(u, coarse, n, scal);
+    k_cr_norm<<<grid_for(n), kThreads, 0, s>>>(u, coarse_p, n, scal);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cr_candidates(const CrArgs &a, const double *u, double tol, cudaStream_t s)
 {
     const int g = grid_for(a.n);
-    k_cr_cand<<<g, kThreads, 0, s>>>(u, a.coarse, a.scal, tol, a.state, a.lam, a.n);
+    k_cr_cand<<<g, kThreads, 0, s>>>(u, a.coarse_p, a.perm, a.scal, tol, a.state, a.ismax, a.lam,
+                                     a.n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_cr_strength<<<g, kThreads, 0, s>>>(a.prp, a.pcol, a.ls, a.coarse, a.state, a.theta, a.strong,
@@ -272,11 +281,10 @@ cudaError_t launch_cr_mis_rounds(const CrArgs &a, int32_t rounds, cudaStream_t s
 {
     const int g = grid_for(a.n);
     for (int32_t r = 0; r < rounds; ++r) {
-        k_mis_init<<<g, kThreads, 0, s>>>(a.state, a.ismax, a.n);
         k_mis_compare<<<g, kThreads, 0, s>>>(a.prp, a.pcol, a.strong, a.state, a.lam, a.key, a.ismax,
                                              a.n);
         k_mis_select<<<g, kThreads, 0, s>>>(a.state, a.ismax, a.n);
-        k_mis_remove<<<g, kThreads, 0, s>>>(a.prp, a.pcol, a.strong, a.state, a.n);
+        k_mis_remove<<<g, kThreads, 0, s>>>(a.prp, a.pcol, a.strong, a.state, a.ismax, a.n);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -288,7 +296,7 @@ cudaError_t launch_cr_mis_rounds(const CrArgs &a, int32_t rounds, cudaStream_t s
 
 cudaError_t launch_cr_add(const CrArgs &a, cudaStream_t s)
 {
-    k_cr_add<<<grid_for(a.n), kThreads, 0, s>>>(a.state, a.coarse, a.n);
+    k_cr_add<<<grid_for(a.n), kThreads, 0, s>>>(a.state, a.perm, a.coarse, a.coarse_p, a.n);
     return cudaGetLastError();
 }
 
