@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(128) k_ls_interp_rows(InterpArgs A)
     double *yv = rsm + t;                        // y_k        at yv[k * T]
     double *Gm = yv + (size_t)K * T;              // G_ab       at Gm[(a * MT + b) * T]
     double *bv = Gm + (size_t)MT * MT * T;        // b_a        at bv[a * T]
-    int32_t *cd = reinterpret_cast<int32_t *>(rsm + (size_t)(K + MT * MT + MT) * T) + t;
+    double *sg = bv + (size_t)MT * T;             // sqrt(G_aa) at sg[a * T]
+    int32_t *cd = reinterpret_cast<int32_t *>(rsm + (size_t)(K + MT * MT + 2 * MT) * T) + t;
     const TS *X = (const TS *)A.x;
     int32_t nrows = 0;
     for (int q = 0; q <= MT; ++q) nrows += A.bcnt[q];
@@ -372,7 +373,9 @@ __global__ void __launch_bounds__(128) k_ls_interp_rows(InterpArgs A)
                 if (A.coarse[j]) cd[(m++) * T] = j;
             }
         }
-        // Gram matrix row by row (row a kept in registers), right-hand side, S_yy
+        // Gram matrix row by row (row a kept in registers), right-hand side, S_yy.
+        // With unit weights G_ab = sum_k x_ak x_bk = G_ba bit for bit (the same
+        // products, summed in the same order), so only c >= a is computed.
         for (int a = 0; a < m; ++a) {
             double g[MT];
 #pragma unroll
@@ -388,12 +391,21 @@ __global__ void __launch_bounds__(128) k_ls_interp_rows(InterpArgs A)
                 ba = __dadd_rn(ba, __dmul_rn(wy, xak));
 #pragma unroll
                 for (int c = 0; c < MT; ++c)
-                    if (c < m) g[c] = __dadd_rn(g[c], __dmul_rn(wxa, widen<TS>(X + (int64_t)cd[c * T] * Kp, k)));
+                    if (c < m && (!UNIT_W || c >= a))
+                        g[c] = __dadd_rn(g[c], __dmul_rn(wxa, widen<TS>(X + (int64_t)cd[c * T] * Kp, k)));
             }
 #pragma unroll
-            for (int c = 0; c < MT; ++c)
-                if (c < m) Gm[(a * MT + c) * T] = g[c];
+            for (int c = 0; c < MT; ++c) {
+                if (c >= m) continue;
+                if (!UNIT_W) {
+                    Gm[(a * MT + c) * T] = g[c];
+                } else if (c >= a) {
+                    Gm[(a * MT + c) * T] = g[c];
+                    Gm[(c * MT + a) * T] = g[c];
+                }
+            }
             bv[a * T] = ba;
+            sg[a * T] = sqrt(Gm[(a * MT + a) * T]);
         }
         double syy = 0.0;
         for (int k = 0; k < K; ++k) {
@@ -401,6 +413,7 @@ __global__ void __launch_bounds__(128) k_ls_interp_rows(InterpArgs A)
             const double wy = UNIT_W ? yk : __dmul_rn(A.w64[k], yk);
             syy = __dadd_rn(syy, __dmul_rn(wy, yk));
         }
+        const double sy = sqrt(syy);
         // every subset of each size in lexicographic order; first smallest LS
         double best_ls[kInterpMaxCaliber + 1];
         int best_idx[kInterpMaxCaliber + 1][kInterpMaxCaliber];
@@ -421,7 +434,33 @@ __global__ void __launch_bounds__(128) k_ls_interp_rows(InterpArgs A)
                     bs[a] = bv[idx[a] * T];
                     for (int c = 0; c < s; ++c) Gs[a * s + c] = Gm[(idx[a] * MT + idx[c]) * T];
                 }
+                bool exact = false;
                 if (solve_small(s, Gs, bs, p) == 0) {
+                    exact = !have[s];
+                    if (!exact) {
+                        // Pruning.  With S, b, G the stored sums, the value
+                        //   q = S - 2 p.b + p.G.p
+                        // and the explicit residual sum both approximate
+                        // sum_k w_k (y_k - p.x_k)^2; their rounding errors are
+                        // at most (s^2 + 5s + 2K + 6) u M^2 together, with
+                        // M = ||y||_w + sum_a |p_a| ||x_a||_w (Cauchy-Schwarz,
+                        // Minkowski).  If q minus four times that bound is not
+                        // below the best explicit value of this size, the
+                        // subset can neither beat nor tie it (a tie goes to
+                        // the earlier subset), and its explicit sum is skipped.
+                        double q = syy, mm = sy;
+                        for (int a = 0; a < s; ++a) {
+                            q = __dsub_rn(q, __dmul_rn(__dmul_rn(2.0, p[a]), bv[idx[a] * T]));
+                            mm = __dadd_rn(mm, __dmul_rn(fabs(p[a]), sg[idx[a] * T]));
+                        }
+                        for (int a = 0; a < s; ++a)
+                            for (int c = 0; c < s; ++c)
+                                q = __dadd_rn(q, __dmul_rn(__dmul_rn(p[a], Gm[(idx[a] * MT + idx[c]) * T]), p[c]));
+                        const double bound = (double)(4 * (s * s + 6 * s + 2 * K + 8)) * 0x1p-53 * mm * mm;
+                        exact = !(__dsub_rn(q, bound) >= best_ls[s]);
+                    }
+                }
+                if (exact) {
                     double r = 0.0;
                     for (int k = 0; k < K; ++k) {
                         double ek = yv[k * T];
@@ -487,8 +526,8 @@ cudaError_t launch_rows_kernel(const InterpArgs &a, cudaStream_t s)
 {
     constexpr int T = 128;
     constexpr int MT = kInterpRowCand;
-    const size_t smem = (size_t)T * (8 * (a.K + MT * MT + MT) + 4 * MT);
-    constexpr size_t smem_max = (size_t)T * (8 * (kMaxK + MT * MT + MT) + 4 * MT);
+    const size_t smem = (size_t)T * (8 * (a.K + MT * MT + 2 * MT) + 4 * MT);
+    constexpr size_t smem_max = (size_t)T * (8 * (kMaxK + MT * MT + 2 * MT) + 4 * MT);
     static bool opted = false;
     if (!opted) {
         cudaError_t e = cudaFuncSetAttribute(k_ls_interp_rows<TS, UNIT_W>,

@@ -105,6 +105,36 @@ def test_interp_unit_weights_both_kernels(prec):
         assert np.array_equal(g, w_)
 
 
+@pytest.mark.parametrize("unit_w", [True, False])
+def test_interp_ties_and_exact_fits(unit_w):
+    """Plain target with planted structure: coarse candidates that repeat one
+    another exactly (ties between sets, singular pairs) and fine rows that
+    are exact combinations of two coarse neighbours (LS = 0 up to rounding),
+    so that sets whose LS values are equal or nearly equal compete."""
+    rp, col, val = inputs.random_csr(800, 3.0, 31, symmetric_pattern=True)
+    n, K = len(rp) - 1, 8
+    rng = np.random.default_rng(5)
+    coarse = (rng.random(n) < 0.45).astype(np.uint8)
+    X = rng.integers(-64, 65, size=(n, K)) / 64.0
+    base = rng.integers(-64, 65, size=K) / 64.0
+    cidx = np.flatnonzero(coarse)
+    X[cidx[::3]] = base                                     # a third of the coarse rows equal
+    for i in np.flatnonzero(coarse == 0)[::2]:
+        nb = [j for j in col[rp[i]:rp[i + 1]] if coarse[j]]
+        if len(nb) >= 2:
+            X[i] = 0.5 * X[nb[0]] - 0.25 * X[nb[1]]         # exact in FP64
+    w = np.ones(K) if unit_w else rng.uniform(0.5, 2.0, K)
+    with amgd.Handle(rp, col, val, K, 1) as h:
+        h.set_target(amgd.AMGD_TARGET_PLAIN)
+        h.set_weights(w)
+        h.set_vectors(X)
+        got = h.ls_interpolation(coarse, 3, 1.5)
+    Y = oracle.target(rp, col, val, X, oracle.TARGET_PLAIN)
+    want = oracle.ls_interp(X, Y, rp, col, coarse, 3, 1.5, w)
+    for g, w_ in zip(got, want):
+        assert np.array_equal(g, w_)
+
+
 def test_interp_too_many_candidates():
     rp, col, val = inputs.graph_laplacian(300, 12.0, 2)
     with amgd.Handle(rp, col, val, 8, 1) as h:
