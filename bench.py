@@ -548,10 +548,10 @@ def interp_flops(rp, col, coarse, K, caliber):
 
 
 def cr_sweep_bytes(n, nnz, ncolors):
-    """Algorithmic bytes of one F-relaxation sweep (K = 1, FP64 values): the
-    CSR once, the diagonal slot and value per row, the mask and colors once
-    per color phase, u read once per color phase and written once."""
-    return nnz * 12 + 4 * (n + 1) + 12 * n + ncolors * (5 * n + 8 * n) + 8 * n
+    """Algorithmic bytes of one F-relaxation sweep (K = 1, FP64 values, rows
+    in color order): the CSR, the diagonal and the coarse mask once, u read
+    once per color phase and written once."""
+    return nnz * 12 + 4 * (n + 1) + 8 * n + n + ncolors * 8 * n + 8 * n
 
 
 def run_coarsen(args, cfg, w, mats, color, precision, ws, rank, flush):
