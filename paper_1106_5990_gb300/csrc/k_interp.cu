@@ -26,6 +26,8 @@
 // threads), the rest one warp per row (lanes over Gram entries and subsets).
 #include <math.h>
 
+#include <type_traits>
+
 #include "amgd_internal.cuh"
 
 namespace amgd {
@@ -51,6 +53,18 @@ __device__ __forceinline__ double widen_f32_bits(uint32_t u)
     return __longlong_as_double((long long)bits);
 }
 
+// the product of two BF16 numbers as a double: their 8-bit significands
+// multiply exactly in FP32 whenever the result is a normal FP32 number, and
+// that number widens exactly; otherwise the FP64 product (also exact)
+__device__ __forceinline__ double bf16_product(uint16_t a, uint16_t b)
+{
+    const float p = __fmul_rn(__uint_as_float((uint32_t)a << 16), __uint_as_float((uint32_t)b << 16));
+    const uint32_t u = __float_as_uint(p);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e != 0u && e != 0xffu) return widen_f32_bits(u);
+    return __dmul_rn(widen_f32_bits((uint32_t)a << 16), widen_f32_bits((uint32_t)b << 16));
+}
+
 template <class TS> __device__ __forceinline__ double widen(const TS *p, int k);
 template <> __device__ __forceinline__ double widen<double>(const double *p, int k) { return p[k]; }
 template <> __device__ __forceinline__ double widen<float>(const float *p, int k)
@@ -60,6 +74,23 @@ template <> __device__ __forceinline__ double widen<float>(const float *p, int k
 template <> __device__ __forceinline__ double widen<__nv_bfloat16>(const __nv_bfloat16 *p, int k)
 {
     return widen_f32_bits((uint32_t)__bfloat16_as_ushort(p[k]) << 16);
+}
+
+// The size penalty's decision r < pow(c, e) (r, c normalised LS values, e =
+// gamma times the size difference), with CUDA's FP64 pow.  Most decisions are
+// far from the boundary: log2 of both sides in FP32 decides them when they
+// differ by more than a margin that covers the FP32 errors many times over;
+// the rest call pow.  The decision is therefore always the one pow gives.
+__device__ __forceinline__ bool penalty_less(double r, double c, double e)
+{
+    const float rf = (float)r, cf = (float)c;
+    if (e > 0.0 && rf >= 1.17549435e-38f && cf >= 1.17549435e-38f && rf <= 3.0e38f && cf <= 3.0e38f) {
+        const float lr = log2f(rf), lp = (float)e * log2f(cf);
+        const float margin = 1e-3f * (1.0f + fabsf(lr) + fabsf(lp));
+        if (lr < lp - margin) return true;
+        if (lr > lp + margin) return false;
+    }
+    return r < pow(c, e);
 }
 
 // C(nn, kk) for nn <= 32, kk <= 4
@@ -263,7 +294,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_ls_interp(InterpArgs A)
                 for (int s = 1; s <= kInterpMaxCaliber; ++s) {
                     if (!have[s]) continue;
                     const double cur = best_ls[chosen] / syy;
-                    if (best_ls[s] / syy < pow(cur, A.gamma * (double)(s - chosen))) chosen = s;
+                    if (penalty_less(best_ls[s] / syy, cur, A.gamma * (double)(s - chosen))) chosen = s;
                 }
             }
             A.cnt[i] = chosen;
@@ -281,28 +312,40 @@ __global__ void __launch_bounds__(kWarps * 32) k_ls_interp(InterpArgs A)
 // (bucket min(m, kInterpRowCand + 1)) and a position inside the bucket
 __global__ void k_interp_classify(InterpArgs A)
 {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+    // one row per thread; bucket positions come from block-local counters,
+    // one global atomic per bucket and block
+    __shared__ int32_t cnt_s[kInterpBuckets], base_s[kInterpBuckets];
+    if (threadIdx.x < kInterpBuckets) cnt_s[threadIdx.x] = 0;
+    __syncthreads();
+    const int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    int b = -1, local = 0;
+    if (i < A.n) {
         if (A.coarse[i]) {
             A.cnt[i] = 1;
             A.sel_col[(int64_t)i * kInterpMaxCaliber] = i;
             A.sel_val[(int64_t)i * kInterpMaxCaliber] = 1.0;
             A.ls[i] = 0.0;
-            continue;
+        } else {
+            int m = 0;
+            const int q1 = A.prp[i + 1];
+            for (int q = A.prp[i]; q < q1; ++q) m += A.coarse[A.pcol[q]] != 0;
+            if (m > kInterpMaxCand) {
+                atomicOr(A.err, 1u);
+                A.cnt[i] = 0;
+                A.ls[i] = __longlong_as_double(0x7ff8000000000000ll);   // NaN
+                A.bkt[i] = 0xff;
+            } else {
+                b = m <= kInterpRowCand ? m : kInterpRowCand + 1;
+                A.bkt[i] = (uint8_t)b;
+                local = atomicAdd(&cnt_s[b], 1);
+            }
         }
-        int m = 0;
-        const int q1 = A.prp[i + 1];
-        for (int q = A.prp[i]; q < q1; ++q) m += A.coarse[A.pcol[q]] != 0;
-        if (m > kInterpMaxCand) {
-            atomicOr(A.err, 1u);
-            A.cnt[i] = 0;
-            A.ls[i] = __longlong_as_double(0x7ff8000000000000ll);   // NaN
-            A.bkt[i] = 0xff;
-            continue;
-        }
-        const int b = m <= kInterpRowCand ? m : kInterpRowCand + 1;
-        A.bkt[i] = (uint8_t)b;
-        A.pos[i] = atomicAdd(&A.bcnt[b], 1);
     }
+    __syncthreads();
+    if (threadIdx.x < kInterpBuckets && cnt_s[threadIdx.x] > 0)
+        base_s[threadIdx.x] = atomicAdd(&A.bcnt[threadIdx.x], cnt_s[threadIdx.x]);
+    __syncthreads();
+    if (b >= 0) A.pos[i] = base_s[b] + local;
 }
 
 // list = buckets kInterpRowCand, ..., 1, 0 (largest candidate count first, so
@@ -389,10 +432,21 @@ __global__ void __launch_bounds__(128) k_ls_interp_rows(InterpArgs A)
                 const double yk = yv[k * T];
                 const double wy = UNIT_W ? yk : __dmul_rn(wk, yk);
                 ba = __dadd_rn(ba, __dmul_rn(wy, xak));
+                if constexpr (UNIT_W && std::is_same<TS, __nv_bfloat16>::value) {
+                    // x_ak x_ck of two BF16 numbers: exact FP32 product (bit-equal
+                    // to the FP64 product), one FP64 addition per term
+                    const uint16_t ab = __bfloat16_as_ushort(xa[k]);
 #pragma unroll
-                for (int c = 0; c < MT; ++c)
-                    if (c < m && (!UNIT_W || c >= a))
-                        g[c] = __dadd_rn(g[c], __dmul_rn(wxa, widen<TS>(X + (int64_t)cd[c * T] * Kp, k)));
+                    for (int c = 0; c < MT; ++c)
+                        if (c < m && c >= a)
+                            g[c] = __dadd_rn(g[c], bf16_product(ab, __bfloat16_as_ushort(
+                                                                        X[(int64_t)cd[c * T] * Kp + k])));
+                } else {
+#pragma unroll
+                    for (int c = 0; c < MT; ++c)
+                        if (c < m && (!UNIT_W || c >= a))
+                            g[c] = __dadd_rn(g[c], __dmul_rn(wxa, widen<TS>(X + (int64_t)cd[c * T] * Kp, k)));
+                }
             }
 #pragma unroll
             for (int c = 0; c < MT; ++c) {
@@ -492,7 +546,7 @@ __global__ void __launch_bounds__(128) k_ls_interp_rows(InterpArgs A)
             for (int s = 1; s <= kInterpMaxCaliber; ++s) {
                 if (!have[s]) continue;
                 const double cur = best_ls[chosen] / syy;
-                if (best_ls[s] / syy < pow(cur, A.gamma * (double)(s - chosen))) chosen = s;
+                if (penalty_less(best_ls[s] / syy, cur, A.gamma * (double)(s - chosen))) chosen = s;
             }
         }
         A.cnt[i] = chosen;
@@ -568,7 +622,7 @@ cudaError_t launch_ls_interp(int storage, const InterpArgs &a, cudaStream_t s)
     if (e != cudaSuccess) return e;
     const int64_t nb = ((int64_t)a.n + 255) / 256;
     const unsigned g = (unsigned)(nb < 152 * 16 ? nb : 152 * 16);
-    k_interp_classify<<<g, 256, 0, s>>>(a);
+    k_interp_classify<<<(unsigned)nb, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_interp_list<<<g, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -145,6 +145,29 @@ def test_cr_full_size_aniso9_1024():
     assert np.array_equal(Cg, Cw)
 
 
+def test_interp_full_size_aniso9_1024_bf16():
+    """LS interpolation (caliber 2, unit weights) at the full 1024 x 1024 size
+    on BF16-stored vectors (the oracle's relaxed vectors rounded on the CPU)
+    and the oracle's CR coarse set: P equals the oracle's bit for bit."""
+    N, K, seed, nu, theta = 1024, 16, 1, 8, 0.5
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
+    color = inputs.red_black(N)
+    want = oracle.build(rp, col, val, K, seed, nu, 1.0, theta, oracle.SWEEP_MCGS, color)
+    C, _ = oracle.cr_coarsen(rp, col, val, rp, col, want["ls"], theta=theta, nu=5, omega=1.0,
+                             sweep=oracle.SWEEP_MCGS, color=color, delta=0.6, tol=0.5,
+                             max_sets=12, seed=5)
+    X = torch.from_numpy(want["X"]).to(torch.bfloat16).to(torch.float64).numpy()
+    Y = oracle.target(rp, col, val, X)
+    Pw = oracle.ls_interp(X, Y, rp, col, C, 2, 1.5)
+    with amgd.Handle(rp, col, val, K, seed) as h:
+        h.set_precision("bf16")
+        h.set_coloring(color)
+        h.set_vectors(X)
+        Pg = h.ls_interpolation(C, 2, 1.5)
+    for g, w_ in zip(Pg, Pw):
+        assert np.array_equal(g, w_)
+
+
 def test_cr_then_interpolation():
     """Algorithm 1's coarse set feeds the LS interpolation of §4.3: both GPU
     steps in a row equal both oracle steps in a row."""
