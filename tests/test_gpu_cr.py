@@ -80,6 +80,20 @@ def test_cr_matches_oracle(name, c0):
     assert (Cg >= C0).all()
 
 
+def test_cr_jacobi_on_colored_handle():
+    """A handle with a coloring keeps its matrix in color order; Jacobi
+    F-relaxation over that order gives the same coarse set as the oracle."""
+    rp, col, val, color, sweep, omega, d, want = _setup("aniso9_48_mcgs")
+    args = dict(theta=0.5, nu=4, omega=0.7, delta=0.6, tol=0.5, max_sets=12, seed=9)
+    Cw, rw = oracle.cr_coarsen(rp, col, val, rp, col, want["ls"], sweep=oracle.SWEEP_JACOBI,
+                               **args)
+    with amgd.Handle(rp, col, val, 8, 3) as h:
+        h.set_coloring(color)
+        Cg, rg = h.cr_coarsen(None, ls=want["ls"], sweep=amgd.AMGD_SWEEP_JACOBI, **args)
+    assert len(rw) >= 2
+    assert np.array_equal(rg, rw) and np.array_equal(Cg, Cw)
+
+
 def _band_free(prp, pcol, ls, theta, band=1e-9):
     """No two off-diagonal LS values of a row have a ratio within band of theta."""
     n = len(prp) - 1
