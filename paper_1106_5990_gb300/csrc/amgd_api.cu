@@ -100,6 +100,7 @@ struct amgd_ctx {
     double *cr_u[2] = {nullptr, nullptr};
     uint8_t *cr_coarse = nullptr, *cr_state = nullptr, *cr_ismax = nullptr, *cr_strong = nullptr;
     uint8_t *cr_coarse_p = nullptr;              // coarse mask in the sweeps' row order
+    double *cr_cdiag = nullptr;                  // omega / a_rr in the sweeps' row order
     size_t cr_strong_len = 0;
     int32_t *cr_lam = nullptr;
     uint64_t *cr_key = nullptr;
@@ -1473,11 +1474,13 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
     CK(h, cudaMemcpyAsync(h->cr_coarse, coarse, (size_t)n,
                           coarse_mem == AMGD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     if (!h->cr_coarse_p) CK(h, dalloc(&h->cr_coarse_p, (size_t)n));
+    if (!h->cr_cdiag) CK(h, dalloc(&h->cr_cdiag, (size_t)n));
     CrArgs a;
     a.rp = h->rp_p;
     a.col = h->col_p;
     a.val = h->val64;
     a.diag = h->diag64;
+    a.cdiag = h->cr_cdiag;
     a.perm = h->perm;
     a.coarse_p = h->cr_coarse_p;
     a.prp = h->prp;
@@ -1499,6 +1502,8 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
     const int64_t sweep_launches = sweep == AMGD_SWEEP_MCGS ? ncolors : 1;
     h->cr_rounds = 0;
     h->cr_launches = ls ? 0 : 1;                  // the LS export
+    CK(h, launch_cr_cdiag(a, s));
+    ++h->cr_launches;
     for (;;) {
         // nu F-relaxation sweeps from the constant start (Eq. (3.4))
         CK(h, launch_cr_start(a, h->cr_u[0], s));
@@ -1868,7 +1873,7 @@ int amgd_destroy(amgd_handle h)
                     h->s_col_tmp, h->tmp64, h->ckpt, h->seg, h->adj_vec, h->adj_slot, h->lsb,
                     h->adj_part, h->at_rp, h->at_row, h->at_slot, h->edge_tiles, h->mirror,
                     h->ip_coarse, h->ip_sel_col, h->ip_cnt, h->ip_sel_val, h->ip_ls, h->ip_rp,
-                    h->ip_out, h->ip_pos, h->ip_list, h->ip_bcnt, h->ip_bkt, h->cr_u[0], h->cr_u[1], h->cr_coarse, h->cr_coarse_p, h->cr_state,
+                    h->ip_out, h->ip_pos, h->ip_list, h->ip_bcnt, h->ip_bkt, h->cr_u[0], h->cr_u[1], h->cr_coarse, h->cr_coarse_p, h->cr_cdiag, h->cr_state,
                     h->cr_ismax, h->cr_strong, h->cr_lam, h->cr_key, h->cr_scal};
     for (void *p : ptrs) dfree(p);
     delete h;

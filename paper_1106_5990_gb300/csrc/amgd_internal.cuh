@@ -337,6 +337,7 @@ struct CrArgs {
     const int32_t *rp, *col;        // A with rows in color order (the sweeps' layout)
     const double *val;              // its values (FP64)
     const double *diag;             // its diagonal
+    double *cdiag;                  // omega / diagonal (color order), formed once per call
     const int32_t *perm;            // caller row of each color-ordered row (NULL: identity)
     uint8_t *coarse_p;              // coarse mask in color order
     const int32_t *prp, *pcol;      // pattern of the strength graph (G_d), caller order
@@ -353,6 +354,8 @@ struct CrArgs {
 };
 // coarse_p from coarse, u = 1 on F and 0 on C (color order)
 cudaError_t launch_cr_start(const CrArgs &a, double *u, cudaStream_t s);
+// cdiag = omega / diag, the weight of every sweep of the call
+cudaError_t launch_cr_cdiag(const CrArgs &a, cudaStream_t s);
 // one F-relaxation sweep u -> un over color-ordered rows: Jacobi (one range
 // [0, n)) or multicolor Gauss-Seidel (one launch per color range)
 cudaError_t launch_cr_sweep(const CrArgs &a, bool mcgs, const int64_t *color_start,

@@ -45,15 +45,26 @@ __global__ void k_cr_start(const int32_t *__restrict__ perm, const uint8_t *__re
 // Jacobi (r0 = 0, r1 = n, every neighbour from u), or one color of a
 // multicolor Gauss-Seidel sweep (neighbours of earlier colors -- rows below
 // r0 -- from un, all others from u).  Coarse rows stay 0 (Eq. (3.4)).
+//
+// The row weight omega / a_rr is the same correctly rounded quotient in every
+// sweep, so it is formed once per call (k_cr_cdiag) rather than per sweep: on
+// this part a double division costs about as much as the row's sum.
+__global__ void k_cr_cdiag(const double *__restrict__ diag, double omega,
+                           double *__restrict__ cdiag, int32_t n)
+{
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        cdiag[r] = omega / diag[r];
+}
+
 __global__ void k_cr_sweep(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                           const double *__restrict__ val, const double *__restrict__ diag,
+                           const double *__restrict__ val, const double *__restrict__ cdiag,
                            const uint8_t *__restrict__ coarse_p, int32_t r0, int32_t r1,
-                           double omega, const double *__restrict__ u, double *un)
+                           const double *__restrict__ u, double *un)
 {
     for (int32_t r = r0 + blockIdx.x * blockDim.x + threadIdx.x; r < r1;
          r += gridDim.x * blockDim.x) {
         if (coarse_p[r]) { un[r] = 0.0; continue; }
-        const double c = omega / diag[r];
+        const double c = cdiag[r];
         double acc = 0.0;
         const int32_t e = rp[r + 1];
         for (int32_t p = rp[r]; p < e; ++p) {
@@ -237,19 +248,25 @@ cudaError_t launch_cr_start(const CrArgs &a, double *u, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_cr_cdiag(const CrArgs &a, cudaStream_t s)
+{
+    k_cr_cdiag<<<grid_for(a.n), kThreads, 0, s>>>(a.diag, a.omega, a.cdiag, a.n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cr_sweep(const CrArgs &a, bool mcgs, const int64_t *color_start,
                             int32_t ncolors, const double *u, double *un, cudaStream_t s)
 {
     if (!mcgs) {
-        k_cr_sweep<<<grid_for(a.n), kThreads, 0, s>>>(a.rp, a.col, a.val, a.diag, a.coarse_p, 0,
-                                                      a.n, a.omega, u, un);
+        k_cr_sweep<<<grid_for(a.n), kThreads, 0, s>>>(a.rp, a.col, a.val, a.cdiag, a.coarse_p, 0,
+                                                      a.n, u, un);
         return cudaGetLastError();
     }
     for (int32_t cc = 0; cc < ncolors; ++cc) {
         const int32_t r0 = (int32_t)color_start[cc], r1 = (int32_t)color_start[cc + 1];
         if (r1 <= r0) continue;
-        k_cr_sweep<<<grid_for(r1 - r0), kThreads, 0, s>>>(a.rp, a.col, a.val, a.diag, a.coarse_p,
-                                                         r0, r1, a.omega, u, un);
+        k_cr_sweep<<<grid_for(r1 - r0), kThreads, 0, s>>>(a.rp, a.col, a.val, a.cdiag, a.coarse_p,
+                                                         r0, r1, u, un);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

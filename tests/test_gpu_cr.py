@@ -151,9 +151,10 @@ def test_cr_full_size_aniso9_1024():
                                                         t_or, 1e3 * t_gpu, rounds, launches))
     stages = len(rw)
     assert rounds >= 4 * (stages - 1)
-    # per stage: start, 5 sweeps x 2 colors, norm; per added set: candidates,
-    # strength, keys, add, 3 kernels per round and one count per batch of rounds
-    lower = stages * 12 + (stages - 1) * 4 + 3 * rounds
+    # the sweep weights once; per stage: start, 5 sweeps x 2 colors, norm; per
+    # added set: candidates, strength, keys, add, 3 kernels per round and one
+    # count per batch of rounds
+    lower = 1 + stages * 12 + (stages - 1) * 4 + 3 * rounds
     assert lower < launches <= lower + rounds // 4
     assert np.array_equal(rg, rw)
     assert np.array_equal(Cg, Cw)
