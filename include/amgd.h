@@ -167,6 +167,35 @@ int amgd_get_vectors(amgd_handle h, double *X, int mem);
 int amgd_set_values(amgd_handle h, const double *val, int mem);
 
 /*
+ * Stream-ordered value updates and results, for a stream of matrices that
+ * share one pattern (each replayed through a captured build).  No call below
+ * synchronises; copies run on two copy streams of the handle, double-buffered,
+ * so that the upload of the next values and the download of the last strength
+ * graph overlap the build between them.
+ * amgd_set_values_async -- like amgd_set_values: val[nnz] (host: page-locked
+ *   memory for the copy to be asynchronous; or device) is copied into one of
+ *   two staging buffers, checked on the device (finite, nonzero diagonal) and
+ *   applied in the handle's stream order.  val must stay valid and unchanged
+ *   until amgd_sync returns.  Values that fail the check are applied all the
+ *   same (results computed from them are meaningless) and the next amgd_sync
+ *   returns the error.
+ * amgd_strength_async -- the current strength graph M^d (§4.2) as CSR, like
+ *   amgd_strength: s_row_ptr[n+1] and the first min(cap, E) columns of s_col
+ *   (E the stored off-diagonals of the pattern), in host or device memory
+ *   (mem); valid after amgd_sync.  The next amgd_sync returns CAPACITY if the
+ *   graph has more than cap columns.
+ * amgd_sync -- waits for every asynchronous copy and kernel of the handle and
+ *   reports the deferred errors.  Until it returns, calls that change the
+ *   layout or the captured graph (precision, coloring, search depth, autotune,
+ *   graph capture) return STATE.
+ *   Errors: ARG, STATE (no distances yet, for amgd_strength_async), CSR,
+ *   ZERO_DIAG, CAPACITY (at amgd_sync), CUDA.
+ */
+int amgd_set_values_async(amgd_handle h, const double *val, int mem);
+int amgd_strength_async(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap, int mem);
+int amgd_sync(amgd_handle h);
+
+/*
  * amgd_relax -- nu sweeps on A x = 0 applied to all K vectors (§3):
  *   AMGD_SWEEP_JACOBI: x_i <- x_i - (omega / a_ii) sum_j a_ij x_j
  *   AMGD_SWEEP_MCGS:   as set by amgd_set_coloring, SOR weight omega

@@ -80,6 +80,9 @@ SIGNATURES = {
     "amgd_ls_interpolation": (_int, [_P, _P, _int, _i32, _f64, _P, _P, _P, _i64, _P, _P, _int]),
     "amgd_distance_pattern": (_int, [_P, _P, _P, _i64, _P, _int]),
     "amgd_cr_stats": (_int, [_P, _P, _P]),
+    "amgd_set_values_async": (_int, [_P, _P, _int]),
+    "amgd_strength_async": (_int, [_P, _P, _P, _i64, _int]),
+    "amgd_sync": (_int, [_P]),
     "amgd_cr_coarsen": (_int, [_P, _P, _int, _P, _int, _int, _f64, _i32, _f64, _f64, _f64, _i32,
                                _u64, _P, _P]),
     "amgd_backward": (_int, [_P, _P, _int, _P, _P, _P]),
@@ -354,6 +357,27 @@ class Handle:
                                        omega, nu, theta, delta, tol, max_sets, seed,
                                        rho.ctypes.data, ctypes.byref(m)))
         return c, rho[:m.value]
+
+    def set_values_async(self, val):
+        """Stream-ordered value update (numpy array, pinned torch tensor or
+        device tensor); val must stay unchanged until sync()."""
+        v = val if _is_torch(val) else _host(val, np.float64)
+        p, mem = ptr_mem(v)
+        self._ck(lib().amgd_set_values_async(self.h, p, mem))
+        return v
+
+    def strength_async(self, s_rp, s_col):
+        """Stream-ordered strength CSR into s_rp (n+1 int64) and s_col (int32,
+        its length is the capacity); valid after sync()."""
+        p_rp, mem = ptr_mem(s_rp)
+        p_col, mem2 = ptr_mem(s_col)
+        assert mem == mem2, "outputs must live in the same memory"
+        cap = s_col.numel() if _is_torch(s_col) else s_col.size
+        self._ck(lib().amgd_strength_async(self.h, p_rp, p_col, cap, mem))
+
+    def sync(self):
+        """Wait for the asynchronous work of the handle; raises deferred errors."""
+        self._ck(lib().amgd_sync(self.h))
 
     def cr_stats(self):
         """(selection rounds, kernel launches) of the last cr_coarsen."""

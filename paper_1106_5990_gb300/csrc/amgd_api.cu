@@ -107,6 +107,19 @@ struct amgd_ctx {
     unsigned long long *cr_scal = nullptr;
     int32_t cr_rounds = 0;                       // selection rounds of the last amgd_cr_coarsen
     int64_t cr_launches = 0;                     // kernels it launched
+    // asynchronous value updates and results (stream-ordered, double-buffered)
+    cudaStream_t up_stream = nullptr, down_stream = nullptr;
+    cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+    cudaEvent_t ev_res[2] = {nullptr, nullptr}, ev_down[2] = {nullptr, nullptr};
+    double *stage[2] = {nullptr, nullptr};
+    int64_t *res_rp[2] = {nullptr, nullptr};
+    int32_t *res_col[2] = {nullptr, nullptr};
+    int64_t res_col_len = 0;
+    uint32_t *async_err = nullptr;               // value-check bits of asynchronous updates
+    int up_slot = 0, res_slot = 0;
+    bool async_pending = false;
+    struct PendingOut { int64_t *rp; int mem; int64_t cap; };
+    std::vector<PendingOut> pending_out;         // strength outputs checked at amgd_sync
     int32_t *edge_tiles = nullptr;               // row tiles of the edge pass (over the pattern)
     int32_t n_edge_tiles = 0;
     // pattern of the fits, threshold and strength graph: the graph G_d of A^d
@@ -678,6 +691,7 @@ int amgd_set_stream(amgd_handle h, void *stream)
 int amgd_set_precision(amgd_handle h, int storage)
 {
     if (!h) return AMGD_ERR_ARG;
+    if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (storage != AMGD_FP64 && storage != AMGD_FP32 && storage != AMGD_BF16)
         return fail(h, AMGD_ERR_ARG, "unknown storage precision");
     if (storage == h->storage) return AMGD_OK;
@@ -756,6 +770,7 @@ int amgd_set_weights(amgd_handle h, const double *w)
 int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int mem)
 {
     if (!h) return AMGD_ERR_ARG;
+    if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (ncolors < 1 || (!color && h->n > 0)) return fail(h, AMGD_ERR_ARG, "bad coloring arguments");
     const int64_t n = h->n;
     std::vector<int32_t> c((size_t)n);
@@ -895,6 +910,126 @@ int amgd_set_values(amgd_handle h, const double *val, int mem)
     return AMGD_OK;
 }
 
+namespace {
+
+int async_setup(amgd_ctx *h)
+{
+    if (h->up_stream) return AMGD_OK;
+    CK(h, cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking));
+    CK(h, cudaStreamCreateWithFlags(&h->down_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        CK(h, cudaEventCreateWithFlags(&h->ev_up[k], cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->ev_used[k], cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->ev_res[k], cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->ev_down[k], cudaEventDisableTiming));
+    }
+    CK(h, dalloc(&h->async_err, 1));
+    CK(h, cudaMemset(h->async_err, 0, sizeof(uint32_t)));
+    return AMGD_OK;
+}
+
+}  // namespace
+
+int amgd_set_values_async(amgd_handle h, const double *val, int mem)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (!val && h->nnz) return fail(h, AMGD_ERR_ARG, "val is NULL");
+    if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
+    int rc = async_setup(h);
+    if (rc != AMGD_OK) return rc;
+    if (!h->stage[0]) {
+        CK(h, dalloc(&h->stage[0], (size_t)h->nnz + 4));
+        CK(h, dalloc(&h->stage[1], (size_t)h->nnz + 4));
+    }
+    const int k = h->up_slot;
+    h->up_slot ^= 1;
+    // the slot's previous contents must have been applied before it is refilled
+    CK(h, cudaStreamWaitEvent(h->up_stream, h->ev_used[k], 0));
+    CK(h, cudaMemcpyAsync(h->stage[k], val, h->nnz * sizeof(double),
+                          mem == AMGD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          h->up_stream));
+    CK(h, cudaEventRecord(h->ev_up[k], h->up_stream));
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_up[k], 0));
+    CK(h, launch_check_values(h->stage[k], h->nnz, h->diag_slot, (int32_t)h->n, h->async_err, h->stream));
+    rc = permute_values(h, h->stage[k]);
+    if (rc != AMGD_OK) return rc;
+    CK(h, cudaEventRecord(h->ev_used[k], h->stream));
+    h->async_pending = true;
+    h->have_dist = false;
+    h->traj_valid = false;
+    return AMGD_OK;
+}
+
+int amgd_strength_async(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap, int mem)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (!h->have_dist) return fail(h, AMGD_ERR_STATE, "amgd_distances or a captured build must run first");
+    if (!s_row_ptr || (!s_col && cap > 0) || cap < 0) return fail(h, AMGD_ERR_ARG, "bad output buffers");
+    if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
+    int rc = async_setup(h);
+    if (rc != AMGD_OK) return rc;
+    if (!h->res_rp[0] || h->res_col_len < h->E_p) {
+        CK(h, cudaStreamSynchronize(h->down_stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (int k = 0; k < 2; ++k) {
+            dfree(h->res_col[k]);
+            h->res_col[k] = nullptr;
+            if (!h->res_rp[k]) CK(h, dalloc(&h->res_rp[k], (size_t)h->n + 1));
+        }
+        h->res_col_len = 0;
+        for (int k = 0; k < 2; ++k) CK(h, dalloc(&h->res_col[k], (size_t)(h->E_p > 0 ? h->E_p : 1)));
+        h->res_col_len = h->E_p;
+    }
+    const int k = h->res_slot;
+    h->res_slot ^= 1;
+    // the slot's previous copy to the caller must be done before it is rewritten
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_down[k], 0));
+    CK(h, launch_strength(h->count, h->prp, h->pcol, h->flag, (int32_t)h->n, h->tile, h->res_rp[k],
+                          h->res_col[k], h->stream));
+    CK(h, cudaEventRecord(h->ev_res[k], h->stream));
+    CK(h, cudaStreamWaitEvent(h->down_stream, h->ev_res[k], 0));
+    const cudaMemcpyKind kind = mem == AMGD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(h, cudaMemcpyAsync(s_row_ptr, h->res_rp[k], ((size_t)h->n + 1) * sizeof(int64_t), kind, h->down_stream));
+    const int64_t ncol = cap < h->E_p ? cap : h->E_p;
+    if (ncol > 0)
+        CK(h, cudaMemcpyAsync(s_col, h->res_col[k], (size_t)ncol * sizeof(int32_t), kind, h->down_stream));
+    CK(h, cudaEventRecord(h->ev_down[k], h->down_stream));
+    h->pending_out.push_back({s_row_ptr, mem, cap});
+    h->async_pending = true;
+    return AMGD_OK;
+}
+
+int amgd_sync(amgd_handle h)
+{
+    if (!h) return AMGD_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->up_stream) {
+        CK(h, cudaStreamSynchronize(h->up_stream));
+        CK(h, cudaStreamSynchronize(h->down_stream));
+    }
+    h->async_pending = false;
+    std::vector<amgd_ctx::PendingOut> outs;
+    outs.swap(h->pending_out);
+    if (h->async_err) {
+        uint32_t err = 0;
+        CK(h, cudaMemcpy(&err, h->async_err, sizeof err, cudaMemcpyDeviceToHost));
+        if (err) {
+            CK(h, cudaMemset(h->async_err, 0, sizeof err));
+            h->have_dist = false;
+            if (err & 1u) return fail(h, AMGD_ERR_CSR, "an asynchronous value update had a non-finite value");
+            return fail(h, AMGD_ERR_ZERO_DIAG, "an asynchronous value update had a zero diagonal");
+        }
+    }
+    for (const auto &o : outs) {
+        int64_t total = 0;
+        if (o.mem == AMGD_MEM_HOST) total = o.rp[h->n];
+        else CK(h, cudaMemcpy(&total, o.rp + h->n, sizeof total, cudaMemcpyDeviceToHost));
+        if (total > o.cap)
+            return fail(h, AMGD_ERR_CAPACITY, "strength output needs " + std::to_string(total) + " columns");
+    }
+    return poll_status(h);
+}
+
 int amgd_relax(amgd_handle h, int32_t nu, double omega, int sweep_type)
 {
     if (!h) return AMGD_ERR_ARG;
@@ -973,6 +1108,7 @@ int amgd_graph_capture(amgd_handle h, uint64_t seed, int32_t nu, double omega, i
                        double theta, int64_t *s_row_ptr, int32_t *s_col, int64_t cap)
 {
     if (!h) return AMGD_ERR_ARG;
+    if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (nu < 0 || !std::isfinite(omega)) return fail(h, AMGD_ERR_ARG, "nu < 0 or omega not finite");
     if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(h, AMGD_ERR_ARG, "theta must be finite and >= 0");
     if (sweep_type != AMGD_SWEEP_JACOBI && sweep_type != AMGD_SWEEP_MCGS)
@@ -1109,6 +1245,7 @@ extern "C" {
 int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache_path)
 {
     if (!h) return AMGD_ERR_ARG;
+    if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (sweep_type != AMGD_SWEEP_JACOBI && sweep_type != AMGD_SWEEP_MCGS)
         return fail(h, AMGD_ERR_ARG, "unknown sweep type");
     if (sweep_type == AMGD_SWEEP_MCGS && !h->perm)
@@ -1265,6 +1402,7 @@ bool depth_pattern(const std::vector<int32_t> &rp, const std::vector<int32_t> &c
 int amgd_set_search_depth(amgd_handle h, int32_t d)
 {
     if (!h) return AMGD_ERR_ARG;
+    if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (d < 1 || d > 16) return fail(h, AMGD_ERR_ARG, "search depth must be in 1..16");
     if (d == h->depth) return AMGD_OK;
     std::vector<int32_t> prp, pcol;
@@ -1787,6 +1925,7 @@ int amgd_graph_capture_backward(amgd_handle h, uint64_t seed, int32_t nu, double
                                 double theta, double *val_bar)
 {
     if (!h) return AMGD_ERR_ARG;
+    if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (nu < 0 || !std::isfinite(omega)) return fail(h, AMGD_ERR_ARG, "nu < 0 or omega not finite");
     if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(h, AMGD_ERR_ARG, "theta must be finite and >= 0");
     if (!val_bar && h->nnz) return fail(h, AMGD_ERR_ARG, "val_bar is NULL");
@@ -1849,6 +1988,18 @@ int amgd_destroy(amgd_handle h)
 {
     if (!h) return AMGD_OK;
     if (h->stream || h->x[0]) cudaStreamSynchronize(h->stream);
+    if (h->up_stream) {
+        cudaStreamSynchronize(h->up_stream);
+        cudaStreamSynchronize(h->down_stream);
+        cudaStreamDestroy(h->up_stream);
+        cudaStreamDestroy(h->down_stream);
+        for (int k = 0; k < 2; ++k) {
+            cudaEventDestroy(h->ev_up[k]);
+            cudaEventDestroy(h->ev_used[k]);
+            cudaEventDestroy(h->ev_res[k]);
+            cudaEventDestroy(h->ev_down[k]);
+        }
+    }
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1873,7 +2024,8 @@ int amgd_destroy(amgd_handle h)
                     h->s_col_tmp, h->tmp64, h->ckpt, h->seg, h->adj_vec, h->adj_slot, h->lsb,
                     h->adj_part, h->at_rp, h->at_row, h->at_slot, h->edge_tiles, h->mirror,
                     h->ip_coarse, h->ip_sel_col, h->ip_cnt, h->ip_sel_val, h->ip_ls, h->ip_rp,
-                    h->ip_out, h->ip_pos, h->ip_list, h->ip_bcnt, h->ip_bkt, h->cr_u[0], h->cr_u[1], h->cr_coarse, h->cr_coarse_p, h->cr_cdiag, h->cr_state,
+                    h->ip_out, h->ip_pos, h->ip_list, h->ip_bcnt, h->ip_bkt, h->cr_u[0], h->cr_u[1], h->cr_coarse, h->cr_coarse_p, h->cr_cdiag, h->stage[0], h->stage[1], h->res_rp[0],
+                    h->res_rp[1], h->res_col[0], h->res_col[1], h->async_err, h->cr_state,
                     h->cr_ismax, h->cr_strong, h->cr_lam, h->cr_key, h->cr_scal};
     for (void *p : ptrs) dfree(p);
     delete h;
