@@ -242,6 +242,18 @@ def test_empty_matrix():
         h.relax(2, 0.7)
         h.distances(0.5)
         s_rp, s_col = h.strength()
+        # coarsening, interpolation and the stream-ordered calls on no rows
+        C, rho = h.cr_coarsen(np.zeros(0, np.uint8), ls=np.zeros(0))
+        assert len(C) == 0 and list(rho) == [0.0]
+        P = h.ls_interpolation(np.zeros(0, np.uint8), 2)
+        assert list(P[0]) == [0] and len(P[1]) == 0
+        h.set_values_async(val)
+        o_rp = np.full(1, -1, np.int64)
+        h.sync()
+        h.distances(0.5)
+        h.strength_async(o_rp, np.zeros(0, np.int32))
+        h.sync()
+        assert list(o_rp) == [0]
     assert list(s_rp) == [0] and len(s_col) == 0
 
 
