@@ -16,6 +16,8 @@
 
 #include "amgd_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace amgd;
 
 struct amgd_ctx {
@@ -174,6 +176,16 @@ Shape default_shape(int st, int K)
 }
 
 
+
+// NVTX range over one C-ABI call (header-only NVTX v3: free when no tool is
+// attached, named ranges in ncu / Nsight timelines when one is)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define AMGD_RANGE(name) NvtxRange amgd_nvtx_range_(name)
 
 int fail(amgd_ctx *h, int code, const std::string &msg)
 {
@@ -690,6 +702,7 @@ int amgd_set_stream(amgd_handle h, void *stream)
 
 int amgd_set_precision(amgd_handle h, int storage)
 {
+    AMGD_RANGE("amgd_set_precision");
     if (!h) return AMGD_ERR_ARG;
     if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (storage != AMGD_FP64 && storage != AMGD_FP32 && storage != AMGD_BF16)
@@ -769,6 +782,7 @@ int amgd_set_weights(amgd_handle h, const double *w)
 
 int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int mem)
 {
+    AMGD_RANGE("amgd_set_coloring");
     if (!h) return AMGD_ERR_ARG;
     if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (ncolors < 1 || (!color && h->n > 0)) return fail(h, AMGD_ERR_ARG, "bad coloring arguments");
@@ -841,6 +855,7 @@ int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int 
 
 int amgd_init_vectors(amgd_handle h, uint64_t seed)
 {
+    AMGD_RANGE("amgd_init_vectors");
     if (!h) return AMGD_ERR_ARG;
     return run_init(h, seed, h->stream);
 }
@@ -887,6 +902,7 @@ int amgd_get_vectors(amgd_handle h, double *X, int mem)
 
 int amgd_set_values(amgd_handle h, const double *val, int mem)
 {
+    AMGD_RANGE("amgd_set_values");
     if (!h) return AMGD_ERR_ARG;
     if (!val && h->nnz) return fail(h, AMGD_ERR_ARG, "val is NULL");
     if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
@@ -932,6 +948,7 @@ int async_setup(amgd_ctx *h)
 
 int amgd_set_values_async(amgd_handle h, const double *val, int mem)
 {
+    AMGD_RANGE("amgd_set_values_async");
     if (!h) return AMGD_ERR_ARG;
     if (!val && h->nnz) return fail(h, AMGD_ERR_ARG, "val is NULL");
     if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
@@ -962,6 +979,7 @@ int amgd_set_values_async(amgd_handle h, const double *val, int mem)
 
 int amgd_strength_async(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap, int mem)
 {
+    AMGD_RANGE("amgd_strength_async");
     if (!h) return AMGD_ERR_ARG;
     if (!h->have_dist) return fail(h, AMGD_ERR_STATE, "amgd_distances or a captured build must run first");
     if (!s_row_ptr || (!s_col && cap > 0) || cap < 0) return fail(h, AMGD_ERR_ARG, "bad output buffers");
@@ -1001,6 +1019,7 @@ int amgd_strength_async(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64
 
 int amgd_sync(amgd_handle h)
 {
+    AMGD_RANGE("amgd_sync");
     if (!h) return AMGD_ERR_ARG;
     CK(h, cudaStreamSynchronize(h->stream));
     if (h->up_stream) {
@@ -1032,6 +1051,7 @@ int amgd_sync(amgd_handle h)
 
 int amgd_relax(amgd_handle h, int32_t nu, double omega, int sweep_type)
 {
+    AMGD_RANGE("amgd_relax");
     if (!h) return AMGD_ERR_ARG;
     if (nu < 0 || !std::isfinite(omega)) return fail(h, AMGD_ERR_ARG, "nu < 0 or omega not finite");
     if (sweep_type != AMGD_SWEEP_JACOBI && sweep_type != AMGD_SWEEP_MCGS)
@@ -1045,6 +1065,7 @@ int amgd_relax(amgd_handle h, int32_t nu, double omega, int sweep_type)
 
 int amgd_distances(amgd_handle h, double theta, double *a, double *dist, double *ls, int mem)
 {
+    AMGD_RANGE("amgd_distances");
     if (!h) return AMGD_ERR_ARG;
     if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(h, AMGD_ERR_ARG, "theta must be finite and >= 0");
     if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
@@ -1071,6 +1092,7 @@ int amgd_distances(amgd_handle h, double theta, double *a, double *dist, double 
 int amgd_strength(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap,
                   int64_t *nnz_s, int mem)
 {
+    AMGD_RANGE("amgd_strength");
     if (!h) return AMGD_ERR_ARG;
     if (!h->have_dist) return fail(h, AMGD_ERR_STATE, "amgd_distances must run first");
     if (!s_row_ptr || (!s_col && cap > 0) || cap < 0) return fail(h, AMGD_ERR_ARG, "bad output buffers");
@@ -1107,6 +1129,7 @@ int amgd_strength(amgd_handle h, int64_t *s_row_ptr, int32_t *s_col, int64_t cap
 int amgd_graph_capture(amgd_handle h, uint64_t seed, int32_t nu, double omega, int sweep_type,
                        double theta, int64_t *s_row_ptr, int32_t *s_col, int64_t cap)
 {
+    AMGD_RANGE("amgd_graph_capture");
     if (!h) return AMGD_ERR_ARG;
     if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (nu < 0 || !std::isfinite(omega)) return fail(h, AMGD_ERR_ARG, "nu < 0 or omega not finite");
@@ -1244,6 +1267,7 @@ extern "C" {
 
 int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache_path)
 {
+    AMGD_RANGE("amgd_autotune");
     if (!h) return AMGD_ERR_ARG;
     if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (sweep_type != AMGD_SWEEP_JACOBI && sweep_type != AMGD_SWEEP_MCGS)
@@ -1347,6 +1371,7 @@ int amgd_phase_times(amgd_handle h, float *ms)
 
 int amgd_graph_launch(amgd_handle h)
 {
+    AMGD_RANGE("amgd_graph_launch");
     if (!h) return AMGD_ERR_ARG;
     if (!h->gexec) return fail(h, AMGD_ERR_STATE, "no captured graph");
     CK(h, cudaGraphLaunch(h->gexec, h->stream));
@@ -1401,6 +1426,7 @@ bool depth_pattern(const std::vector<int32_t> &rp, const std::vector<int32_t> &c
 
 int amgd_set_search_depth(amgd_handle h, int32_t d)
 {
+    AMGD_RANGE("amgd_set_search_depth");
     if (!h) return AMGD_ERR_ARG;
     if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (d < 1 || d > 16) return fail(h, AMGD_ERR_ARG, "search depth must be in 1..16");
@@ -1468,6 +1494,7 @@ int amgd_ls_interpolation(amgd_handle h, const uint8_t *coarse, int coarse_mem, 
                           double gamma, int64_t *p_row_ptr, int32_t *p_col, double *p_val,
                           int64_t cap, int64_t *nnz_p, double *ls, int mem)
 {
+    AMGD_RANGE("amgd_ls_interpolation");
     if (!h) return AMGD_ERR_ARG;
     if (caliber < 1 || caliber > kInterpMaxCaliber) return fail(h, AMGD_ERR_ARG, "caliber must be in 1..4");
     if (!(gamma >= 0.0) || !std::isfinite(gamma)) return fail(h, AMGD_ERR_ARG, "gamma must be finite and >= 0");
@@ -1565,6 +1592,7 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
                     int sweep, double omega, int32_t nu, double theta, double delta, double tol,
                     int32_t max_sets, uint64_t seed, double *rho, int32_t *n_rho)
 {
+    AMGD_RANGE("amgd_cr_coarsen");
     if (!h) return AMGD_ERR_ARG;
     if (n_rho) *n_rho = 0;
     if (h->nmat != 1) return fail(h, AMGD_ERR_UNSUPPORTED, "coarsening needs a single-matrix handle");
@@ -1882,6 +1910,7 @@ int backward_checks(amgd_ctx *h)
 int amgd_backward(amgd_handle h, const double *ls_bar, int mem, double *val_bar,
                   double *omega_bar, double *loss)
 {
+    AMGD_RANGE("amgd_backward");
     if (!h) return AMGD_ERR_ARG;
     if (mem != AMGD_MEM_HOST && mem != AMGD_MEM_DEVICE) return fail(h, AMGD_ERR_ARG, "bad mem");
     if (!val_bar && h->nnz) return fail(h, AMGD_ERR_ARG, "val_bar is NULL");
@@ -1924,6 +1953,7 @@ int amgd_backward_scalars(amgd_handle h, double *omega_bar, double *loss)
 int amgd_graph_capture_backward(amgd_handle h, uint64_t seed, int32_t nu, double omega,
                                 double theta, double *val_bar)
 {
+    AMGD_RANGE("amgd_graph_capture_backward");
     if (!h) return AMGD_ERR_ARG;
     if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
     if (nu < 0 || !std::isfinite(omega)) return fail(h, AMGD_ERR_ARG, "nu < 0 or omega not finite");
