@@ -37,6 +37,7 @@ CASES = {
     "random_800_d2": (lambda: inputs.random_csr(800, 4.0, 5, symmetric_pattern=True), None, 0.7, 2),
     "graph_3000": (lambda: inputs.graph_laplacian(3000, 8.0, 4), None, 2.0 / 3.0, 1),
     "jump3d_12": (lambda: inputs.jump3d_7pt(12, 2.0, 2), None, 0.8, 1),
+    "aniso5_40_d3": (lambda: inputs.aniso2d_5pt(40, 1e-2), None, 2.0 / 3.0, 3),
 }
 
 

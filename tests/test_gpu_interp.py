@@ -135,6 +135,25 @@ def test_interp_ties_and_exact_fits(unit_w):
         assert np.array_equal(g, w_)
 
 
+@pytest.mark.parametrize("K", [1, 3, 64])
+def test_interp_extreme_K(K):
+    """K = 1 (every one-point fit exact, so the penalty decides), an odd K and
+    the largest K, on the thread and the warp kernels (search depth 2)."""
+    rp, col, val = inputs.random_csr(700, 2.5, 17, symmetric_pattern=True)
+    n = len(rp) - 1
+    coarse = (np.random.default_rng(8).random(n) < 0.4).astype(np.uint8)
+    X = oracle.relax(rp, col, val, oracle.tv_init(n, K, 5), 2, 0.7)
+    prp, pcol = oracle.distance_graph(rp, col, 2)
+    with amgd.Handle(rp, col, val, K, 5) as h:
+        h.set_search_depth(2)
+        h.set_vectors(X)
+        got = h.ls_interpolation(coarse, 3, 1.5)
+    Y = oracle.target(rp, col, val, X)
+    want = oracle.ls_interp(X, Y, prp, pcol, coarse, 3, 1.5)
+    for g, w_ in zip(got, want):
+        assert np.array_equal(g, w_)
+
+
 def test_interp_too_many_candidates():
     rp, col, val = inputs.graph_laplacian(300, 12.0, 2)
     with amgd.Handle(rp, col, val, 8, 1) as h:
