@@ -451,6 +451,54 @@ class Handle:
         return list(ms)
 
 
+def build(A, K, seed=0, nu=4, omega=2.0 / 3.0, sweep=AMGD_SWEEP_JACOBI, theta=0.5,
+          precision="fp64", color=None, target=AMGD_TARGET_RESIDUAL, weights=None, depth=1):
+    """The whole strength build in one call: K test vectors from `seed`, nu
+    sweeps, the one-point fits and the strength graph (§3, §4.1, §4.2).
+
+    A: a torch sparse CSR tensor (CPU or CUDA; float64 values) or a
+    (row_ptr, col, val) triple of numpy arrays.  color: the coloring of the
+    multicolor sweep (required for AMGD_SWEEP_MCGS).  Returns (a, dist, S):
+    the per-slot fit coefficient and algebraic distance r = 1/LS (in the slot
+    order of the pattern: A's, or the graph of A^depth) and S = (s_row_ptr,
+    s_col), the strength graph.  Torch CUDA tensors when A is on the GPU,
+    numpy arrays otherwise."""
+    dev = False
+    if _is_torch(A):
+        import torch
+        dev = A.is_cuda
+        rp = A.crow_indices().to(torch.int64).contiguous()
+        col = A.col_indices().to(torch.int32).contiguous()
+        val = A.values().to(torch.float64).contiguous()
+    else:
+        rp, col, val = A
+    with Handle(rp, col, val, K, seed) as h:
+        h.set_precision(precision)
+        if target != AMGD_TARGET_RESIDUAL:
+            h.set_target(target)
+        if weights is not None:
+            h.set_weights(weights)
+        if color is not None:
+            h.set_coloring(color)
+        if depth > 1:
+            h.set_search_depth(depth)
+        h.relax(nu, omega, sweep)
+        if dev:
+            import torch
+            out = {k: torch.empty(h.nnz_p, dtype=torch.float64, device=A.device)
+                   for k in ("a", "dist")}
+            h.distances(theta, want=("a", "dist"), out=out)
+            s_rp = torch.empty(h.n + 1, dtype=torch.int64, device=A.device)
+            s_col = torch.empty(max(h.E_p, 1), dtype=torch.int32, device=A.device)
+            h.strength(s_rp, s_col)
+            torch.cuda.synchronize(A.device)
+            S = (s_rp, s_col[: int(s_rp[-1].item())])
+        else:
+            out = h.distances(theta, want=("a", "dist"))
+            S = h.strength()
+    return out["a"], out["dist"], S
+
+
 def header_symbols(header_path: str | None = None) -> list:
     """Names of the functions declared in include/amgd.h."""
     import re

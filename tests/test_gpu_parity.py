@@ -233,6 +233,32 @@ def test_edge_case_matrices(K):
             compare_fp64(rp, col, val, got, want, 0.5)
 
 
+@pytest.mark.parametrize("where", ["cuda", "cpu", "numpy"])
+def test_one_call_build(where):
+    """amgd.build on a torch sparse CSR tensor (GPU or CPU) or a numpy triple
+    equals the oracle's build (FP64)."""
+    import torch
+    rp, col, val = inputs.aniso2d_9pt(32, 1e-3, math.pi / 6)
+    color = inputs.red_black(32)
+    want = oracle.build(rp, col, val, 8, 3, 4, 1.0, 0.5, oracle.SWEEP_MCGS, color)
+    if where == "numpy":
+        A = (rp, col, val)
+    else:
+        A = torch.sparse_csr_tensor(torch.from_numpy(rp), torch.from_numpy(col.astype(np.int64)),
+                                    torch.from_numpy(val), size=(1024, 1024)).to(where)
+    a, dist, (s_rp, s_col) = amgd.build(A, 8, seed=3, nu=4, omega=1.0, sweep=amgd.AMGD_SWEEP_MCGS,
+                                        theta=0.5, color=color)
+    if where == "cuda":
+        a, dist, s_rp, s_col = (t.cpu().numpy() for t in (a, dist, s_rp, s_col))
+    rows, cols = edge_rows(rp, col)
+    off = rows != cols
+    syy, sxx = ls_scales(rp, col, want["X"], want["Y"])
+    check_a(a, want["a"], syy, sxx, off)
+    with np.errstate(divide="ignore"):
+        check_ls(1.0 / dist, want["ls"], syy, off)
+    check_flags(flags_from_strength(rp, col, s_rp, s_col), want, rp, col, 0.5, 1e-9)
+
+
 def test_empty_matrix():
     rp = np.zeros(1, np.int64)
     col = np.zeros(0, np.int32)
