@@ -7,11 +7,11 @@
 // sweeps use, so a color phase is one contiguous range of rows), the max norm
 // of the result (exact: a maximum of bit patterns), the candidates
 // sigma_i = |u_i| / ||u|| > tol, the strength graph restricted to F, and an
-// independent set of the candidates.  The set is the
-// greedy set in a fixed priority order (more candidates depending strongly on
-// the point first, then a Philox key, then the smaller index); it is reached
-// by rounds of local maxima, which select exactly the points the greedy order
-// selects, so the result does not depend on the thread schedule.
+// independent set of the candidates.  The set is the greedy set in a fixed
+// priority order (more candidates depending strongly on the point first, then
+// a Philox key, then the smaller index); it is reached by rounds of local
+// maxima, which select exactly the points the greedy order selects, so the
+// result does not depend on the thread schedule.
 //
 // Rounding follows the sweeps of the test vectors: a row sum is a chain of
 // fused multiply-adds in CSR order and the update is x_i - (omega/a_ii) s as
@@ -41,14 +41,9 @@ __global__ void k_cr_start(const int32_t *__restrict__ perm, const uint8_t *__re
     }
 }
 
-// one F-relaxation phase over the color-ordered rows [r0, r1): weighted
-// Jacobi (r0 = 0, r1 = n, every neighbour from u), or one color of a
-// multicolor Gauss-Seidel sweep (neighbours of earlier colors -- rows below
-// r0 -- from un, all others from u).  Coarse rows stay 0 (Eq. (3.4)).
-//
 // The row weight omega / a_rr is the same correctly rounded quotient in every
-// sweep, so it is formed once per call (k_cr_cdiag) rather than per sweep: on
-// this part a double division costs about as much as the row's sum.
+// sweep, so it is formed once per call rather than per sweep: on this part a
+// double division costs about as much as the row's sum.
 __global__ void k_cr_cdiag(const double *__restrict__ diag, double omega,
                            double *__restrict__ cdiag, int32_t n)
 {
@@ -56,6 +51,10 @@ __global__ void k_cr_cdiag(const double *__restrict__ diag, double omega,
         cdiag[r] = omega / diag[r];
 }
 
+// one F-relaxation phase over the color-ordered rows [r0, r1): weighted
+// Jacobi (r0 = 0, r1 = n, every neighbour from u), or one color of a
+// multicolor Gauss-Seidel sweep (neighbours of earlier colors -- rows below
+// r0 -- from un, all others from u).  Coarse rows stay 0 (Eq. (3.4)).
 __global__ void k_cr_sweep(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                            const double *__restrict__ val, const double *__restrict__ cdiag,
                            const uint8_t *__restrict__ coarse_p, int32_t r0, int32_t r1,
