@@ -362,10 +362,11 @@ def run_e2e(h, mats, w, sweep, steps, adjoint=None):
                 E_s=E_s)
 
 
-def oracle_step(oracle, rp, col, val, w, color):
+def oracle_step(oracle, rp, col, val, w, color, keep=None):
     """One step of the workload on the FP64 oracle: the strength build, or
     for a workload with a checkpoint interval the forward path and its
-    reverse pass (the oracle keeps every iterate)."""
+    reverse pass (the oracle keeps every iterate).  keep (a dict) receives
+    the build's outputs."""
     if w.get("adjoint"):
         X0 = oracle.tv_init(len(rp) - 1, w["K"], w["seed"])
         oracle.adjoint_jacobi(rp, col, val, X0, w["nu"], w["omega"], w["theta"])
@@ -373,12 +374,47 @@ def oracle_step(oracle, rp, col, val, w, color):
         b = oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
                          sweep=oracle.SWEEP_MCGS if w["sweep"] == "mcgs" else oracle.SWEEP_JACOBI,
                          color=color, d=w.get("depth", 1))
+        if keep is not None:
+            keep.update(b)
         return len(b["pcol"]) - (len(rp) - 1)
     return len(col) - (len(rp) - 1)
 
 
-def cpu_oracle_time(cfg, w, budget_s=20.0):
-    """The FP64 oracle (single thread) on a bounded sample of the workload."""
+def accuracy_vs_oracle(h, mat, ref, theta):
+    """End-to-end error of the GPU build (its storage precision) against the
+    FP64 oracle's build of the same matrix, seed and sweeps: relative error of
+    LS where LS is not a cancellation residue (LS >= 1e-6 S_yy), and the edges
+    whose strength flag differs, inside and outside the band |rho - theta| <=
+    1e-2 (rho = min_k LS_ik / LS_ij, the oracle's)."""
+    rp, col, _ = mat
+    n = len(rp) - 1
+    got = h.distances(theta, want=("ls",))["ls"]
+    s_rp, s_col = h.strength()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    off = rows != col
+    want = ref["ls"]
+    syy = np.einsum("ij,ij->i", ref["Y"], ref["Y"])
+    big = off & (want >= 1e-6 * syy[rows])
+    rel = np.abs(got[big] - want[big]) / want[big]
+    srows = np.repeat(np.arange(n), np.diff(s_rp))
+    flag = np.isin(rows.astype(np.int64) * n + col, srows.astype(np.int64) * n + s_col)
+    m = np.full(n, np.inf)
+    np.minimum.at(m, rows[off], want[off])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rho = np.where(want[off] > 0, m[rows[off]] / want[off], 1.0)
+    diff = flag[off] != (ref["flag"][off] == 1)
+    band = np.abs(rho - theta) <= 1e-2
+    return {"against": "FP64 oracle build of the same matrix, seed and sweeps",
+            "ls_rel_err": {"median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99)),
+                           "max": float(rel.max())},
+            "edges": int(off.sum()), "strength_flips": int(diff.sum()),
+            "flips_outside_band_1e-2": int((diff & ~band).sum())}
+
+
+def cpu_oracle_time(cfg, w, budget_s=20.0, keep=None):
+    """The FP64 oracle (single thread) on a bounded sample of the workload.
+    keep (a dict): receives the first build when the sample is the whole
+    single-matrix workload."""
     import oracle
     if cfg in ("c1", "c5"):
         mats, color = make_matrix(cfg)
@@ -398,9 +434,11 @@ def cpu_oracle_time(cfg, w, budget_s=20.0):
     edges = 0
     t0 = time.perf_counter()
     reps = 0
+    whole = cfg in ("c1", "c2") and len(mats) == 1
     while True:
         for rp, col, val in mats:
-            edges += oracle_step(oracle, rp, col, val, w, color)
+            edges += oracle_step(oracle, rp, col, val, w, color,
+                                 keep if (whole and reps == 0 and keep is not None) else None)
         reps += 1
         if time.perf_counter() - t0 > budget_s / 3 or reps >= 3:
             break
@@ -901,7 +939,10 @@ def main():
     line["clocks"] = {k: r["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} \
         if r["clocks"] else None
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_oracle_time(cfg, w)
+        ref = {}
+        line["cpu_baseline"] = cpu_oracle_time(cfg, w, keep=ref)
+        if ref and not args.scale:
+            line["accuracy"] = accuracy_vs_oracle(r["h"], mats[0], ref, w["theta"])
     r["h"].close()
     if rank == 0:
         print(json.dumps(line), flush=True)
