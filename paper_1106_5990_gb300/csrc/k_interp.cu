@@ -36,9 +36,6 @@ namespace {
 constexpr int kWarps = 4;                    // warps per block
 constexpr int kMaxK = 64;                    // components per vector
 // shared memory of one warp, in doubles (the candidate list takes 16 doubles)
-constexpr int kWarpDoubles = kInterpMaxCand * kMaxK + kInterpMaxCand * kInterpMaxCand +
-                             kInterpMaxCand + 2 * kMaxK + kInterpMaxCand / 2;
-constexpr int kInterpSmem = kWarps * kWarpDoubles * (int)sizeof(double);
 
 // exact widening to double.  Normal BF16/FP32 numbers are re-biased by bit
 // manipulation on the integer pipe (exponent + 1023 - 127, mantissa shifted
@@ -152,40 +149,62 @@ __device__ __forceinline__ int solve_small(int s, double *Gs, double *bs, double
     return 0;
 }
 
-// the subset's fit: 0 and p, res, or -1 when the normal equations are singular
-__device__ int fit_subset(int s, const int *idx, const double *G, const double *b, int m,
-                          const double *xs, const double *y, const double *w, int K, double *p,
-                          double &res)
+
+// shared memory of one warp of k_ls_interp for K components: the Gram matrix
+// (kInterpMaxCand^2), b and sqrt(G_aa) (kInterpMaxCand each), y and w (K
+// each), in doubles; then the candidate rows in the storage type; then the
+// candidate columns
+template <class TS>
+__host__ __device__ constexpr int warp_interp_bytes(int K)
 {
-    double Gs[kInterpMaxCaliber * kInterpMaxCaliber], bs[kInterpMaxCaliber];
-    for (int a = 0; a < s; ++a) {
-        bs[a] = b[idx[a]];
-        for (int c = 0; c < s; ++c) Gs[a * s + c] = G[idx[a] * m + idx[c]];
-    }
-    if (solve_small(s, Gs, bs, p) != 0) return -1;
-    double r = 0.0;
-    for (int k = 0; k < K; ++k) {
-        double e = y[k];
-        for (int a = 0; a < s; ++a) e = __dsub_rn(e, __dmul_rn(p[a], xs[idx[a] * kMaxK + k]));
-        r = __dadd_rn(r, __dmul_rn(__dmul_rn(w[k], e), e));
-    }
-    res = r;
-    return 0;
+    return (kInterpMaxCand * kInterpMaxCand + 2 * kInterpMaxCand + 2 * K) * 8 +
+           ((kInterpMaxCand * K * (int)sizeof(TS) + 15) & ~15) + kInterpMaxCand * 4;
 }
 
-template <class TS>
+template <class TS> __device__ __forceinline__ double widen_val(TS v);
+template <> __device__ __forceinline__ double widen_val<double>(double v) { return v; }
+template <> __device__ __forceinline__ double widen_val<float>(float v)
+{
+    return widen_f32_bits(__float_as_uint(v));
+}
+template <> __device__ __forceinline__ double widen_val<__nv_bfloat16>(__nv_bfloat16 v)
+{
+    return widen_f32_bits((uint32_t)__bfloat16_as_ushort(v) << 16);
+}
+
+// (w_k x_ak) x_ck with the definition's rounding; with unit weights and BF16
+// storage the product is formed exactly in FP32 (bf16_product)
+template <class TS, bool UNIT_W>
+__device__ __forceinline__ double gram_term(TS xa, TS xc, double wk)
+{
+    if constexpr (UNIT_W && std::is_same<TS, __nv_bfloat16>::value) {
+        return bf16_product(__bfloat16_as_ushort(xa), __bfloat16_as_ushort(xc));
+    } else {
+        const double a = widen_val<TS>(xa);
+        return __dmul_rn(UNIT_W ? a : __dmul_rn(wk, a), widen_val<TS>(xc));
+    }
+}
+
+// One warp per fine row with more than kInterpRowCand candidates: lanes over
+// Gram entries (one triangle under unit weights, where G_ac = G_ca bit for
+// bit) and over subsets; each lane prunes its subsets against its own best
+// explicit LS with the rounding-error bound of the thread kernel.
+template <class TS, bool UNIT_W>
 __global__ void __launch_bounds__(kWarps * 32) k_ls_interp(InterpArgs A)
 {
-    extern __shared__ __align__(16) double ism[];
+    extern __shared__ __align__(16) unsigned char ism[];
     const int wib = threadIdx.x / 32, lane = threadIdx.x % 32;
-    double *xs = ism + (size_t)wib * kWarpDoubles;                 // candidate vectors
-    double *G = xs + kInterpMaxCand * kMaxK;                       // Gram matrix
-    double *b = G + kInterpMaxCand * kInterpMaxCand;               // right-hand side
-    double *y = b + kInterpMaxCand;                                // target
-    double *w = y + kMaxK;                                         // weights
-    int32_t *cand = reinterpret_cast<int32_t *>(w + kMaxK);        // candidate columns
-    const TS *X = (const TS *)A.x;
     const int K = A.K, Kp = A.Kp, C = A.caliber;
+    unsigned char *base = ism + (size_t)wib * warp_interp_bytes<TS>(K);
+    double *G = reinterpret_cast<double *>(base);                   // Gram matrix, stride m
+    double *b = G + kInterpMaxCand * kInterpMaxCand;                // right-hand side
+    double *sg = b + kInterpMaxCand;                                // sqrt(G_aa)
+    double *y = sg + kInterpMaxCand;                                // target
+    double *w = y + K;                                              // weights
+    TS *xs = reinterpret_cast<TS *>(w + K);                         // candidate rows, stride K
+    int32_t *cand = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(xs) +
+                                                ((kInterpMaxCand * K * (int)sizeof(TS) + 15) & ~15));
+    const TS *X = (const TS *)A.x;
     for (int k = lane; k < K; k += 32) w[k] = A.w64[k];
     __syncwarp();
 
@@ -231,27 +250,47 @@ __global__ void __launch_bounds__(kWarps * 32) k_ls_interp(InterpArgs A)
         __syncwarp();
         for (int t = lane; t < m * K; t += 32) {
             const int a = t / K, k = t % K;
-            xs[a * kMaxK + k] = widen<TS>(X + (int64_t)cand[a] * Kp, k);
+            xs[a * K + k] = X[(int64_t)cand[a] * Kp + k];
         }
         __syncwarp();
-        // Gram matrix and right-hand side: sum_k (w_k u_k) v_k in component order
-        for (int t = lane; t < m * m; t += 32) {
-            const int a = t / m, c = t % m;
+        // Gram matrix (G_ac = sum_k (w_k x_ak) x_ck in component order) and b
+        const int ntri = UNIT_W ? m * (m + 1) / 2 : m * m;
+        for (int t = lane; t < ntri; t += 32) {
+            int a, c;
+            if (UNIT_W) {
+                a = 0;
+                int rowbase = 0;
+                while (t >= rowbase + (m - a)) { rowbase += m - a; ++a; }
+                c = a + (t - rowbase);
+            } else {
+                a = t / m;
+                c = t % m;
+            }
             double g = 0.0;
-            for (int k = 0; k < K; ++k) g = __dadd_rn(g, __dmul_rn(__dmul_rn(w[k], xs[a * kMaxK + k]), xs[c * kMaxK + k]));
-            G[t] = g;
+            for (int k = 0; k < K; ++k) g = __dadd_rn(g, gram_term<TS, UNIT_W>(xs[a * K + k], xs[c * K + k], w[k]));
+            G[a * m + c] = g;
+            if (UNIT_W) G[c * m + a] = g;
         }
         for (int a = lane; a < m; a += 32) {
             double g = 0.0;
-            for (int k = 0; k < K; ++k) g = __dadd_rn(g, __dmul_rn(__dmul_rn(w[k], y[k]), xs[a * kMaxK + k]));
+            for (int k = 0; k < K; ++k) {
+                const double wy = UNIT_W ? y[k] : __dmul_rn(w[k], y[k]);
+                g = __dadd_rn(g, __dmul_rn(wy, widen_val<TS>(xs[a * K + k])));
+            }
             b[a] = g;
         }
         double syy = 0.0;
-        for (int k = 0; k < K; ++k) syy = __dadd_rn(syy, __dmul_rn(__dmul_rn(w[k], y[k]), y[k]));
+        for (int k = 0; k < K; ++k) {
+            const double wy = UNIT_W ? y[k] : __dmul_rn(w[k], y[k]);
+            syy = __dadd_rn(syy, __dmul_rn(wy, y[k]));
+        }
+        __syncwarp();
+        for (int a = lane; a < m; a += 32) sg[a] = sqrt(G[a * m + a]);
+        const double sy = sqrt(syy);
         __syncwarp();
 
-        // best set of every size: lane-local best, then a warp reduction
-        // (smallest LS, then smallest rank)
+        // best set of every size: lane-local best (pruned against itself), then
+        // a warp reduction (smallest LS, then smallest rank)
         double best_ls[kInterpMaxCaliber + 1];
         int best_idx[kInterpMaxCaliber + 1][kInterpMaxCaliber];
         double best_p[kInterpMaxCaliber + 1][kInterpMaxCaliber];
@@ -266,10 +305,36 @@ __global__ void __launch_bounds__(kWarps * 32) k_ls_interp(InterpArgs A)
             int64_t mine_rank = INT64_MAX;
             for (int64_t t = lane; t < total; t += 32) {
                 int idx[kInterpMaxCaliber];
-                double p[kInterpMaxCaliber], res;
+                double Gs[kInterpMaxCaliber * kInterpMaxCaliber], bs[kInterpMaxCaliber];
+                double p[kInterpMaxCaliber];
                 unrank(m, s, t, idx);
-                if (fit_subset(s, idx, G, b, m, xs, y, w, K, p, res) == 0 && res < mine) {
-                    mine = res;
+                for (int a = 0; a < s; ++a) {
+                    bs[a] = b[idx[a]];
+                    for (int c = 0; c < s; ++c) Gs[a * s + c] = G[idx[a] * m + idx[c]];
+                }
+                if (solve_small(s, Gs, bs, p) != 0) continue;
+                if (mine_rank != INT64_MAX) {
+                    // the bound of the thread kernel (see k_ls_interp_rows)
+                    double q = syy, mm = sy;
+                    for (int a = 0; a < s; ++a) {
+                        q = __dsub_rn(q, __dmul_rn(__dmul_rn(2.0, p[a]), b[idx[a]]));
+                        mm = __dadd_rn(mm, __dmul_rn(fabs(p[a]), sg[idx[a]]));
+                    }
+                    for (int a = 0; a < s; ++a)
+                        for (int c = 0; c < s; ++c)
+                            q = __dadd_rn(q, __dmul_rn(__dmul_rn(p[a], G[idx[a] * m + idx[c]]), p[c]));
+                    const double bound = (double)(4 * (s * s + 6 * s + 2 * K + 8)) * 0x1p-53 * mm * mm;
+                    if (__dsub_rn(q, bound) >= mine) continue;
+                }
+                double r = 0.0;
+                for (int k = 0; k < K; ++k) {
+                    double ek = y[k];
+                    for (int a = 0; a < s; ++a) ek = __dsub_rn(ek, __dmul_rn(p[a], widen_val<TS>(xs[idx[a] * K + k])));
+                    const double we = UNIT_W ? ek : __dmul_rn(w[k], ek);
+                    r = __dadd_rn(r, __dmul_rn(we, ek));
+                }
+                if (r < mine) {
+                    mine = r;
                     mine_rank = t;
                 }
             }
@@ -284,8 +349,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_ls_interp(InterpArgs A)
                 have[s] = true;
                 best_ls[s] = bl;
                 unrank(m, s, br, best_idx[s]);
-                double res;
-                fit_subset(s, best_idx[s], G, b, m, xs, y, w, K, best_p[s], res);
+                // the winning set's weights, solved again (the same elimination)
+                double Gs[kInterpMaxCaliber * kInterpMaxCaliber], bs[kInterpMaxCaliber];
+                for (int a = 0; a < s; ++a) {
+                    bs[a] = b[best_idx[s][a]];
+                    for (int c = 0; c < s; ++c) Gs[a * s + c] = G[best_idx[s][a] * m + best_idx[s][c]];
+                }
+                solve_small(s, Gs, bs, best_p[s]);
             }
         }
         if (lane == 0) {
@@ -595,21 +665,29 @@ cudaError_t launch_rows_kernel(const InterpArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <class TS, bool UNIT_W>
+cudaError_t launch_warp_kernel(const InterpArgs &a, cudaStream_t s)
+{
+    static bool opted = false;
+    if (!opted) {
+        const cudaError_t e = cudaFuncSetAttribute(k_ls_interp<TS, UNIT_W>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   kWarps * warp_interp_bytes<TS>(kMaxK));
+        if (e != cudaSuccess) return e;
+        opted = true;
+    }
+    const int64_t want = ((int64_t)a.n + kWarps - 1) / kWarps;
+    const unsigned grid = (unsigned)(want < 152 * 8 ? want : 152 * 8);
+    k_ls_interp<TS, UNIT_W><<<grid, kWarps * 32, kWarps * warp_interp_bytes<TS>(a.K), s>>>(a);
+    return cudaGetLastError();
+}
+
 template <class TS>
 cudaError_t launch_interp_typed(const InterpArgs &a, cudaStream_t s)
 {
     cudaError_t e = a.unit_w ? launch_rows_kernel<TS, true>(a, s) : launch_rows_kernel<TS, false>(a, s);
     if (e != cudaSuccess) return e;
-    static bool opted = false;
-    if (!opted) {
-        e = cudaFuncSetAttribute(k_ls_interp<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kInterpSmem);
-        if (e != cudaSuccess) return e;
-        opted = true;
-    }
-    const int64_t want = ((int64_t)a.n + kWarps - 1) / kWarps;
-    const unsigned grid = (unsigned)(want < 152 * 4 ? want : 152 * 4);
-    k_ls_interp<TS><<<grid, kWarps * 32, kInterpSmem, s>>>(a);
-    return cudaGetLastError();
+    return a.unit_w ? launch_warp_kernel<TS, true>(a, s) : launch_warp_kernel<TS, false>(a, s);
 }
 
 }  // namespace

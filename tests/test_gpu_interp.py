@@ -105,8 +105,9 @@ def test_interp_unit_weights_both_kernels(prec):
         assert np.array_equal(g, w_)
 
 
+@pytest.mark.parametrize("depth", [1, 2])
 @pytest.mark.parametrize("unit_w", [True, False])
-def test_interp_ties_and_exact_fits(unit_w):
+def test_interp_ties_and_exact_fits(unit_w, depth):
     """Plain target with planted structure: coarse candidates that repeat one
     another exactly (ties between sets, singular pairs) and fine rows that
     are exact combinations of two coarse neighbours (LS = 0 up to rounding),
@@ -124,13 +125,15 @@ def test_interp_ties_and_exact_fits(unit_w):
         if len(nb) >= 2:
             X[i] = 0.5 * X[nb[0]] - 0.25 * X[nb[1]]         # exact in FP64
     w = np.ones(K) if unit_w else rng.uniform(0.5, 2.0, K)
+    prp, pcol = oracle.distance_graph(rp, col, depth)     # depth 2: rows with > 8 candidates
     with amgd.Handle(rp, col, val, K, 1) as h:
         h.set_target(amgd.AMGD_TARGET_PLAIN)
         h.set_weights(w)
+        h.set_search_depth(depth)
         h.set_vectors(X)
         got = h.ls_interpolation(coarse, 3, 1.5)
     Y = oracle.target(rp, col, val, X, oracle.TARGET_PLAIN)
-    want = oracle.ls_interp(X, Y, rp, col, coarse, 3, 1.5, w)
+    want = oracle.ls_interp(X, Y, prp, pcol, coarse, 3, 1.5, w)
     for g, w_ in zip(got, want):
         assert np.array_equal(g, w_)
 
