@@ -411,7 +411,7 @@ def accuracy_vs_oracle(h, mat, ref, theta):
             "flips_outside_band_1e-2": int((diff & ~band).sum())}
 
 
-def cpu_oracle_time(cfg, w, budget_s=20.0, keep=None):
+def cpu_oracle_time(cfg, w, sample_s=20.0, keep=None):
     """The FP64 oracle (single thread) on a bounded sample of the workload.
     keep (a dict): receives the first build when the sample is the whole
     single-matrix workload."""
@@ -440,7 +440,7 @@ def cpu_oracle_time(cfg, w, budget_s=20.0, keep=None):
             edges += oracle_step(oracle, rp, col, val, w, color,
                                  keep if (whole and reps == 0 and keep is not None) else None)
         reps += 1
-        if time.perf_counter() - t0 > budget_s / 3 or reps >= 3:
+        if time.perf_counter() - t0 > sample_s / 3 or reps >= 3:
             break
     dt = time.perf_counter() - t0
     return dict(value=edges / dt, unit="edges/s", cores=1, kind="oracle",
@@ -763,7 +763,7 @@ def oracle_coarsen_step(oracle, rp, col, val, w, color, b):
     return len(rp) - 1
 
 
-def cpu_coarsen_time(w, budget_s=20.0, N=512):
+def cpu_coarsen_time(w, sample_s=20.0, N=512):
     """The FP64 oracle (single thread) on CR + interpolation of an N x N
     sub-grid of the same operator (its own build, untimed)."""
     import oracle
@@ -777,7 +777,7 @@ def cpu_coarsen_time(w, budget_s=20.0, N=512):
     while True:
         rows += oracle_coarsen_step(oracle, rp, col, val, w, color, b)
         reps += 1
-        if time.perf_counter() - t0 > budget_s / 3 or reps >= 3:
+        if time.perf_counter() - t0 > sample_s / 3 or reps >= 3:
             break
     dt = time.perf_counter() - t0
     return dict(value=rows / dt, unit="rows/s", cores=1, kind="oracle",

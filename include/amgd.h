@@ -450,7 +450,7 @@ int amgd_graph_capture_backward(amgd_handle h, uint64_t seed, int32_t nu, double
  *   any memory.  The paper has no counterpart to this entry point: it exists
  *   for callers that cannot call cudaMalloc (code running inside a memory
  *   pool or arena that owns every device allocation of the process, or a
- *   loop that must never take the driver's allocation lock), since every
+ *   loop that must never take the CUDA driver's allocation lock), since every
  *   handle-based entry point allocates device memory for its handle.
  *
  *   All pointers are DEVICE memory of the current device:

@@ -5,7 +5,7 @@
 // Why it exists: some callers cannot call cudaMalloc -- code running inside a
 // memory pool or arena that owns every device allocation of the process, an
 // allocator-free real-time loop, or a host thread that must never take the
-// driver's allocation lock.  Every handle-based entry point allocates device
+// CUDA driver's allocation lock.  Every handle-based entry point allocates device
 // memory (the handle owns its buffers), so such callers get this one entry
 // point instead: the caller passes every input and output buffer, and the only
 // working memory is the file-scope array below.

@@ -1,7 +1,7 @@
 """amgd_strength_noalloc: the strength CSR for callers that cannot allocate.
 
 Callers that run inside a memory pool or arena owning every device
-allocation, or that must never take the driver's allocation lock, cannot use
+allocation, or that must never take the CUDA driver's allocation lock, cannot use
 the handle-based entry points (a handle allocates its buffers).  They get
 amgd_strength_noalloc, which works only in caller buffers plus a static
 device array of the library.  This file checks, through the C ABI, that two
