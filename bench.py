@@ -926,6 +926,27 @@ def main():
                         "mixed_over_fp64": value / v64}
         r64["h"].close()
 
+    # FP32 storage beside a BF16 headline: the mixed configuration whose end-to-end
+    # distances stay within 1e-3 of the FP64 oracle (BF16 storage alone moves them by
+    # about 2e-3); its accuracy is taken against the same oracle build below
+    r32 = None
+    if not args.no_side and precision == "bf16":
+        side_steps = max(3, min(args.steps, 100))
+        r32 = run_gpu_arm(mats, color, w, "fp32", side_steps, 3, rank, flush, want_clocks=False,
+                          tune_cache=args.tune_cache)
+        v32, t32 = whole_job(float(r32["step_ms"].sum()), E, side_steps)
+        ab32 = step_bytes(r32, "fp32")
+        rl32 = r32["phase_ms"][1] / launches_relax
+        a32 = ab32["relax_per_launch"] / (rl32 * 1e-3) / 1e9
+        line["fp32"] = {"value": v32, "unit": "edges/s", "ms_per_step": t32,
+                        "steps": side_steps, "shapes": {"relax": list(r32["shapes"][0]),
+                                                        "edge": list(r32["shapes"][1])},
+                        "phase_ms": dict(zip(names, r32["phase_ms"].tolist())),
+                        "relax_launch_us": rl32 * 1e3, "relax_hbm_gbs": a32,
+                        "relax_hbm_frac": a32 / peak}
+        if "fp64" in line:
+            line["fp32"]["over_fp64"] = v32 / line["fp64"]["value"]
+
     e2e_steps = max(3, min(args.steps, 50))
     e = run_e2e(r["h"], mats, w, r["sweep"], e2e_steps, adjoint=adj)
     v_e2e, _ = whole_job(1e3 * e["seconds"], E, 1)
@@ -943,6 +964,10 @@ def main():
         line["cpu_baseline"] = cpu_oracle_time(cfg, w, keep=ref)
         if ref and not args.scale:
             line["accuracy"] = accuracy_vs_oracle(r["h"], mats[0], ref, w["theta"])
+            if r32 is not None:
+                line["fp32"]["accuracy"] = accuracy_vs_oracle(r32["h"], mats[0], ref, w["theta"])
+    if r32 is not None:
+        r32["h"].close()
     r["h"].close()
     if rank == 0:
         print(json.dumps(line), flush=True)
