@@ -421,6 +421,35 @@ def test_generator_matches_paper_stencil_SA():
         assert abs(row[(2 + dy) * N + 2 + dx] - v) <= 1e-12
 
 
+def test_generator_cross_term_matches_paper_Sxy():
+    """The 7-point generator's u_xy part is the S~_xy of Eq. (5.6) (alpha = pi/4):
+    A = -h^2 (a u_xx + b u_xy + c u_yy), so A minus its five-point part is
+    -b h^2 S~_xy, for any eps and any alpha that uses the same neighbours."""
+    parts, cur = [], None
+    for l in open(os.path.join(GOLDEN, "stencil_Sxy.txt")):
+        if not l.strip() or l.startswith("#"):
+            continue
+        if l.startswith("part"):
+            cur = []
+            parts.append(cur)
+        else:
+            cur.append([float(v) for v in l.split()])
+    assert len(parts) == 2 and all(np.array(p).shape == (3, 3) for p in parts)
+    M = (np.array(parts[0]) + np.array(parts[1])) / 2.0        # h^2 S~_xy
+    want = {(dx, dy): M[1 - dy, 1 + dx] for dx in (-1, 0, 1) for dy in (-1, 0, 1)
+            if M[1 - dy, 1 + dx] != 0.0}
+    assert len(want) == 7 and abs(sum(want.values())) == 0.0    # annihilates constants
+    for eps, alpha in ((0.1, np.pi / 4), (1e-3, np.pi / 6), (0.3, np.pi / 8)):
+        a, b, c = inputs.aniso_coefficients(eps, alpha)
+        st = inputs.aniso7_stencil(eps, alpha, "ne")
+        five = {(0, 0): 2 * a + 2 * c, (1, 0): -a, (-1, 0): -a, (0, 1): -c, (0, -1): -c}
+        got = {k: -(st.get(k, 0.0) - five.get(k, 0.0)) / b for k in set(st) | set(five)}
+        got = {k: v for k, v in got.items() if abs(v) > 1e-12}
+        assert set(got) == set(want), (eps, alpha)
+        for k in want:
+            assert abs(got[k] - want[k]) <= 1e-12, (eps, alpha, k)
+
+
 def test_check_csr(orc):
     rp, col, val = inputs.lap1d(4)
     assert orc.check_csr(rp, col, val) == 0
