@@ -158,14 +158,58 @@ def ptr_mem(x):
     if x is None:
         return None, AMGD_MEM_HOST
     if _is_torch(x):
-        assert x.is_contiguous()
+        if not x.is_contiguous():
+            raise ValueError("the library needs a contiguous tensor")
         return x.data_ptr(), (AMGD_MEM_DEVICE if x.is_cuda else AMGD_MEM_HOST)
-    assert x.flags["C_CONTIGUOUS"]
+    if not isinstance(x, np.ndarray) or not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("the library needs a contiguous numpy array")
     return x.ctypes.data, AMGD_MEM_HOST
 
 
 def _host(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _count(x) -> int:
+    return x.numel() if _is_torch(x) else x.size
+
+
+def arg_in(x, dtype, count, name):
+    """An input buffer for the library: a contiguous numpy array or torch
+    tensor of `dtype` with at least `count` elements.  Another dtype, or a
+    non-contiguous layout, is converted (a copy on the same device).  The
+    library reads exactly the documented number of elements, so a shorter
+    buffer is refused here instead of being read past its end."""
+    if _is_torch(x):
+        import torch
+        td = getattr(torch, np.dtype(dtype).name)
+        if x.dtype != td or not x.is_contiguous():
+            x = x.to(td).contiguous()
+    else:
+        x = _host(x, dtype)
+    if _count(x) < count:
+        raise ValueError("%s: %d elements, the library reads %d" % (name, _count(x), count))
+    return x
+
+
+def arg_out(x, dtype, count, name):
+    """An output buffer the library writes: it must already be a contiguous,
+    writable numpy array or torch tensor of `dtype` with at least `count`
+    elements (a converted copy would not be the caller's buffer)."""
+    if _is_torch(x):
+        import torch
+        td = getattr(torch, np.dtype(dtype).name)
+        if x.dtype != td or not x.is_contiguous():
+            raise TypeError("%s: expected a contiguous %s tensor, got %s%s"
+                            % (name, td, x.dtype, "" if x.is_contiguous() else " (strided)"))
+    elif (not isinstance(x, np.ndarray) or x.dtype != np.dtype(dtype)
+          or not x.flags["C_CONTIGUOUS"] or not x.flags["WRITEABLE"]):
+        raise TypeError("%s: expected a contiguous writable numpy array of %s"
+                        % (name, np.dtype(dtype).name))
+    if _count(x) < count:
+        raise ValueError("%s: %d elements, the library writes up to %d"
+                         % (name, _count(x), count))
+    return x
 
 
 class Handle:
@@ -175,19 +219,23 @@ class Handle:
         L = lib()
         self.h = ctypes.c_void_p()
         if batch is None:
-            if _is_torch(row_ptr):
-                rp, c, v = row_ptr.contiguous(), col.contiguous(), val.contiguous()
-                n = rp.numel() - 1
-            else:
-                rp, c, v = _host(row_ptr, np.int64), _host(col, np.int32), _host(val, np.float64)
-                n = len(rp) - 1
+            rp = arg_in(row_ptr, np.int64, 1, "row_ptr")
+            n = _count(rp) - 1
+            nnz = int(rp[-1])                  # the library reads col and val up to row_ptr[n]
+            c = arg_in(col, np.int32, max(nnz, 0), "col")
+            v = arg_in(val, np.float64, max(nnz, 0), "val")
             self._keep = (rp, c, v)
             prp, mem = ptr_mem(rp)
             check(L.amgd_create(prp, ptr_mem(c)[0], ptr_mem(v)[0], n, K, seed, mem,
                                 ctypes.byref(self.h)))
         else:
-            mats = [(_host(r, np.int64), _host(c, np.int32), _host(v, np.float64))
-                    for r, c, v in batch]
+            mats = []                          # host arrays (the batch form reads host memory)
+            for b, (r, c, v) in enumerate(batch):
+                r = arg_in(_host(r, np.int64), np.int64, 1, "row_ptr of matrix %d" % b)
+                nnz = max(int(r[-1]), 0)
+                mats.append((r, arg_in(_host(c, np.int32), np.int32, nnz, "col of matrix %d" % b),
+                             arg_in(_host(v, np.float64), np.float64, nnz,
+                                    "val of matrix %d" % b)))
             nmat = len(mats)
             arr = lambda xs: (ctypes.c_void_p * nmat)(*[x.ctypes.data for x in xs])
             rps, cols, vals = arr([m[0] for m in mats]), arr([m[1] for m in mats]), \
@@ -202,6 +250,8 @@ class Handle:
                            ctypes.byref(k), ctypes.byref(nm)), self.h)
         self.n, self.nnz, self.E, self.K, self.nmat = n.value, nnz.value, E.value, k.value, nm.value
         self.nnz_p, self.E_p = self.nnz, self.E       # entries of the fit pattern (G_d)
+        self._pending = []        # buffers of asynchronous calls, kept alive until sync()
+        self._graph_keep = ()     # buffers a captured graph writes, kept alive with it
 
     # -- plumbing -------------------------------------------------------------
     def _ck(self, status):
@@ -250,12 +300,8 @@ class Handle:
             self._ck(lib().amgd_set_weights(self.h, w.ctypes.data))
 
     def set_coloring(self, color, ncolors=None):
-        if _is_torch(color):
-            c = color.to(dtype=__import__("torch").int32).contiguous()
-            nc = int(c.max().item()) + 1 if ncolors is None else ncolors
-        else:
-            c = _host(color, np.int32)
-            nc = int(c.max()) + 1 if ncolors is None else ncolors
+        c = arg_in(color, np.int32, self.n, "color")
+        nc = int(c.max()) + 1 if ncolors is None else ncolors
         p, mem = ptr_mem(c)
         self._ck(lib().amgd_set_coloring(self.h, p, nc, mem))
 
@@ -263,18 +309,18 @@ class Handle:
         self._ck(lib().amgd_init_vectors(self.h, seed))
 
     def set_vectors(self, X):
-        X = X if _is_torch(X) else _host(X, np.float64)
+        X = arg_in(X, np.float64, self.n * self.K, "X")
         p, mem = ptr_mem(X)
         self._ck(lib().amgd_set_vectors(self.h, p, mem))
 
     def get_vectors(self, out=None):
         out = np.empty((self.n, self.K), dtype=np.float64) if out is None else out
-        p, mem = ptr_mem(out)
+        p, mem = ptr_mem(arg_out(out, np.float64, self.n * self.K, "out"))
         self._ck(lib().amgd_get_vectors(self.h, p, mem))
         return out
 
     def set_values(self, val):
-        val = val if _is_torch(val) else _host(val, np.float64)
+        val = arg_in(val, np.float64, self.nnz, "val")
         p, mem = ptr_mem(val)
         self._ck(lib().amgd_set_values(self.h, p, mem))
 
@@ -304,9 +350,14 @@ class Handle:
         unless `out` supplies device tensors)."""
         if out is None:
             out = {k: np.empty(self.nnz_p, dtype=np.float64) for k in want}
+        for k, v in out.items():
+            if k not in ("a", "dist", "ls"):
+                raise ValueError("distances: unknown output %r" % k)
+            arg_out(v, np.float64, self.nnz_p, k)
         ptrs = [ptr_mem(out.get(k))[0] for k in ("a", "dist", "ls")]
         mems = {ptr_mem(v)[1] for v in out.values()} or {AMGD_MEM_HOST}
-        assert len(mems) == 1
+        if len(mems) != 1:
+            raise ValueError("distances: all outputs must live in the same memory")
         self._ck(lib().amgd_distances(self.h, theta, ptrs[0], ptrs[1], ptrs[2], mems.pop()))
         return out
 
@@ -319,15 +370,16 @@ class Handle:
             self._ck(lib().amgd_strength(self.h, s_rp.ctypes.data, s_col.ctypes.data, self.E_p,
                                          ctypes.byref(nnz_s), AMGD_MEM_HOST))
             return s_rp, s_col[:nnz_s.value]
-        p_rp, mem = ptr_mem(s_row_ptr)
-        p_col, _ = ptr_mem(s_col)
-        cap = s_col.numel() if _is_torch(s_col) else len(s_col)
-        self._ck(lib().amgd_strength(self.h, p_rp, p_col, cap, None, mem))
+        p_rp, mem = ptr_mem(arg_out(s_row_ptr, np.int64, self.n + 1, "s_row_ptr"))
+        p_col, mem2 = ptr_mem(arg_out(s_col, np.int32, 0, "s_col"))
+        if mem != mem2:
+            raise ValueError("strength: outputs must live in the same memory")
+        self._ck(lib().amgd_strength(self.h, p_rp, p_col, _count(s_col), None, mem))
         return s_row_ptr, s_col
 
     def ls_interpolation(self, coarse, caliber, gamma=1.5):
         """Least-squares interpolation (host numpy): (p_row_ptr, p_col, p_val, ls)."""
-        c = coarse if _is_torch(coarse) else _host(coarse, np.uint8)
+        c = arg_in(coarse, np.uint8, self.n, "coarse")
         pc, cmem = ptr_mem(c)
         p_rp = np.empty(self.n + 1, dtype=np.int64)
         ls = np.empty(self.n, dtype=np.float64)
@@ -347,9 +399,11 @@ class Handle:
         None for the handle's last distances."""
         c = (np.zeros(self.n, dtype=np.uint8) if coarse0 is None
              else np.array(_host(coarse0, np.uint8), dtype=np.uint8, copy=True))
+        if c.size < self.n:
+            raise ValueError("coarse0: %d elements, the library reads %d" % (c.size, self.n))
         p_ls, ls_mem = None, AMGD_MEM_HOST
         if ls is not None:
-            ls = ls if _is_torch(ls) else _host(ls, np.float64)
+            ls = arg_in(ls, np.float64, self.nnz_p, "ls")
             p_ls, ls_mem = ptr_mem(ls)
         rho = np.empty(max_sets + 1, dtype=np.float64)
         m = ctypes.c_int32()
@@ -361,23 +415,33 @@ class Handle:
     def set_values_async(self, val):
         """Stream-ordered value update (numpy array, pinned torch tensor or
         device tensor); val must stay unchanged until sync()."""
-        v = val if _is_torch(val) else _host(val, np.float64)
+        if _is_torch(val):
+            # read by a copy that runs after this call returns: a converted
+            # temporary would be freed first, so the tensor must already match
+            v = arg_out(val, np.float64, self.nnz, "val")
+        else:
+            v = arg_in(val, np.float64, self.nnz, "val")
         p, mem = ptr_mem(v)
         self._ck(lib().amgd_set_values_async(self.h, p, mem))
+        self._pending.append(v)                  # alive until sync()
         return v
 
     def strength_async(self, s_rp, s_col):
         """Stream-ordered strength CSR into s_rp (n+1 int64) and s_col (int32,
         its length is the capacity); valid after sync()."""
-        p_rp, mem = ptr_mem(s_rp)
-        p_col, mem2 = ptr_mem(s_col)
-        assert mem == mem2, "outputs must live in the same memory"
-        cap = s_col.numel() if _is_torch(s_col) else s_col.size
-        self._ck(lib().amgd_strength_async(self.h, p_rp, p_col, cap, mem))
+        p_rp, mem = ptr_mem(arg_out(s_rp, np.int64, self.n + 1, "s_rp"))
+        p_col, mem2 = ptr_mem(arg_out(s_col, np.int32, 0, "s_col"))
+        if mem != mem2:
+            raise ValueError("strength_async: outputs must live in the same memory")
+        self._ck(lib().amgd_strength_async(self.h, p_rp, p_col, _count(s_col), mem))
+        self._pending.append((s_rp, s_col))
 
     def sync(self):
         """Wait for the asynchronous work of the handle; raises deferred errors."""
-        self._ck(lib().amgd_sync(self.h))
+        try:
+            self._ck(lib().amgd_sync(self.h))
+        finally:
+            self._pending.clear()
 
     def cr_stats(self):
         """(selection rounds, kernel launches) of the last cr_coarsen."""
@@ -395,12 +459,13 @@ class Handle:
         arrays (host) or torch tensors (device or host), nnz float64."""
         if out is None:
             out = np.empty(self.nnz, dtype=np.float64)
-        p_out, mem = ptr_mem(out)
+        p_out, mem = ptr_mem(arg_out(out, np.float64, self.nnz, "out"))
         p_in = None
         if ls_bar is not None:
-            ls_bar = ls_bar if _is_torch(ls_bar) else _host(ls_bar, np.float64)
+            ls_bar = arg_in(ls_bar, np.float64, self.nnz, "ls_bar")
             p_in, mem_in = ptr_mem(ls_bar)
-            assert mem_in == mem, "ls_bar and out must live in the same memory"
+            if mem_in != mem:
+                raise ValueError("backward: ls_bar and out must live in the same memory")
         wb, loss = ctypes.c_double(), ctypes.c_double()
         self._ck(lib().amgd_backward(self.h, p_in, mem, p_out, ctypes.byref(wb),
                                      ctypes.byref(loss)))
@@ -415,13 +480,20 @@ class Handle:
     def graph_capture_backward(self, seed, nu, omega, theta, val_bar):
         """Capture forward + reverse pass (built-in loss) into the handle's
         graph; val_bar: device float64 tensor of nnz entries."""
+        vb = arg_out(val_bar, np.float64, self.nnz, "val_bar")
         self._ck(lib().amgd_graph_capture_backward(self.h, seed, nu, omega, theta,
-                                                   ptr_mem(val_bar)[0]))
+                                                   ptr_mem(vb)[0]))
+        self._graph_keep = (vb,)
 
     def graph_capture(self, seed, nu, omega, sweep, theta, s_row_ptr, s_col):
-        cap = s_col.numel() if _is_torch(s_col) else len(s_col)
+        """Capture a whole build into the handle's CUDA graph; s_row_ptr (n+1
+        int64) and s_col (int32, its length is the capacity) are device
+        tensors the replays write."""
+        rp = arg_out(s_row_ptr, np.int64, self.n + 1, "s_row_ptr")
+        col = arg_out(s_col, np.int32, 0, "s_col")
         self._ck(lib().amgd_graph_capture(self.h, seed, nu, omega, sweep, theta,
-                                          ptr_mem(s_row_ptr)[0], ptr_mem(s_col)[0], cap))
+                                          ptr_mem(rp)[0], ptr_mem(col)[0], _count(col)))
+        self._graph_keep = (rp, col)
 
     def graph_launch(self):
         self._ck(lib().amgd_graph_launch(self.h))

@@ -90,3 +90,41 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(amgd, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         amgd.lib()
+
+
+def test_binding_checks_buffers_before_the_library():
+    """The binding hands the library only buffers of the documented dtype and
+    length: inputs of another dtype are converted, outputs must match, and a
+    short buffer is refused instead of being read or written past its end."""
+    torch = pytest.importorskip("torch")
+    # inputs: converted (numpy and torch), length checked
+    x = amgd.arg_in([1, 2, 3], np.int64, 3, "x")
+    assert x.dtype == np.int64 and x.flags["C_CONTIGUOUS"]
+    t = amgd.arg_in(torch.arange(6, dtype=torch.int32)[::2], np.float64, 3, "t")
+    assert t.dtype == torch.float64 and t.is_contiguous() and t.tolist() == [0.0, 2.0, 4.0]
+    same = torch.zeros(4, dtype=torch.float64)
+    assert amgd.arg_in(same, np.float64, 4, "same") is same          # no copy when it matches
+    with pytest.raises(ValueError):
+        amgd.arg_in(np.zeros(2), np.float64, 3, "short")
+    with pytest.raises(ValueError):
+        amgd.arg_in(torch.zeros(2), np.float64, 3, "short")
+    # outputs: must already be right
+    out = np.zeros(5, np.int32)
+    assert amgd.arg_out(out, np.int32, 5, "out") is out
+    for bad in (np.zeros(5, np.int64), np.zeros(10, np.int32)[::2], [0] * 5,
+                torch.zeros(5, dtype=torch.int64)):
+        with pytest.raises(TypeError):
+            amgd.arg_out(bad, np.int32, 5, "out")
+    ro = np.zeros(5, np.int32)
+    ro.flags.writeable = False
+    with pytest.raises(TypeError):
+        amgd.arg_out(ro, np.int32, 5, "out")
+    with pytest.raises(ValueError):
+        amgd.arg_out(np.zeros(4, np.int32), np.int32, 5, "out")
+    with pytest.raises(ValueError):
+        amgd.arg_out(torch.zeros(4, dtype=torch.int32), np.int32, 5, "out")
+    # ptr_mem refuses strided buffers (no assert that -O would strip)
+    with pytest.raises(ValueError):
+        amgd.ptr_mem(np.zeros(10)[::2])
+    with pytest.raises(ValueError):
+        amgd.ptr_mem(torch.zeros(10)[::2])
