@@ -460,8 +460,8 @@ int amgd_graph_capture_backward(amgd_handle h, uint64_t seed, int32_t nu, double
  *     s_row_ptr[n+1], s_col[cap]: the output CSR, rows in order, kept
  *       columns in slot order.  If s_row_ptr[n] > cap after the call, only
  *       the first cap columns were written.
- *   theta >= 0.  stream: a cudaStream_t (NULL = legacy default stream); the
- *   call only enqueues work.
+ *   n >= 0 and theta >= 0 (else ARG).  stream: a cudaStream_t (NULL =
+ *   legacy default stream); the call only enqueues work.
  *
  *   Working memory: a file-scope device array of 65536 int32 (256 KiB, one
  *   entry per tile of 4096 rows) that every GPU loading the library keeps

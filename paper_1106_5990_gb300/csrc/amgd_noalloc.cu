@@ -165,9 +165,13 @@ extern "C" int amgd_strength_noalloc(const int64_t *row_ptr, const int32_t *col,
                                      int64_t n, double theta, int64_t *s_row_ptr, int32_t *s_col,
                                      int64_t cap, void *stream)
 {
-    if (n < 0 || n > kNaMaxRows) {
+    if (n < 0) {
+        amgd::set_thread_error("amgd_strength_noalloc: n = " + std::to_string(n) + " < 0");
+        return AMGD_ERR_ARG;
+    }
+    if (n > kNaMaxRows) {
         amgd::set_thread_error("amgd_strength_noalloc: n = " + std::to_string(n) +
-                               " is outside 0.." + std::to_string(kNaMaxRows) +
+                               " is above " + std::to_string(kNaMaxRows) +
                                " (the static scratch holds " + std::to_string(kNaMaxTiles) +
                                " tiles of " + std::to_string(kNaTileRows) + " rows)");
         return AMGD_ERR_UNSUPPORTED;

@@ -80,9 +80,40 @@ def test_create_rejects_bad_input_on_host(L, case, code):
 
 def test_null_arguments(L):
     assert L.amgd_create(None, None, None, 0, 4, 0, 0, None) == amgd.AMGD_ERR_ARG
+    assert L.amgd_create_batch(0, None, None, None, None, 4, 0, 0, None) == amgd.AMGD_ERR_ARG
     assert L.amgd_destroy(None) == amgd.AMGD_OK
     assert L.amgd_relax(None, 1, 1.0, 0) == amgd.AMGD_ERR_ARG
     assert L.amgd_strength(None, None, None, 0, None, 0) == amgd.AMGD_ERR_ARG
+
+
+def test_noalloc_rejects_arguments_on_the_host(L):
+    """Size and pointer checks of amgd_strength_noalloc run before any CUDA
+    call (this machine has no GPU)."""
+    P = ctypes.c_void_p(16)          # never dereferenced: every call below fails its checks
+    assert L.amgd_strength_noalloc(P, P, P, -1, 0.5, P, P, 0, None) == amgd.AMGD_ERR_ARG
+    assert "< 0" in amgd.amgd_last_error(None)
+    assert L.amgd_strength_noalloc(P, P, P, 268_435_457, 0.5, P, P, 0, None) == \
+        amgd.AMGD_ERR_UNSUPPORTED
+    assert "268435456" in amgd.amgd_last_error(None)
+    assert L.amgd_strength_noalloc(None, P, P, 4, 0.5, P, P, 0, None) == amgd.AMGD_ERR_ARG
+    assert L.amgd_strength_noalloc(P, None, P, 4, 0.5, P, P, 0, None) == amgd.AMGD_ERR_ARG
+    assert L.amgd_strength_noalloc(P, P, P, 4, -0.5, P, P, 0, None) == amgd.AMGD_ERR_ARG
+    assert L.amgd_strength_noalloc(P, P, P, 4, 0.5, P, None, 3, None) == amgd.AMGD_ERR_ARG
+    assert L.amgd_strength_noalloc(P, P, P, 4, 0.5, P, P, -1, None) == amgd.AMGD_ERR_ARG
+
+
+# entry points whose first argument is not a handle, or that accept a NULL one
+_NOT_HANDLE_FIRST = {"amgd_create", "amgd_create_batch", "amgd_destroy", "amgd_strength_noalloc",
+                     "amgd_status_string", "amgd_last_error"}
+
+
+@pytest.mark.parametrize("name", sorted(set(amgd.SIGNATURES) - _NOT_HANDLE_FIRST))
+def test_every_handle_call_rejects_a_null_handle(L, name):
+    """A NULL handle is an argument error on the host: no entry point
+    dereferences it or reaches the device (this machine has no GPU)."""
+    _, argtypes = amgd.SIGNATURES[name]
+    args = [None if t is ctypes.c_void_p or t is ctypes.c_char_p else t(0) for t in argtypes]
+    assert getattr(L, name)(*args) == amgd.AMGD_ERR_ARG, name
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
