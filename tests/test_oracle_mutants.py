@@ -20,7 +20,8 @@ import test_oracle_pins as pins
 PINS = [pins.pin_philox_numpy, pins.pin_tv_init, pins.pin_jacobi_dense_power,
         pins.pin_mcgs_proper_coloring_is_gauss_seidel, pins.pin_mcgs_snapshot_matrix_form,
         pins.pin_target, pins.pin_ls_lstsq, pins.pin_ls_brute_force, pins.pin_ls_invariants,
-        pins.pin_ls_exact_cases, pins.pin_degree_one_rows, pins.pin_threshold,
+        pins.pin_ls_exact_cases, pins.pin_integer_weights_repeat_vectors,
+        pins.pin_degree_one_rows, pins.pin_threshold,
         pins.pin_strength_csr, adj.pin_adjoint_fd, adj.pin_adjoint_homogeneity,
         adj.pin_adjoint_special_cases, graph.pin_distance_graph_matrix_power,
         graph.pin_edge_ls_graph, interp.pin_interp_brute_force, interp.pin_interp_single_point,
@@ -107,6 +108,12 @@ MUTANTS = [
     ("cr_not_restarted", "u[i] = coarse[i] ? 0.0 : 1.0;", "u[i] = coarse[i] ? 0.0 : (stage ? u[i] : 1.0);", 0),
     ("adj_weights_dropped", "Xbar[j * K + kappa] += -lsb[p] * 2.0 * w[kappa] * a[p] * e;",
      "Xbar[j * K + kappa] += -lsb[p] * 2.0 * a[p] * e;", 0),
+    ("ls_syx_unweighted", "syx += w[kappa] * y[kappa] * x[kappa];",
+     "syx += y[kappa] * x[kappa];", 0),
+    ("ls_sxx_unweighted", "sxx += w[kappa] * x[kappa] * x[kappa];",
+     "sxx += x[kappa] * x[kappa];", 0),
+    ("graph_syx_unweighted", "syx += w[kappa] * y[kappa] * x[kappa];",
+     "syx += y[kappa] * x[kappa];", 1),
 ]
 
 

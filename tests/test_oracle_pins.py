@@ -331,6 +331,39 @@ def test_degree_one_rows(orc):
     pin_degree_one_rows(orc)
 
 
+def pin_integer_weights_repeat_vectors(orc):
+    """An integer weight w_k counts test vector k w_k times (the weighted
+    functional of §4.1 is the plain one over a block in which column k is
+    repeated w_k times): fits with weights (1, 3, 2, ...) equal unweighted fits
+    over the expanded block, for both targets, and so do the flags."""
+    rp, col, val, X = small_problem(17, n=30, K=6)
+    w = np.array([1.0, 3.0, 2.0, 1.0, 4.0, 2.0])
+    rep = np.repeat(np.arange(6), w.astype(int))
+    Xr = X[:, rep]
+    for mode in (oracle.TARGET_RESIDUAL, oracle.TARGET_PLAIN):
+        Y = orc.target(rp, col, val, X, mode)
+        a_w, ls_w = orc.edge_ls(rp, col, val, X, Y, w, mode)
+        Yr = orc.target(rp, col, val, Xr, mode)
+        np.testing.assert_array_equal(Yr, Y[:, rep])        # the target is per column
+        a_r, ls_r = orc.edge_ls(rp, col, val, Xr, Yr, None, mode)
+        rows, cols = _edges(rp, col)
+        off = rows != cols
+        syy = (w * Y[rows] ** 2).sum(1)
+        assert np.all(np.abs(a_w[off] - a_r[off]) <= 1e-12 * np.maximum(1.0, np.abs(a_r[off])))
+        assert np.all(np.abs(ls_w[off] - ls_r[off]) <= 1e-12 * syy[off])
+        f_w, _ = orc.threshold(rp, col, ls_w, 0.5)
+        f_r, _ = orc.threshold(rp, col, ls_r, 0.5)
+        m = np.array([ls_r[off][rows[off] == i].min() if (rows[off] == i).any() else 0.0
+                      for i in range(len(rp) - 1)])
+        rho = np.where(ls_r[off] > 0, m[rows[off]] / np.where(ls_r[off] > 0, ls_r[off], 1), 1.0)
+        clear = np.abs(rho - 0.5) > 1e-9
+        np.testing.assert_array_equal(f_w[off][clear], f_r[off][clear])
+
+
+def test_integer_weights_repeat_vectors(orc):
+    pin_integer_weights_repeat_vectors(orc)
+
+
 def test_K1_fits_are_exact(orc):
     """k = 1 < caliber: every one-point fit reproduces the target (Remark in
     §3.1: uniqueness needs k >= c); LS is zero up to rounding."""
