@@ -1,0 +1,56 @@
+"""The roofline numerator of bench.py on CPU: the algorithmic bytes of one
+relaxation launch, derived here from the per-launch formula of the kernel
+table (one color phase: the phase's share of A's CSR, the rows it writes and
+the vector block it reads), for the 1024 x 1024 rotated-anisotropy 9-point
+workload of the default bench line, plus the invariants of the whole-step
+count."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def c2():
+    mats, color = bench.make_matrix("c2")
+    rp, col, _ = mats[0]
+    n, nnz = len(rp) - 1, len(col)
+    return n, nnz, nnz - n, int(color.max()) + 1
+
+
+def test_c2_sizes(c2):
+    n, nnz, E, ncolors = c2
+    # 9-point stencil on 1024^2, neighbours outside the grid dropped: each of
+    # the 4 * 1024 boundary rows loses 3 entries, the 4 corners one fewer
+    assert n == 1024 * 1024 and nnz == 9 * n - 3 * 4 * 1024 + 4 and E == nnz - n
+    assert (n, nnz, E, ncolors) == (1_048_576, 9_424_900, 8_376_324, 2)
+
+
+def test_relax_launch_bytes_c2_bf16(c2):
+    n, nnz, E, C = c2
+    K, s_x, s_a = 16, 2, 4
+    # one color phase: 1/C of the CSR (column int32 + value), the row starts,
+    # its rows written once and the whole vector block read once
+    per_launch = (nnz * (4 + s_a) + 4 * (n + 1)) / C + (C + 1) / C * n * K * s_x
+    ab = bench.algorithmic_bytes(n, nnz, E, 0, K, 8, C, "bf16", True)
+    assert ab["relax_per_launch"] == per_launch == 90_128_402.0
+
+
+def test_step_bytes_invariants(c2):
+    n, nnz, E, C = c2
+    E_s = E // 2
+    by = {p: bench.algorithmic_bytes(n, nnz, E, E_s, 16, 8, C, p, True)
+          for p in ("bf16", "fp32", "fp64")}
+    assert by["bf16"]["total"] < by["fp32"]["total"] < by["fp64"]["total"]
+    for p, ab in by.items():
+        assert ab["relax"] == 8 * ab["sweep"] == 8 * C * ab["relax_per_launch"]
+        assert ab["total"] == ab["init"] + ab["relax"] + ab["edge"] + ab["strength"]
+        ab16 = bench.algorithmic_bytes(n, nnz, E, E_s, 16, 16, C, p, True)
+        assert ab16["relax"] == 2 * ab["relax"]                    # linear in the sweeps
+    # the fit pattern of depth d > 1 only adds to the edge pass
+    d2 = bench.algorithmic_bytes(n, nnz, E, E_s, 16, 8, C, "bf16", True, nnz_p=3 * nnz)
+    assert d2["relax"] == by["bf16"]["relax"] and d2["edge"] > by["bf16"]["edge"]
