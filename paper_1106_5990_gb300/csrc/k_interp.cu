@@ -26,6 +26,7 @@
 // threads), the rest one warp per row (lanes over Gram entries and subsets).
 #include <math.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "amgd_internal.cuh"
@@ -645,6 +646,25 @@ __global__ void k_interp_fill(const int64_t *__restrict__ row_ptr, const int32_t
     }
 }
 
+// A dynamic shared-memory opt-in is an attribute of a kernel in one
+// device's context, so it is made once per device (a second GPU driven by the
+// same process gets its own).  Two host threads making the first call at once
+// both set the same value, which is harmless.
+constexpr int kOptDevices = 64;
+
+template <class F>
+cudaError_t opt_in_smem(F *kernel, std::atomic<bool> (&done)[kOptDevices], int bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool tracked = dev >= 0 && dev < kOptDevices;
+    if (tracked && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && tracked) done[dev].store(true, std::memory_order_release);
+    return e;
+}
+
 template <class TS, bool UNIT_W>
 cudaError_t launch_rows_kernel(const InterpArgs &a, cudaStream_t s)
 {
@@ -652,13 +672,9 @@ cudaError_t launch_rows_kernel(const InterpArgs &a, cudaStream_t s)
     constexpr int MT = kInterpRowCand;
     const size_t smem = (size_t)T * (8 * (a.K + MT * MT + 2 * MT) + 4 * MT);
     constexpr size_t smem_max = (size_t)T * (8 * (kMaxK + MT * MT + 2 * MT) + 4 * MT);
-    static bool opted = false;
-    if (!opted) {
-        cudaError_t e = cudaFuncSetAttribute(k_ls_interp_rows<TS, UNIT_W>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-        if (e != cudaSuccess) return e;
-        opted = true;
-    }
+    static std::atomic<bool> opted[kOptDevices] = {};
+    const cudaError_t e = opt_in_smem(k_ls_interp_rows<TS, UNIT_W>, opted, (int)smem_max);
+    if (e != cudaSuccess) return e;
     const int64_t want = ((int64_t)a.n + T - 1) / T;
     const unsigned grid = (unsigned)(want < 152 * 4 ? want : 152 * 4);
     k_ls_interp_rows<TS, UNIT_W><<<grid, T, smem, s>>>(a);
@@ -668,14 +684,10 @@ cudaError_t launch_rows_kernel(const InterpArgs &a, cudaStream_t s)
 template <class TS, bool UNIT_W>
 cudaError_t launch_warp_kernel(const InterpArgs &a, cudaStream_t s)
 {
-    static bool opted = false;
-    if (!opted) {
-        const cudaError_t e = cudaFuncSetAttribute(k_ls_interp<TS, UNIT_W>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   kWarps * warp_interp_bytes<TS>(kMaxK));
-        if (e != cudaSuccess) return e;
-        opted = true;
-    }
+    static std::atomic<bool> opted[kOptDevices] = {};
+    const cudaError_t e = opt_in_smem(k_ls_interp<TS, UNIT_W>, opted,
+                                      kWarps * warp_interp_bytes<TS>(kMaxK));
+    if (e != cudaSuccess) return e;
     const int64_t want = ((int64_t)a.n + kWarps - 1) / kWarps;
     const unsigned grid = (unsigned)(want < 152 * 8 ? want : 152 * 8);
     k_ls_interp<TS, UNIT_W><<<grid, kWarps * 32, kWarps * warp_interp_bytes<TS>(a.K), s>>>(a);
