@@ -172,6 +172,29 @@ def pin_cr_spectral_limit(orc):
     assert abs(rho[0] - want) <= 1e-2 * want, (rho[0], want)
 
 
+def pin_cr_red_black_closed_form(orc):
+    """C = the red points of a red-black ordering leaves F without F-F
+    couplings on the 1D and 2D five-point Laplacians (A_ff is diagonal), so
+    one F-relaxation sweep multiplies u by exactly (1 - omega): rho_f =
+    |1 - omega| for Jacobi and Gauss-Seidel alike (Eq. (3.5) for a diagonal
+    E_f), and with delta above it no set is added."""
+    N = 8
+    rp2, col2, val2 = inputs.poisson2d_5pt(N)
+    red2 = (inputs.red_black(N) == 0).astype(np.uint8)
+    rp1, col1, val1 = inputs.lap1d(17)
+    red1 = (np.arange(17) % 2 == 0).astype(np.uint8)
+    for rp, col, val, C0 in ((rp1, col1, val1, red1), (rp2, col2, val2, red2)):
+        ls = np.ones(len(col))
+        color = C0.astype(np.int32)           # a proper 2-coloring of these graphs
+        for omega in (0.5, 0.8, 1.25):
+            for sweep in (oracle.SWEEP_JACOBI, oracle.SWEEP_MCGS):
+                C, rho = orc.cr_coarsen(rp, col, val, rp, col, ls, 0.5, 3, omega, sweep,
+                                        color if sweep == oracle.SWEEP_MCGS else None,
+                                        abs(1 - omega) + 1e-9, 0.5, 5, 0, C0)
+                assert len(rho) == 1 and abs(rho[0] - abs(1 - omega)) <= 1e-14, (omega, sweep)
+                assert np.array_equal(C, C0)
+
+
 def pin_cr_special_cases(orc):
     N = 6
     rp, col, val = inputs.poisson2d_5pt(N)
@@ -203,6 +226,10 @@ def test_cr_stage_brute_force(orc):
 
 def test_cr_spectral_limit(orc):
     pin_cr_spectral_limit(orc)
+
+
+def test_cr_red_black_closed_form(orc):
+    pin_cr_red_black_closed_form(orc)
 
 
 def test_cr_special_cases(orc):

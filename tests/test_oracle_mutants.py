@@ -26,7 +26,7 @@ PINS = [pins.pin_philox_numpy, pins.pin_tv_init, pins.pin_jacobi_dense_power,
         adj.pin_adjoint_special_cases, graph.pin_distance_graph_matrix_power,
         graph.pin_edge_ls_graph, interp.pin_interp_brute_force, interp.pin_interp_single_point,
         interp.pin_interp_monotone_and_exact, cr.pin_cr_stage_brute_force,
-        cr.pin_cr_spectral_limit, cr.pin_cr_special_cases]
+        cr.pin_cr_spectral_limit, cr.pin_cr_red_black_closed_form, cr.pin_cr_special_cases]
 
 # (name, text to find, replacement, occurrence index)
 MUTANTS = [
