@@ -40,8 +40,15 @@
  *
  * Parity pins (see tests/): Philox against numpy's Philox4x64-10; sweeps
  * against dense matrix powers and a triangular solve; LS against a library
- * least-squares solve and brute-force minimisation; the 7-point stencil
- * generator against the worked stencil S_A of §5.1.
+ * least-squares solve, brute-force minimisation, its normal equation and
+ * closed forms (exact fits, scaling, integer weights as repeated vectors);
+ * the reverse pass against central finite differences; G_d against 0/1
+ * matrix powers; interpolation against brute force over all subsets; CR
+ * stages against dense powers, numpy's Philox and parallel local-maximum
+ * rounds, its estimate against the spectral radius and the closed form
+ * |1 - omega| of a red-black split; the stencil generators against the
+ * worked stencils S_A and S~_xy of §5.1.  Every function has a pin; planted
+ * mistakes in a copy of this file must each fail one (test_oracle_mutants).
  */
 #include <math.h>
 #include <stdint.h>
