@@ -78,6 +78,37 @@ def test_create_rejects_bad_input_on_host(L, case, code):
     assert amgd.amgd_last_error(None)
 
 
+def _create_batch(mats, K=4):
+    nm = len(mats)
+    rps = [np.ascontiguousarray(m[0], np.int64) for m in mats]
+    cols = [np.ascontiguousarray(m[1], np.int32) for m in mats]
+    vals = [np.ascontiguousarray(m[2], np.float64) for m in mats]
+    arr = lambda xs: (ctypes.c_void_p * nm)(*[x.ctypes.data for x in xs])
+    ns = np.array([len(r) - 1 for r in rps], np.int64)
+    h = ctypes.c_void_p()
+    st = amgd.lib().amgd_create_batch(nm, arr(rps), arr(cols), arr(vals), ns.ctypes.data, K, 0,
+                                      amgd.AMGD_MEM_HOST, ctypes.byref(h))
+    return st, h
+
+
+def test_create_batch_rejects_a_bad_matrix_on_host(L):
+    """Every matrix of a batch is validated on the host before any device
+    work, and the message names the matrix and the row."""
+    good = inputs.lap1d(6)
+    rp, col, val = (x.copy() for x in inputs.lap1d(5))
+    col[2] = 9
+    st, h = _create_batch([good, (rp, col, val)])
+    assert st == amgd.AMGD_ERR_CSR and not h.value
+    assert "matrix 1" in amgd.amgd_last_error(None)
+    rp, col, val = (x.copy() for x in inputs.lap1d(5))
+    val[0] = 0.0
+    st, h = _create_batch([(rp, col, val), good])
+    assert st == amgd.AMGD_ERR_ZERO_DIAG and not h.value
+    assert "matrix 0" in amgd.amgd_last_error(None)
+    st, h = _create_batch([good, good], K=65)
+    assert st == amgd.AMGD_ERR_UNSUPPORTED and not h.value
+
+
 def test_null_arguments(L):
     assert L.amgd_create(None, None, None, 0, 4, 0, 0, None) == amgd.AMGD_ERR_ARG
     assert L.amgd_create_batch(0, None, None, None, None, 4, 0, 0, None) == amgd.AMGD_ERR_ARG
