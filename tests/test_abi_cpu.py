@@ -109,6 +109,34 @@ def test_create_batch_rejects_a_bad_matrix_on_host(L):
     assert st == amgd.AMGD_ERR_UNSUPPORTED and not h.value
 
 
+def test_create_rejects_sizes_beyond_the_abi_on_host(L):
+    """0 <= n < 2^31 and nnz < 2^31: the limits are checked before an array
+    is read past what the caller passed (row_ptr is read only after n is
+    accepted, col and val only after nnz = row_ptr[n] is)."""
+    h = ctypes.c_void_p()
+    rp = np.array([0, 1], np.int64)
+    col = np.zeros(1, np.int32)
+    val = np.ones(1)
+    args = lambda r, n: (r.ctypes.data, col.ctypes.data, val.ctypes.data, n, 4, 0,
+                         amgd.AMGD_MEM_HOST, ctypes.byref(h))
+    assert L.amgd_create(*args(rp, -1)) == amgd.AMGD_ERR_ARG
+    assert L.amgd_create(*args(rp, 1 << 31)) == amgd.AMGD_ERR_UNSUPPORTED
+    assert "2^31" in amgd.amgd_last_error(None)
+    big = np.array([0, 1 << 31], np.int64)                     # nnz = 2^31, col never read
+    assert L.amgd_create(*args(big, 1)) == amgd.AMGD_ERR_UNSUPPORTED
+    neg = np.array([0, -5], np.int64)
+    assert L.amgd_create(*args(neg, 1)) == amgd.AMGD_ERR_CSR
+    # a batch whose total row count reaches 2^31
+    nm = 2
+    ptrs = (ctypes.c_void_p * nm)(rp.ctypes.data, rp.ctypes.data)
+    cptrs = (ctypes.c_void_p * nm)(col.ctypes.data, col.ctypes.data)
+    vptrs = (ctypes.c_void_p * nm)(val.ctypes.data, val.ctypes.data)
+    ns = np.array([1 << 30, 1 << 30], np.int64)
+    assert L.amgd_create_batch(nm, ptrs, cptrs, vptrs, ns.ctypes.data, 4, 0, amgd.AMGD_MEM_HOST,
+                               ctypes.byref(h)) == amgd.AMGD_ERR_UNSUPPORTED
+    assert not h.value
+
+
 def test_null_arguments(L):
     assert L.amgd_create(None, None, None, 0, 4, 0, 0, None) == amgd.AMGD_ERR_ARG
     assert L.amgd_create_batch(0, None, None, None, None, 4, 0, 0, None) == amgd.AMGD_ERR_ARG
