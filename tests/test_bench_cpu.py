@@ -54,3 +54,23 @@ def test_step_bytes_invariants(c2):
     # the fit pattern of depth d > 1 only adds to the edge pass
     d2 = bench.algorithmic_bytes(n, nnz, E, E_s, 16, 8, C, "bf16", True, nnz_p=3 * nnz)
     assert d2["relax"] == by["bf16"]["relax"] and d2["edge"] > by["bf16"]["edge"]
+
+
+def test_depth2_pattern_of_c2_operator():
+    """The search-depth-2 workload fits over the graph of A^2: on the 9-point
+    grid operator that is the 5 x 5 block around each point (25 entries in the
+    interior), cut at the boundary; E_2 = 25,104,420 off-diagonals at 1024^2."""
+    import oracle
+    mats, _ = bench.make_matrix("c6")
+    rp, col, _ = mats[0]
+    n = len(rp) - 1
+    prp, pcol = oracle.distance_graph(rp, col, 2)
+    N = 1024
+    # rows lose 2 (boundary line) or 1 (next line) of the 5 offsets per direction
+    per_axis = [5] * N
+    per_axis[0] = per_axis[-1] = 3
+    per_axis[1] = per_axis[-2] = 4
+    s = sum(per_axis)
+    assert len(pcol) == s * s and len(pcol) - n == 25_104_420
+    i = 500 * N + 500
+    assert prp[i + 1] - prp[i] == 25
