@@ -7,9 +7,12 @@ The metric is edges/s = E (stored off-diagonals) / step time.
 
 Default workload (rotated anisotropic diffusion, 9-point stencil on a
 1024 x 1024 grid, eps = 1e-3, alpha = pi/6; K = 16 vectors, nu = 8
-red-black Gauss-Seidel sweeps, theta = 0.5): the mixed path (BF16 vector
-storage, FP32 arithmetic) is the headline, the FP64 path is measured beside
-it on the same matrix.
+red-black Gauss-Seidel sweeps, theta = 0.5): the headline is the mixed path
+that meets the accuracy contract against the FP64 oracle (FP32 vector
+storage, FP32 arithmetic: distances within 1e-3, strength set identical
+outside +-1e-2 of theta); the FP64 path and the BF16-storage path (faster,
+but outside the distance bar end to end) are measured beside it on the same
+matrix, each with its own accuracy against the oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config c1..c7]
                   [--precision bf16|fp32|fp64] [--impl ours|reference]
@@ -52,7 +55,7 @@ WORKLOADS = {
                precision="fp64"),
     "c2": dict(name="rotated anisotropic diffusion 9-point, 1024x1024 grid, eps=1e-3, "
                     "alpha=pi/6; K=16, nu=8 red-black Gauss-Seidel, theta=0.5",
-               K=16, seed=1, nu=8, omega=1.0, sweep="mcgs", theta=0.5, precision="bf16"),
+               K=16, seed=1, nu=8, omega=1.0, sweep="mcgs", theta=0.5, precision="fp32"),
     "c3": dict(name="3D jump-coefficient diffusion 7-point, 128^3 cells, lognormal(0,2) "
                     "coefficients, harmonic faces; K=32, nu=6 Jacobi omega=0.8",
                K=32, seed=3, nu=6, omega=0.8, sweep="jacobi", theta=0.5, precision="fp32"),
@@ -404,11 +407,14 @@ def accuracy_vs_oracle(h, mat, ref, theta):
         rho = np.where(want[off] > 0, m[rows[off]] / want[off], 1.0)
     diff = flag[off] != (ref["flag"][off] == 1)
     band = np.abs(rho - theta) <= 1e-2
+    outside = int((diff & ~band).sum())
     return {"against": "FP64 oracle build of the same matrix, seed and sweeps",
             "ls_rel_err": {"median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99)),
                            "max": float(rel.max())},
             "edges": int(off.sum()), "strength_flips": int(diff.sum()),
-            "flips_outside_band_1e-2": int((diff & ~band).sum())}
+            "flips_outside_band_1e-2": outside,
+            "bars": "LS relative error <= 1e-3, no strength flip outside +-1e-2 of theta",
+            "meets_accuracy": bool(rel.max() <= 1e-3 and outside == 0)}
 
 
 def cpu_oracle_time(cfg, w, sample_s=20.0, keep=None):
@@ -884,9 +890,14 @@ def main():
                        "graph": "one CUDA graph per step",
                        "shapes": {"relax": list(r["shapes"][0]), "edge": list(r["shapes"][1]),
                                   "legend": "(lanes per row G, 16-byte vectors per lane NV, "
-                                            "nonzeros per gather batch U, TMA-staged CSR), "
+                                            "nonzeros per gather batch U, kernel: relaxation 0 "
+                                            "direct / 1 TMA-staged CSR / 2 cp.async pipelined / "
+                                            "3 chunked per SM; distances 0 rows / 1 tiles), "
                                             "autotuned"}},
             "phase_ms": phases,
+            "timed_region": ("start vectors (Philox) + nu recorded sweeps + distances + reverse "
+                             "pass" if adj else "start vectors (Philox) + nu sweeps + distances, "
+                             "threshold + strength CSR, one CUDA graph per step"),
             "whole_step_gbs": whole, "whole_step_hbm_frac": whole / peak,
             "roofline": roofline}
     if args.scale:
@@ -926,26 +937,27 @@ def main():
                         "mixed_over_fp64": value / v64}
         r64["h"].close()
 
-    # FP32 storage beside a BF16 headline: the mixed configuration whose end-to-end
-    # distances stay within 1e-3 of the FP64 oracle (BF16 storage alone moves them by
-    # about 2e-3); its accuracy is taken against the same oracle build below
-    r32 = None
-    if not args.no_side and precision == "bf16":
+    # the other mixed storage beside the headline (BF16 beside FP32 and the other way
+    # round), timed on the same matrix; its accuracy is taken against the same oracle
+    # build below
+    other = {"fp32": "bf16", "bf16": "fp32"}.get(precision)
+    r_o = None
+    if not args.no_side and other is not None and not adj:
         side_steps = max(3, min(args.steps, 100))
-        r32 = run_gpu_arm(mats, color, w, "fp32", side_steps, 3, rank, flush, want_clocks=False,
+        r_o = run_gpu_arm(mats, color, w, other, side_steps, 3, rank, flush, want_clocks=False,
                           tune_cache=args.tune_cache)
-        v32, t32 = whole_job(float(r32["step_ms"].sum()), E, side_steps)
-        ab32 = step_bytes(r32, "fp32")
-        rl32 = r32["phase_ms"][1] / launches_relax
-        a32 = ab32["relax_per_launch"] / (rl32 * 1e-3) / 1e9
-        line["fp32"] = {"value": v32, "unit": "edges/s", "ms_per_step": t32,
-                        "steps": side_steps, "shapes": {"relax": list(r32["shapes"][0]),
-                                                        "edge": list(r32["shapes"][1])},
-                        "phase_ms": dict(zip(names, r32["phase_ms"].tolist())),
-                        "relax_launch_us": rl32 * 1e3, "relax_hbm_gbs": a32,
-                        "relax_hbm_frac": a32 / peak}
+        v_o, t_o = whole_job(float(r_o["step_ms"].sum()), E, side_steps)
+        ab_o = step_bytes(r_o, other)
+        rl_o = r_o["phase_ms"][1] / launches_relax
+        a_o = ab_o["relax_per_launch"] / (rl_o * 1e-3) / 1e9
+        line[other] = {"value": v_o, "unit": "edges/s", "ms_per_step": t_o,
+                       "steps": side_steps, "shapes": {"relax": list(r_o["shapes"][0]),
+                                                       "edge": list(r_o["shapes"][1])},
+                       "phase_ms": dict(zip(names, r_o["phase_ms"].tolist())),
+                       "relax_launch_us": rl_o * 1e3, "relax_hbm_gbs": a_o,
+                       "relax_hbm_frac": a_o / peak}
         if "fp64" in line:
-            line["fp32"]["over_fp64"] = v32 / line["fp64"]["value"]
+            line[other]["over_fp64"] = v_o / line["fp64"]["value"]
 
     e2e_steps = max(3, min(args.steps, 50))
     e = run_e2e(r["h"], mats, w, r["sweep"], e2e_steps, adjoint=adj)
@@ -964,10 +976,11 @@ def main():
         line["cpu_baseline"] = cpu_oracle_time(cfg, w, keep=ref)
         if ref and not args.scale:
             line["accuracy"] = accuracy_vs_oracle(r["h"], mats[0], ref, w["theta"])
-            if r32 is not None:
-                line["fp32"]["accuracy"] = accuracy_vs_oracle(r32["h"], mats[0], ref, w["theta"])
-    if r32 is not None:
-        r32["h"].close()
+            if r_o is not None:
+                line[other]["accuracy"] = accuracy_vs_oracle(r_o["h"], mats[0], ref, w["theta"])
+                line[other]["meets_accuracy"] = line[other]["accuracy"]["meets_accuracy"]
+    if r_o is not None:
+        r_o["h"].close()
     r["h"].close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -280,7 +280,9 @@ int amgd_graph_launch(amgd_handle h);
  *   use (waits bounded to about one second; a wait that runs out makes the
  *   next synchronising call return AMGD_ERR_TIMEOUT); 2 warp-pipelined, CSR
  *   slices and neighbour rows copied with cp.async two and one row groups
- *   ahead (U must be 4).  For the distance pass, staged selects 0 the row
+ *   ahead (U must be 4); 3 persistent with L2 prefetch, each warp asking
+ *   the L2 for the row pointers and CSR lines of its rows one and two tiles
+ *   ahead.  For the distance pass, staged selects 0 the row
  *   kernel (G lanes per row) or 1 the tile kernel (one thread per stored
  *   entry).  Shapes change speed only, never results beyond the order of
  *   the K-term LS sums.  kernel: AMGD_KERNEL_RELAX (the sweeps) or
@@ -463,10 +465,12 @@ int amgd_graph_capture_backward(amgd_handle h, uint64_t seed, int32_t nu, double
  *   n >= 0 and theta >= 0 (else ARG).  stream: a cudaStream_t (NULL =
  *   legacy default stream); the call only enqueues work.
  *
- *   Working memory: a file-scope device array of 65536 int32 (256 KiB, one
- *   entry per tile of 4096 rows) that every GPU loading the library keeps
- *   until the process exits.  Hence n <= 268,435,456; larger n is rejected
- *   with AMGD_ERR_UNSUPPORTED before any GPU work.  The first call on a
+ *   Working memory: a file-scope device array of 65536 int64 (512 KiB, one
+ *   entry per tile of 4096 rows: the 64-bit offset of the tile's first kept
+ *   edge, so strength graphs with 2^31 or more edges are counted exactly)
+ *   that every GPU loading the library keeps until the process exits.  Hence
+ *   n <= 268,435,456; larger n is rejected with AMGD_ERR_UNSUPPORTED before
+ *   any GPU work.  The first call on a
  *   device looks up the array's device address with that device current
  *   (make this first call before any stream capture).  Every call reuses the
  *   same array; calls whose GPU work overlaps (other streams, other threads

@@ -164,7 +164,7 @@ bool shape_ok(int st, int K, Shape sh)
     if (sh.NV != 1 && sh.NV != 2 && sh.NV != 4) return false;
     if (sh.U != 2 && sh.U != 4 && sh.U != 8) return false;     // U = 2: edge pass only
     if (sh.G < 1 || sh.G > 32 || (sh.G & (sh.G - 1))) return false;
-    if (sh.stage < 0 || sh.stage > 2) return false;
+    if (sh.stage < 0 || sh.stage > 3) return false;
     return sh.G * sh.NV == P;
 }
 
@@ -357,6 +357,7 @@ int run_relax(amgd_ctx *h, int32_t nu, double omega, int sweep, cudaStream_t s)
     a.diag = h->storage == ST_FP64 ? (const void *)h->diag64 : (const void *)h->diag32;
     a.Kp = Kp_of(h->storage, h->K);
     a.omega = omega;
+    a.avg_nnz = h->n ? (float)((double)h->nnz / (double)h->n) : 0.f;
     for (int32_t it = 0; it < nu; ++it) {
         a.xold = h->x[h->cur];
         a.xnew = h->x[1 - h->cur];
@@ -406,6 +407,7 @@ int jacobi_step(amgd_ctx *h, const void *src, void *dst, double omega, cudaStrea
     a.diag = h->storage == ST_FP64 ? (const void *)h->diag64 : (const void *)h->diag32;
     a.Kp = Kp_of(h->storage, h->K);
     a.omega = omega;
+    a.avg_nnz = h->n ? (float)((double)h->nnz / (double)h->n) : 0.f;
     a.xold = src;
     a.xnew = dst;
     a.r0 = 0;
@@ -1301,7 +1303,7 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
     }
     std::vector<Shape> cands;
     const int P = P_of(h->storage, h->K);
-    for (int stage : {0, 1, 2})
+    for (int stage : {0, 1, 2, 3})
         for (int NV : {1, 2, 4})
             for (int U : {4, 8})
                 if (P % NV == 0 && shape_ok(h->storage, h->K, Shape{P / NV, NV, U, stage}) &&

@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 namespace amgd {
@@ -124,9 +125,27 @@ __device__ __forceinline__ uint4 ldg16(const void *p)
 // gathered per batch.  P is fixed by (storage, K); G, NV and U are free.
 struct Shape {
     int G, NV, U;
-    int stage = 0;   // relaxation: 0 direct, 1 TMA-staged CSR, 2 cp.async pipelined;
+    int stage = 0;   // relaxation: 0 direct, 1 TMA-staged CSR, 2 cp.async pipelined,
+                     // 3 persistent with L2 prefetch of the CSR ahead of use;
                      // edge pass: 0 row kernel, 1 tile kernel
 };
+
+// per-device record of a one-time host setting of a kernel (a shared-memory
+// opt-in, a resident-grid size): value 0 means "not yet known".  Host threads
+// that race on an entry compute and store the same value.
+constexpr int kMaxDevices = 64;
+struct PerDevice {
+    std::atomic<int> v[kMaxDevices] = {};
+    int get(int dev) const { return dev >= 0 ? v[dev].load(std::memory_order_relaxed) : 0; }
+    void set(int dev, int x) { if (dev >= 0) v[dev].store(x, std::memory_order_relaxed); }
+};
+// the current device, or -1 if it cannot be used with a PerDevice table
+inline int current_device_index()
+{
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return -1;
+    return d;
+}
 
 // device status bits set by bounded waits that gave up
 constexpr uint32_t kStatusStagingTimeout = 1u;
@@ -148,6 +167,7 @@ struct RelaxArgs {
     int32_t split;        // rows < split take new values (earlier colors)
     int32_t Kp;           // padded row stride (elements)
     double omega;
+    float avg_nnz = 0.f;  // stored entries per row of the whole matrix
 };
 
 struct EdgeArgs {                // everything in the caller's numbering

@@ -10,10 +10,11 @@
 // point instead: the caller passes every input and output buffer, and the only
 // working memory is the file-scope array below.
 //
-// The scratch array holds one int32 per tile of kNaTileRows rows (the
-// exclusive offsets of the tiles' strong-edge counts).  It lives in the
+// The scratch array holds one int64 per tile of kNaTileRows rows (the
+// exclusive offsets of the tiles' strong-edge counts; 64-bit, so a strength
+// graph with 2^31 or more edges is counted exactly).  It lives in the
 // library's device image, so every GPU that loads the library holds its
-// 256 KiB until the process exits.  All calls share it: each call overwrites
+// 512 KiB until the process exits.  All calls share it: each call overwrites
 // the entries of its own tiles before reading them (nothing has to start at
 // zero), and two calls whose work overlaps on the GPU (different streams, or
 // different host threads on the same device) race on it.
@@ -29,13 +30,13 @@
 namespace {
 
 constexpr int kNaTileRows = 4096;
-constexpr int kNaMaxTiles = 65536;            // 256 KiB of scratch
+constexpr int kNaMaxTiles = 65536;            // 512 KiB of scratch
 constexpr int64_t kNaMaxRows = (int64_t)kNaTileRows * kNaMaxTiles;
 constexpr int kNaThreads = 512;
 constexpr int kNaWarps = kNaThreads / 32;
 constexpr int kNaMaxDevices = 64;
 
-static __device__ __align__(256) int32_t g_na_tile_scratch[kNaMaxTiles];
+static __device__ __align__(256) int64_t g_na_tile_scratch[kNaMaxTiles];
 
 // min_k LS_ik over the off-diagonal slots of row i, and the number of strong
 // slots (LS = 0 or theta LS < min), evaluated by one warp
@@ -61,13 +62,13 @@ __device__ __forceinline__ void na_row(const int64_t *rp, const int32_t *col, co
 // pass 1: strong count of every tile into the scratch array
 __global__ void __launch_bounds__(kNaThreads)
 k_na_tile_counts(const int64_t *rp, const int32_t *col, const double *ls, int64_t n,
-                 double theta, int32_t *tile)
+                 double theta, int64_t *tile)
 {
-    __shared__ int warp_tot[kNaWarps];
+    __shared__ long long warp_tot[kNaWarps];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t r0 = (int64_t)blockIdx.x * kNaTileRows;
     const int64_t r1 = min(n, r0 + kNaTileRows);
-    int tot = 0;
+    long long tot = 0;
     for (int64_t i = r0 + warp; i < r1; i += kNaWarps) {
         double m;
         int c;
@@ -77,30 +78,30 @@ k_na_tile_counts(const int64_t *rp, const int32_t *col, const double *ls, int64_
     if (lane == 0) warp_tot[warp] = tot;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int s = 0;
+        long long s = 0;
         for (int w = 0; w < kNaWarps; ++w) s += warp_tot[w];
         tile[blockIdx.x] = s;
     }
 }
 
-// pass 2: exclusive scan of the tile counts, one block
-__global__ void __launch_bounds__(1024) k_na_tile_scan(int32_t *tile, int ntiles)
+// pass 2: exclusive scan of the tile counts, one block (64-bit sums and carry)
+__global__ void __launch_bounds__(1024) k_na_tile_scan(int64_t *tile, int ntiles)
 {
-    __shared__ int part[1024];
-    int carry = 0;
+    __shared__ long long part[1024];
+    long long carry = 0;
     for (int base = 0; base < ntiles; base += 1024) {
         const int k = base + threadIdx.x;
-        const int v = k < ntiles ? tile[k] : 0;
+        const long long v = k < ntiles ? tile[k] : 0;
         part[threadIdx.x] = v;
         __syncthreads();
         for (int o = 1; o < 1024; o <<= 1) {
-            const int t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+            const long long t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
             __syncthreads();
             part[threadIdx.x] += t;
             __syncthreads();
         }
         if (k < ntiles) tile[k] = carry + part[threadIdx.x] - v;
-        const int total = part[1023];
+        const long long total = part[1023];
         __syncthreads();
         carry += total;
     }
@@ -109,11 +110,11 @@ __global__ void __launch_bounds__(1024) k_na_tile_scan(int32_t *tile, int ntiles
 // pass 3: row pointers and kept columns of every tile
 __global__ void __launch_bounds__(kNaThreads)
 k_na_compact(const int64_t *rp, const int32_t *col, const double *ls, int64_t n, double theta,
-             const int32_t *tile, int64_t *s_rp, int32_t *s_col, int64_t cap)
+             const int64_t *tile, int64_t *s_rp, int32_t *s_col, int64_t cap)
 {
-    __shared__ int warp_tot[kNaWarps];
-    __shared__ int warp_off[kNaWarps];
-    __shared__ int blk_tot;
+    __shared__ long long warp_tot[kNaWarps];
+    __shared__ long long warp_off[kNaWarps];
+    __shared__ long long blk_tot;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t r0 = (int64_t)blockIdx.x * kNaTileRows;
     const int64_t r1 = min(n, r0 + kNaTileRows);
@@ -121,7 +122,7 @@ k_na_compact(const int64_t *rp, const int32_t *col, const double *ls, int64_t n,
     const int64_t rows_per_warp = (kNaTileRows + kNaWarps - 1) / kNaWarps;
     const int64_t w0 = min(r1, r0 + warp * rows_per_warp);
     const int64_t w1 = min(r1, w0 + rows_per_warp);
-    int tot = 0;
+    long long tot = 0;
     for (int64_t i = w0; i < w1; ++i) {
         double m;
         int c;
@@ -131,7 +132,7 @@ k_na_compact(const int64_t *rp, const int32_t *col, const double *ls, int64_t n,
     if (lane == 0) warp_tot[warp] = tot;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int s = 0;
+        long long s = 0;
         for (int w = 0; w < kNaWarps; ++w) { warp_off[w] = s; s += warp_tot[w]; }
         blk_tot = s;
     }
@@ -157,7 +158,7 @@ k_na_compact(const int64_t *rp, const int32_t *col, const double *ls, int64_t n,
 }
 
 std::mutex g_na_mu;
-int32_t *g_na_ptr[kNaMaxDevices] = {};
+int64_t *g_na_ptr[kNaMaxDevices] = {};
 
 }  // namespace
 
@@ -188,7 +189,7 @@ extern "C" int amgd_strength_noalloc(const int64_t *row_ptr, const int32_t *col,
         amgd::set_thread_error("amgd_strength_noalloc: no usable current device");
         return AMGD_ERR_CUDA;
     }
-    int32_t *tile = nullptr;
+    int64_t *tile = nullptr;
     {
         // once per device, with that device current: the device address of
         // the scratch array (its host-side name is not a device address)

@@ -469,6 +469,186 @@ k_relax_pipe(RelaxArgs A, int64_t chunk)
     cp_async_wait<0>();
 }
 
+// Chunked persistent variant (stage 3).  One block of kChunkThreads threads
+// per SM owns one contiguous chunk of rows; its warps walk the chunk side by
+// side in groups of RW = 32/G rows (group g of the chunk goes to warp g mod W),
+// so the whole SM moves through consecutive rows together.  On matrices whose
+// neighbours are close in the row order (stencils on grid lines, banded and
+// mesh orderings) the rows an SM gathers are then the few grid lines around
+// its current position, and a line fetched into L1 for one row serves the
+// rows of the next lines too: the L2 -> L1 traffic of the gathers drops from
+// one copy of each vector row per block that touches it towards one per SM.
+// Each warp also asks the L2 for the row-pointer line of its group after next
+// and for the column-index and value lines of its next group (their bounds
+// come from the row pointers prefetched one group earlier), so a row's first
+// two dependent round trips hit L2.  L2 policy: the test-vector block (read
+// by the gathers, written by the update) is loaded and stored with an
+// evict-last hint and the CSR, which streams through once per sweep, with an
+// evict-first hint, so the vectors of the next color phase and sweep tend to
+// stay in the 129 MB L2 instead of being pushed out by the matrix.  Same row
+// sums in the same order as k_relax: same bits.
+constexpr int kChunkThreads = 1024;
+
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ldg16_hint(const void *p, uint64_t pol)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st16_hint(void *p, const uint4 &v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "r"(v.x),
+                 "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ int32_t ld32_hint(const int32_t *p, uint64_t pol)
+{
+    int32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ldv_hint(const float *p, uint64_t pol)
+{
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ldv_hint(const double *p, uint64_t pol)
+{
+    double v;
+    asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+template <class TS, int G, int NV, int U, bool SPLIT>
+__global__ void __launch_bounds__(kChunkThreads, 1) k_relax_chunk(RelaxArgs A, int32_t chunk)
+{
+    using S = Store<TS>;
+    using C = typename S::C;
+    using AV = typename S::A;
+    constexpr int V = S::V, RW = 32 / G, NW = kChunkThreads / 32;
+    constexpr int64_t STEP = (int64_t)NW * RW;            // rows between a warp's groups
+    const int warp = threadIdx.x / 32, lane32 = threadIdx.x % 32;
+    const int lane = lane32 % G, rig = lane32 / G;
+    const TS *xold = (const TS *)A.xold;
+    TS *xnew = (TS *)A.xnew;
+    const AV *val = (const AV *)A.val;
+    const int32_t *col = A.col;
+    const int Kp = A.Kp;
+    const int64_t c0 = (int64_t)A.r0 + (int64_t)blockIdx.x * chunk;
+    const int64_t c1 = min((int64_t)A.r1, c0 + chunk);
+    const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
+
+    for (int64_t wr0 = c0 + (int64_t)warp * RW; wr0 < c1; wr0 += STEP) {
+        // row pointers of this warp's group after next, into L2
+        if (lane32 == 0 && wr0 + 2 * STEP < c1) prefetch_l2(A.rp + wr0 + 2 * STEP);
+        // bounds of this warp's next group (its row pointers were prefetched)
+        int n0 = 0, n1 = 0;
+        if (wr0 + STEP < c1) {
+            n0 = ld32_hint(A.rp + wr0 + STEP, stream);
+            n1 = ld32_hint(A.rp + min(wr0 + STEP + RW, c1), stream);
+        }
+        const int64_t r = wr0 + rig;
+        if (r < c1) {
+            const int p0 = ld32_hint(A.rp + r, stream), p1 = ld32_hint(A.rp + r + 1, stream);
+            Acc<C, V> acc[NV];
+#pragma unroll
+            for (int tt = 0; tt < NV; ++tt) acc[tt].zero();
+            for (int pb = p0; pb < p1; pb += U) {
+                int jj[U];
+                C vv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const bool ok = pb + u < p1;
+                    jj[u] = ok ? ld32_hint(col + pb + u, stream) : -1;
+                    vv[u] = ok ? (C)ldv_hint(val + pb + u, stream) : C(0);
+                }
+                uint4 raw[U][NV];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (jj[u] >= 0) {
+                        const TS *src = (SPLIT && jj[u] < A.split ? (const TS *)xnew : xold) +
+                                        (int64_t)jj[u] * Kp;
+#pragma unroll
+                        for (int tt = 0; tt < NV; ++tt)
+                            raw[u][tt] = ldg16_hint(src + (tt * G + lane) * V, keep);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (jj[u] < 0) break;
+#pragma unroll
+                    for (int tt = 0; tt < NV; ++tt) {
+                        C x[V];
+                        S::unpack(raw[u][tt], x);
+                        acc[tt].fma_piece(vv[u], x);
+                    }
+                }
+            }
+            const C c = (C)A.omega / ldv_hint((const AV *)A.diag + r, stream);
+#pragma unroll
+            for (int tt = 0; tt < NV; ++tt) {
+                C xi[V], out[V];
+                S::unpack(ldg16_hint(xold + r * Kp + (tt * G + lane) * V, keep), xi);
+#pragma unroll
+                for (int e = 0; e < V; ++e) out[e] = fma(-c, acc[tt].get(e), xi[e]);
+                st16_hint(xnew + r * Kp + (tt * G + lane) * V, S::pack(out), keep);
+            }
+        }
+        // column-index and value lines of this warp's next group, into L2
+        if (n1 > n0) {
+            const int64_t q0 = n0 & ~31, nq = ((int64_t)n1 - q0 + 31) / 32;     // 128-byte lines
+            for (int64_t q = lane32; q < nq; q += 32) prefetch_l2(col + q0 + 32 * q);
+            constexpr int EPL = 128 / (int)sizeof(AV);                          // values per line
+            const int64_t v0 = n0 & ~(int64_t)(EPL - 1), nv = ((int64_t)n1 - v0 + EPL - 1) / EPL;
+            for (int64_t q = lane32; q < nv; q += 32) prefetch_l2(val + v0 + EPL * q);
+        }
+    }
+}
+
+template <class TS, int G, int NV, int U>
+cudaError_t go_chunk(const RelaxArgs &a, cudaStream_t s)
+{
+    const int64_t rows = (int64_t)a.r1 - a.r0;
+    if (rows <= 0) return cudaSuccess;
+    constexpr int RW = 32 / G;
+    auto kern = a.split > 0 ? k_relax_chunk<TS, G, NV, U, true> : k_relax_chunk<TS, G, NV, U, false>;
+    static PerDevice sm_count;
+    const int dev = current_device_index();
+    int sms = sm_count.get(dev);
+    if (sms == 0) {
+        int d = 0;
+        cudaGetDevice(&d);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+        if (sms <= 0) sms = 1;
+        sm_count.set(dev, sms);
+    }
+    // one chunk per SM, a whole number of warp groups each
+    int64_t chunk = (rows + sms - 1) / sms;
+    chunk = (chunk + RW - 1) / RW * RW;
+    const int64_t blocks = (rows + chunk - 1) / chunk;
+    kern<<<(unsigned)blocks, kChunkThreads, 0, s>>>(a, (int32_t)chunk);
+    return cudaGetLastError();
+}
+
 template <class TS, int G, int NV>
 cudaError_t go_pipe(const RelaxArgs &a, cudaStream_t s)
 {
@@ -480,18 +660,21 @@ cudaError_t go_pipe(const RelaxArgs &a, cudaStream_t s)
     const int64_t rows = (int64_t)a.r1 - a.r0;
     if (rows <= 0) return cudaSuccess;
     constexpr int smem = PipeLayout<TS, G, NV>::BYTES;
-    static int grid_cap = 0;
+    static PerDevice cache;                  // resident blocks on each device
+    const int dev = current_device_index();
+    int grid_cap = cache.get(dev);
     if (grid_cap == 0) {
         cudaError_t e = cudaFuncSetAttribute(k_relax_pipe<TS, G, NV>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int d = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&d);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_relax_pipe<TS, G, NV>,
                                                           kPipeWarps * 32, smem);
         if (e != cudaSuccess) return e;
         grid_cap = sms * (per_sm > 0 ? per_sm : 1);
+        cache.set(dev, grid_cap);
     }
     // contiguous chunks, a whole number of groups each, one per warp
     constexpr int RG = PipeLayout<TS, G, NV>::RG;
@@ -516,18 +699,21 @@ cudaError_t go_staged(const RelaxArgs &a, cudaStream_t s)
     const int64_t rows = (int64_t)a.r1 - a.r0;
     if (rows <= 0) return cudaSuccess;
     constexpr int smem = stage_smem_bytes<TS, G, NV>();
-    static int grid_cap = 0;                 // resident blocks on this device
+    static PerDevice cache;                  // resident blocks on each device
+    const int dev = current_device_index();
+    int grid_cap = cache.get(dev);
     if (grid_cap == 0) {
         cudaError_t e = cudaFuncSetAttribute(k_relax_staged<TS, G, NV, U>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int d = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&d);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_relax_staged<TS, G, NV, U>,
                                                           kRelaxThreads, smem);
         if (e != cudaSuccess) return e;
         grid_cap = sms * (per_sm > 0 ? per_sm : 1);
+        cache.set(dev, grid_cap);
     }
     const int64_t ntiles = (rows + kRelaxThreads / G - 1) / (kRelaxThreads / G);
     const unsigned grid = (unsigned)(ntiles < grid_cap ? ntiles : grid_cap);
@@ -568,6 +754,13 @@ cudaError_t go(const RelaxArgs &a, cudaStream_t s)
 template <class TS, int G, int NV>
 cudaError_t dispatch_u(int U, int stage, const RelaxArgs &a, cudaStream_t s)
 {
+    if (stage == 3) {
+        switch (U) {
+        case 4: return go_chunk<TS, G, NV, 4>(a, s);
+        case 8: return go_chunk<TS, G, NV, 8>(a, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (U) {
     case 4: return stage == 2 ? go_pipe<TS, G, NV>(a, s)
                  : stage ? go_staged<TS, G, NV, 4>(a, s) : go<TS, G, NV, 4>(a, s);
@@ -624,7 +817,7 @@ int pipe_smem(int G, int NV)
 bool relax_shape_available(int storage, Shape sh)
 {
     if (sh.U != 4 && sh.U != 8) return false;   // the sweeps gather 4 or 8 entries per batch
-    if (!sh.stage) return true;
+    if (!sh.stage || sh.stage == 3) return true;
     if (sh.stage == 2 && (sh.U != 4 || sh.G < 2)) return false;   // no batch size; RG <= 16
     int b = 0;
     switch (storage) {

@@ -11,8 +11,8 @@ only the mixed arithmetic differs:
   * cancellation (LS << S_yy): the FP64 fallback keeps LS accurate.
 End to end (same seed, every stage mixed): strength sets identical outside a
 +-1e-2 band around theta; FP32 storage keeps distances within 1e-3; BF16
-storage is reported by its error quantiles (its vector rounding alone moves
-distances by ~1e-3, see the design notes).
+storage is reported by its error quantiles (rounding the vectors to BF16
+alone moves distances by about 1e-3 end to end).
 """
 import math
 

@@ -142,6 +142,89 @@ def test_mcgs_sweeps_bit_exact(name, coloring, K):
             assert np.array_equal(h.get_vectors(), want)
 
 
+def arrow(n):
+    """1D Laplacian plus a dense first row and column (row 0 holds every
+    column): a row far longer than a gather batch or a tile's CSR lines, next to
+    rows of two or three entries.  Diagonally dominant."""
+    import scipy.sparse as sp
+    i = np.arange(n)
+    rows = np.concatenate([i[1:], i[:-1], np.zeros(n - 1, int), i[1:]])
+    cols = np.concatenate([i[:-1], i[1:], i[1:], np.zeros(n - 1, int)])
+    vals = -np.concatenate([np.ones(2 * (n - 1)), np.full(2 * (n - 1), 0.01)])
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A = A + sp.diags(np.asarray(abs(A).sum(1)).ravel() + 1.0)
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    return (A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data.astype(np.float64))
+
+
+TILE_CASES = {
+    "aniso9_40": (lambda: inputs.aniso2d_9pt(40, 1e-3, math.pi / 6), "redblack"),
+    "graph_2000": (lambda: inputs.graph_laplacian(2000, 8.0, 4), "greedy"),
+    "random_1500": (lambda: inputs.random_csr(1500, 6.0, 11), "greedy"),
+    "arrow_3001": (lambda: arrow(3001), "greedy"),
+}
+
+
+def _coloring(rp, col, kind):
+    n = len(rp) - 1
+    return (inputs.red_black(int(round(math.sqrt(n)))) if kind == "redblack"
+            else inputs.greedy_coloring(rp, col))
+
+
+@pytest.mark.parametrize("U", [4, 8])
+@pytest.mark.parametrize("NV", [1, 2])
+@pytest.mark.parametrize("case", list(TILE_CASES))
+@pytest.mark.parametrize("K", [5, 16, 64])
+def test_stage3_sweeps_bit_exact(case, NV, U, K):
+    """The persistent relaxation kernel with L2 prefetch (stage 3: each warp
+    prefetches the row pointers and CSR lines of its rows one and two tiles
+    ahead) equals the oracle bit for bit in FP64, Jacobi and multicolor
+    Gauss-Seidel, including a dense row far longer than a gather batch next
+    to short rows."""
+    make, kind = TILE_CASES[case]
+    rp, col, val = make()
+    n = len(rp) - 1
+    color = _coloring(rp, col, kind)
+    X0 = oracle.tv_init(n, K, 5)
+    P = 1
+    while 2 * P < K:
+        P *= 2
+    if P % NV:
+        pytest.skip("shape does not tile the row")
+    with amgd.Handle(rp, col, val, K, 5) as h:
+        h.set_kernel_shape(amgd.AMGD_KERNEL_RELAX, P // NV, NV, U, 3)
+        h.relax(3, 0.7, amgd.AMGD_SWEEP_JACOBI)
+        assert np.array_equal(h.get_vectors(), oracle.relax(rp, col, val, X0, 3, 0.7))
+    with amgd.Handle(rp, col, val, K, 5) as h:
+        h.set_coloring(color)
+        h.set_kernel_shape(amgd.AMGD_KERNEL_RELAX, P // NV, NV, U, 3)
+        h.relax(2, 1.1, amgd.AMGD_SWEEP_MCGS)
+        want = oracle.relax(rp, col, val, X0, 2, 1.1, oracle.SWEEP_MCGS, color)
+        assert np.array_equal(h.get_vectors(), want)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("case", list(TILE_CASES))
+def test_stage3_sweeps_mixed_equal_direct(prec, case):
+    """FP32 arithmetic on FP32/BF16 storage: the stage-3 kernel stores the
+    same bits as the direct kernel (same FMA chains in the same order)."""
+    make, kind = TILE_CASES[case]
+    rp, col, val = make()
+    color = _coloring(rp, col, kind)
+    K = 16
+    P = {"fp32": 4, "bf16": 2}[prec]
+    got = []
+    for shape in [(P, 1, 4, 0), (P, 1, 4, 3), (P // 2, 2, 8, 3)]:
+        with amgd.Handle(rp, col, val, K, 6) as h:
+            h.set_precision(prec)
+            h.set_coloring(color)
+            h.set_kernel_shape(amgd.AMGD_KERNEL_RELAX, *shape)
+            h.relax(3, 1.0, amgd.AMGD_SWEEP_MCGS)
+            got.append(h.get_vectors())
+    assert np.array_equal(got[0], got[1]) and np.array_equal(got[0], got[2])
+
+
 # --------------------------------------------------------------------------- full build
 @pytest.mark.parametrize("name", list(MATRICES))
 @pytest.mark.parametrize("K,target", [(8, 0), (16, 0), (16, 1), (5, 0), (33, 0)])
@@ -417,7 +500,7 @@ def _valid_shapes(prec, K):
     P = 1
     while P * V < K:
         P *= 2
-    return [(P // nv, nv, u, st) for st in (0, 1, 2) for nv in (1, 2, 4) for u in (4, 8)
+    return [(P // nv, nv, u, st) for st in (0, 1, 2, 3) for nv in (1, 2, 4) for u in (4, 8)
             if P % nv == 0 and not (st == 2 and u == 8)]
 
 

@@ -88,6 +88,58 @@ def test_noalloc_matches_existing_entry_point_twice(torch):
     assert np.array_equal(got_col[:ref_rp2[-1]], ref_col2[:ref_rp2[-1]])
 
 
+def test_noalloc_truncation_empty_and_side_stream(torch):
+    """cap below the number of kept edges: the first cap columns are written
+    and s_row_ptr still counts every kept edge; n = 0 writes s_row_ptr[0] = 0;
+    a call enqueued on a side stream gives the same result."""
+    N = 64
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
+    ls, ref_rp, ref_col, _ = _reference(torch, rp, col, val, 16, 3, 0.5, inputs.red_black(N))
+    E = int(ref_rp[-1])                                 # kept edges
+    cap = E // 3
+    out_rp = torch.full((len(rp),), -1, dtype=torch.int64, device="cuda")
+    out_col = torch.full((E,), -7, dtype=torch.int32, device="cuda")
+    got_rp, got_col = _noalloc(torch, rp, col, ls, 0.5, cap, out_rp, out_col)
+    assert np.array_equal(got_rp, ref_rp) and got_rp[-1] == E > cap
+    assert np.array_equal(got_col[:cap], ref_col[:cap])
+    assert np.all(got_col[cap:] == -7)                 # nothing written past cap
+
+    empty_rp = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    st = amgd.lib().amgd_strength_noalloc(empty_rp.data_ptr(), 0, 0, 0, 0.5,
+                                          empty_rp.data_ptr(), 0, 0, None)
+    assert st == amgd.AMGD_OK
+    torch.cuda.synchronize()
+    assert empty_rp.item() == 0
+
+    side = torch.cuda.Stream()
+    d_rp = torch.from_numpy(np.ascontiguousarray(rp, np.int64)).cuda()
+    d_col = torch.from_numpy(np.ascontiguousarray(col, np.int32)).cuda()
+    out_rp.fill_(-1)
+    out_col.fill_(-1)
+    torch.cuda.synchronize()
+    st = amgd.lib().amgd_strength_noalloc(d_rp.data_ptr(), d_col.data_ptr(), ls.data_ptr(),
+                                          len(rp) - 1, 0.5, out_rp.data_ptr(),
+                                          out_col.data_ptr(), E, side.cuda_stream)
+    assert st == amgd.AMGD_OK
+    side.synchronize()
+    assert np.array_equal(out_rp.cpu().numpy(), ref_rp)
+    assert np.array_equal(out_col.cpu().numpy(), ref_col[:E])
+
+
+def test_noalloc_more_than_1024_tiles(torch):
+    """4,206,649 rows (1,028 tiles of 4,096 rows): the scan of the tile
+    offsets crosses its 1,024-entry chunk and carries the 64-bit sum."""
+    n = 1024 * 4096 + 12345
+    rp, col, val = inputs.lap1d(n)
+    ls, ref_rp, ref_col, _ = _reference(torch, rp, col, val, 4, 9, 0.5)
+    E = int(ref_rp[-1])
+    out_rp = torch.full((n + 1,), -1, dtype=torch.int64, device="cuda")
+    out_col = torch.full((E,), -1, dtype=torch.int32, device="cuda")
+    got_rp, got_col = _noalloc(torch, rp, col, ls, 0.5, E, out_rp, out_col)
+    assert np.array_equal(got_rp, ref_rp)
+    assert np.array_equal(got_col, ref_col[:E])
+
+
 def test_noalloc_rejects_sizes_beyond_the_static_array(torch):
     dummy = torch.zeros(4, dtype=torch.int64, device="cuda")
     st = amgd.lib().amgd_strength_noalloc(dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(),
