@@ -247,7 +247,7 @@ class ClockSampler:
 # our arm
 # --------------------------------------------------------------------------
 def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_clocks=True,
-                tune_cache=None):
+                tune_cache=None, summation="compensated"):
     """One step = one captured build (or, for a workload with a checkpoint
     interval, one captured forward + reverse step)."""
     import torch
@@ -260,6 +260,7 @@ def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_cloc
         h = amgd.Handle(None, None, None, w["K"], w["seed"], batch=mats)
     h.set_stream(stream)
     h.set_precision(precision)
+    h.set_summation(summation)
     ncolors = 1
     sweep = amgd.AMGD_SWEEP_JACOBI
     if w["sweep"] == "mcgs":
@@ -886,7 +887,10 @@ def main():
             "config": {"workload": w["name"], "config": cfg, "n": n, "nnz": nnz, "E": E,
                        "search_depth": depth, "nnz_pattern": nnz_p,
                        "K": w["K"], "nu": w["nu"], "sweep": w["sweep"], "theta": w["theta"],
-                       "storage": precision, "l2": "flushed between steps (256 MiB write)",
+                       "storage": precision,
+                       "ls_sums": ("compensated FP32 (Kahan-Babuska-Neumaier, TwoSum)"
+                                   if mixed else "FP64"),
+                       "l2": "flushed between steps (256 MiB write)",
                        "graph": "one CUDA graph per step",
                        "shapes": {"relax": list(r["shapes"][0]), "edge": list(r["shapes"][1]),
                                   "legend": "(lanes per row G, 16-byte vectors per lane NV, "
@@ -936,6 +940,20 @@ def main():
                         "relax_hbm_frac": a64 / peak,
                         "mixed_over_fp64": value / v64}
         r64["h"].close()
+
+    # cost of the compensated LS sums: the same build with plain FP32 sums
+    if not args.no_side and mixed and not adj and depth == 1:
+        side_steps = max(3, min(args.steps, 100))
+        r_p = run_gpu_arm(mats, color, w, precision, side_steps, 3, rank, flush,
+                          want_clocks=False, tune_cache=args.tune_cache, summation="plain")
+        v_p, t_p = whole_job(float(r_p["step_ms"].sum()), E, side_steps)
+        line["plain_ls_sums"] = {"value": v_p, "unit": "edges/s", "ms_per_step": t_p,
+                                 "steps": side_steps,
+                                 "distances_ms": float(r_p["phase_ms"][2]),
+                                 "edge_shape": list(r_p["shapes"][1]),
+                                 "compensation_cost_ms": float(r["phase_ms"][2] -
+                                                               r_p["phase_ms"][2])}
+        r_p["h"].close()
 
     # the other mixed storage beside the headline (BF16 beside FP32 and the other way
     # round), timed on the same matrix; its accuracy is taken against the same oracle

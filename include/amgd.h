@@ -74,8 +74,12 @@ typedef struct amgd_ctx *amgd_handle;
 
 /* test-vector storage precision */
 #define AMGD_FP64 0   /* FP64 vectors, FP64 arithmetic                                  */
-#define AMGD_FP32 1   /* FP32 vectors, FP32 arithmetic, compensated FP32 LS sums        */
-#define AMGD_BF16 2   /* BF16 vectors, FP32 arithmetic, compensated FP32 LS sums        */
+#define AMGD_FP32 1   /* FP32 vectors, FP32 arithmetic (LS sums: amgd_set_summation)   */
+#define AMGD_BF16 2   /* BF16 vectors, FP32 arithmetic (LS sums: amgd_set_summation)   */
+
+/* summation of the K-term LS sums on the mixed paths (amgd_set_summation) */
+#define AMGD_SUM_PLAIN       0   /* FP32 fused multiply-add chains                  */
+#define AMGD_SUM_COMPENSATED 1   /* compensated FP32 sums (default)                  */
 
 /*
  * amgd_create -- build a handle for one n x n matrix A in CSR form.
@@ -128,6 +132,25 @@ int amgd_set_precision(amgd_handle h, int storage);
 
 /* LS target: AMGD_TARGET_RESIDUAL (default) or AMGD_TARGET_PLAIN. */
 int amgd_set_target(amgd_handle h, int target);
+
+/*
+ * amgd_set_summation -- how the mixed paths (FP32/BF16 storage, FP32
+ *   arithmetic) form the K-term sums S_xx = sum w x_j^2, S_yx = sum w y_i x_j
+ *   and LS_ij = sum w (y_i - a_ij x_j)^2 of the one-point fit (§4.1, Eq.
+ *   (4.3)).  AMGD_SUM_COMPENSATED (the default): every lane keeps a running
+ *   FP32 sum and the exact rounding error of each of its additions (TwoSum)
+ *   in a second FP32 word (the Kahan-Babuska-Neumaier scheme), the lanes of a
+ *   row combine their pairs with TwoSum in the shuffle reduction, and the two
+ *   words are added once at the end.  AMGD_SUM_PLAIN: FP32 fused
+ *   multiply-add chains.  Either way an edge whose LS falls below 1e-4 of
+ *   sum_k w_k y_k^2 makes its row be redone in FP64 (cancellation).  The
+ *   compensated form is computed by the distance kernel that reads the
+ *   sweeps' row order (edge stage 2, search depth 1); with a search depth
+ *   d > 1 the distance pass sums plainly.  The FP64 path ignores the
+ *   setting.  Drops computed distances and a captured graph.
+ *   Errors: ARG.
+ */
+int amgd_set_summation(amgd_handle h, int mode);
 
 /* LS weights w[K] (host doubles, each > 0 and finite; §3.1 weights
  * omega_kappa of Eq. (3.1)); NULL restores all ones. */
@@ -220,8 +243,9 @@ int amgd_relax(amgd_handle h, int32_t nu, double omega, int sweep_type);
  *   threshold and every per-slot output follow the entries of the graph G_d
  *   of A^d instead of A's (nnz_p entries, see amgd_distance_pattern); the
  *   target is still built from row i of A (Eq. (4.3)).
- *   Mixed precisions compute in FP32 with compensated sums and redo in FP64
- *   an edge whose LS is below 1e-4 * sum_k w_k y_k^2 (cancellation).
+ *   Mixed precisions compute in FP32 -- the LS sums compensated or plain,
+ *   see amgd_set_summation -- and redo in FP64 the row of an edge whose LS
+ *   is below 1e-4 * sum_k w_k y_k^2 (cancellation).
  *   Errors: ARG, CUDA.
  */
 int amgd_distances(amgd_handle h, double theta, double *a, double *dist, double *ls, int mem);
@@ -283,8 +307,12 @@ int amgd_graph_launch(amgd_handle h);
  *   ahead (U must be 4); 3 persistent with L2 prefetch, each warp asking
  *   the L2 for the row pointers and CSR lines of its rows one and two tiles
  *   ahead.  For the distance pass, staged selects 0 the row
- *   kernel (G lanes per row) or 1 the tile kernel (one thread per stored
- *   entry).  Shapes change speed only, never results beyond the order of
+ *   kernel (G lanes per row), 1 the tile kernel (one thread per stored
+ *   entry) or 2 the row kernel reading the vectors in the sweeps' row
+ *   order in place (search depth 1: no caller-order copy of the vectors;
+ *   the only kernel with compensated sums on the mixed paths; U in {2,4};
+ *   the default).  With search depth d > 1 a stage-2 shape runs
+ *   as stage 0.  Shapes change speed only, never results beyond the order of
  *   the K-term LS sums.  kernel: AMGD_KERNEL_RELAX (the sweeps) or
  *   AMGD_KERNEL_EDGE (the distance pass); the shape applies to the current
  *   storage precision.

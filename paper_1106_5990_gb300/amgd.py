@@ -43,6 +43,8 @@ AMGD_FP32 = 1
 AMGD_BF16 = 2
 AMGD_KERNEL_RELAX = 0
 AMGD_KERNEL_EDGE = 1
+AMGD_SUM_PLAIN = 0
+AMGD_SUM_COMPENSATED = 1
 
 PRECISIONS = {"fp64": AMGD_FP64, "fp32": AMGD_FP32, "bf16": AMGD_BF16}
 
@@ -58,6 +60,7 @@ SIGNATURES = {
     "amgd_set_stream": (_int, [_P, _P]),
     "amgd_set_precision": (_int, [_P, _int]),
     "amgd_set_target": (_int, [_P, _int]),
+    "amgd_set_summation": (_int, [_P, _int]),
     "amgd_set_weights": (_int, [_P, _P]),
     "amgd_set_coloring": (_int, [_P, _P, _i32, _int]),
     "amgd_init_vectors": (_int, [_P, _u64]),
@@ -291,6 +294,12 @@ class Handle:
 
     def set_target(self, target):
         self._ck(lib().amgd_set_target(self.h, target))
+
+    def set_summation(self, mode):
+        """AMGD_SUM_COMPENSATED (default) or AMGD_SUM_PLAIN, or "compensated" / "plain"."""
+        if isinstance(mode, str):
+            mode = {"plain": AMGD_SUM_PLAIN, "compensated": AMGD_SUM_COMPENSATED}[mode]
+        self._ck(lib().amgd_set_summation(self.h, mode))
 
     def set_weights(self, w):
         if w is None:

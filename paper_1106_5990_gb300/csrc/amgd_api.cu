@@ -48,6 +48,8 @@ struct amgd_ctx {
     double *diag64_o = nullptr;                  // caller-order diagonal (edge pass)
     float *diag32_o = nullptr;
     void *x_caller = nullptr;                    // caller-order copy of permuted vectors
+    int32_t *pinv = nullptr;                     // caller row -> permuted row
+    int32_t *colx = nullptr;                     // caller CSR, columns in permuted numbering
     uint32_t *defer_count = nullptr;             // rows the mixed edge pass redoes in FP64
     int32_t *defer_list = nullptr;
     std::vector<int64_t> color_start;           // permuted row start of each color
@@ -127,6 +129,7 @@ struct amgd_ctx {
     // pattern of the fits, threshold and strength graph: the graph G_d of A^d
     // (search depth d); for d = 1 these alias A's caller-order pattern
     int32_t depth = 1;
+    int32_t summation = AMGD_SUM_COMPENSATED;   // LS sums of the mixed paths (edge stage 2)
     int32_t *prp = nullptr, *pcol = nullptr;
     int64_t nnz_p = 0, E_p = 0;
     bool last_backward_builtin = false;          // the last reverse pass used the built-in loss
@@ -166,6 +169,14 @@ bool shape_ok(int st, int K, Shape sh)
     if (sh.G < 1 || sh.G > 32 || (sh.G & (sh.G - 1))) return false;
     if (sh.stage < 0 || sh.stage > 3) return false;
     return sh.G * sh.NV == P;
+}
+
+// the distance pass: stages 0 (rows) and 1 (tiles) take every valid shape;
+// stage 2 (the row kernel on the sweeps' row order) 2 or 4 entries per batch
+bool edge_shape_ok(Shape sh)
+{
+    if (sh.stage < 0 || sh.stage > 2) return false;
+    return sh.stage < 2 || sh.U == 2 || sh.U == 4;
 }
 
 // untuned default: one vector per lane, four nonzeros per batch (the
@@ -449,10 +460,12 @@ int run_relax_recorded(amgd_ctx *h, int32_t nu, double omega, cudaStream_t s)
 
 int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
 {
-    // the edge pass runs on the caller's numbering: bring a row-permuted
-    // vector block back to caller order first
+    Shape sh = h->edge_shape[h->storage];
+    if (sh.stage == 2 && h->depth > 1) sh.stage = 0;    // stage 2 covers A's own pattern
+    // stages 0 and 1 run on the caller's numbering: bring a row-permuted vector
+    // block back to caller order first; stage 2 reads the sweeps' row order
     const void *xc = h->x[h->cur];
-    if (h->perm) {
+    if (h->perm && sh.stage != 2) {
         if (!h->x_caller) return fail(h, AMGD_ERR_STATE, "caller-order vector buffer missing");
         CK(h, launch_unpermute(h->storage, h->x[h->cur], h->x_caller, h->perm, (int32_t)h->n,
                                Kp_of(h->storage, h->K), s));
@@ -481,9 +494,15 @@ int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
     a.Kp = Kp_of(h->storage, h->K);
     a.target = h->target;
     a.theta = theta;
+    if (sh.stage == 2) {
+        a.x = h->x[h->cur];                  // the sweeps' row order, read in place
+        a.xrow = h->perm ? h->pinv : nullptr;
+        a.xcol = h->perm ? h->colx : h->col_o;
+    }
+    a.compensated = h->summation == AMGD_SUM_COMPENSATED;
     bool unit_w = true;
     for (double wk : h->h_w) unit_w = unit_w && wk == 1.0;
-    CK(h, launch_edge(h->storage, h->edge_shape[h->storage], unit_w, a, s));
+    CK(h, launch_edge(h->storage, sh, unit_w, a, s));
     h->have_dist = true;
     return AMGD_OK;
 }
@@ -587,7 +606,11 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
     h->h_col = std::move(h_col);
     h->h_diag_slot = std::move(diag_slot);
     h->h_w.assign((size_t)K, 1.0);
-    for (int st = 0; st < 3; ++st) h->relax_shape[st] = h->edge_shape[st] = default_shape(st, K);
+    for (int st = 0; st < 3; ++st) {
+        h->relax_shape[st] = default_shape(st, K);
+        // distances: the sweeps' row order, one vector per lane, two gathers per batch
+        h->edge_shape[st] = Shape{P_of(st, K), 1, 2, 2};
+    }
     cudaGetDevice(&h->device);
 
     auto bail = [&](int rc) {
@@ -766,6 +789,20 @@ int amgd_set_target(amgd_handle h, int target)
     return AMGD_OK;
 }
 
+int amgd_set_summation(amgd_handle h, int mode)
+{
+    if (!h) return AMGD_ERR_ARG;
+    if (mode != AMGD_SUM_PLAIN && mode != AMGD_SUM_COMPENSATED)
+        return fail(h, AMGD_ERR_ARG, "unknown summation mode");
+    if (mode != h->summation) {
+        drop_graph(h);
+        h->summation = mode;
+    }
+    h->have_dist = false;
+    h->traj_valid = false;
+    return AMGD_OK;
+}
+
 int amgd_set_weights(amgd_handle h, const double *w)
 {
     if (!h) return AMGD_ERR_ARG;
@@ -833,6 +870,16 @@ int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int 
     CK(h, cudaMemcpy(h->perm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->rp_p, rp_p.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->col_p, col_p.data(), h->nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    {
+        // the distance pass reads the sweeps' row order in place: the caller CSR
+        // with its columns renumbered, and the permuted row of every caller row
+        std::vector<int32_t> cx((size_t)h->nnz);
+        for (int64_t p = 0; p < h->nnz; ++p) cx[(size_t)p] = inv[(size_t)h->h_col[(size_t)p]];
+        if (!h->pinv) CK(h, dalloc(&h->pinv, (size_t)(n ? n : 1)));
+        if (!h->colx) CK(h, dalloc(&h->colx, (size_t)h->nnz + 16));
+        CK(h, cudaMemcpy(h->pinv, inv.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->colx, cx.data(), h->nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     {
         std::vector<int32_t> sp((size_t)h->nnz);
         for (int64_t r = 0; r < n; ++r) {
@@ -1191,7 +1238,7 @@ int amgd_set_kernel_shape(amgd_handle h, int kernel, int G, int NV, int U, int s
     if (!h) return AMGD_ERR_ARG;
     const Shape sh{G, NV, U, staged};
     if ((kernel != AMGD_KERNEL_RELAX && kernel != AMGD_KERNEL_EDGE) || !shape_ok(h->storage, h->K, sh) ||
-        (kernel == AMGD_KERNEL_EDGE && staged > 1) ||
+        (kernel == AMGD_KERNEL_EDGE && !edge_shape_ok(sh)) ||
         (kernel == AMGD_KERNEL_RELAX && !relax_shape_available(h->storage, sh)))
         return fail(h, AMGD_ERR_ARG, "invalid kernel shape for this storage and K");
     (kernel == AMGD_KERNEL_RELAX ? h->relax_shape : h->edge_shape)[h->storage] = sh;
@@ -1226,7 +1273,8 @@ std::string tune_key(amgd_ctx *h, int sweep_type)
     return "gpu=" + gpu + ";st=" + std::to_string(h->storage) + ";K=" + std::to_string(h->K) +
            ";nb=" + std::to_string(nb) + ";db=" + std::to_string(db) +
            ";sweep=" + std::to_string(sweep_type) + ";colors=" +
-           std::to_string(h->color_start.size() - 1);
+           std::to_string(h->color_start.size() - 1) + ";sum=" + std::to_string(h->summation) +
+           ";depth=" + std::to_string(h->depth);
 }
 
 bool parse_shape(const std::string &line, const char *tag, Shape &sh)
@@ -1289,7 +1337,7 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
                 if (line.compare(0, key.size(), key) == 0 && line.size() > key.size() &&
                     line[key.size()] == ';' && parse_shape(line, "relax", r) &&
                     parse_shape(line, "edge", e) && shape_ok(h->storage, h->K, r) &&
-                    shape_ok(h->storage, h->K, e) && e.stage <= 1 &&
+                    shape_ok(h->storage, h->K, e) && edge_shape_ok(e) &&
                     relax_shape_available(h->storage, r))
                     found = true;       // the last matching line wins
             }
@@ -1326,12 +1374,17 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
             if (prc != AMGD_OK) { h->relax_shape[h->storage] = keep_r; return prc; }
         }
     }
-    // edge pass: stage 0 row kernel, stage 1 tile kernel
-    for (int stage : {0, 1})
+    // edge pass: stage 0 row kernel, stage 1 tile kernel, stage 2 the sweeps'
+    // row order (search depth 1).  With compensated sums on a mixed path only
+    // stage 2 is a candidate: it is the kernel that sums with compensation.
+    const bool comp_only = h->storage != ST_FP64 && h->summation == AMGD_SUM_COMPENSATED &&
+                           h->depth == 1;
+    for (int stage : {0, 1, 2})
         for (int NV : {1, 2, 4})
             for (int U : {2, 4, 8}) {
                 const Shape c{P / NV, NV, U, stage};
-                if (P % NV != 0 || !shape_ok(h->storage, h->K, c)) continue;
+                if (P % NV != 0 || !shape_ok(h->storage, h->K, c) || !edge_shape_ok(c)) continue;
+                if ((stage == 2) != comp_only && (comp_only || h->depth > 1)) continue;
                 float ms = 0.f;
                 h->edge_shape[h->storage] = c;
                 const int rc = time_ms(h, [&]() { return run_edge(h, 0.5, h->stream); }, 5, ms);
@@ -2043,6 +2096,8 @@ int amgd_destroy(amgd_handle h)
         dfree(h->col_p);
         dfree(h->val64);
         dfree(h->slot_perm);
+        dfree(h->pinv);
+        dfree(h->colx);
     }
     if (h->depth > 1) {
         dfree(h->prp);

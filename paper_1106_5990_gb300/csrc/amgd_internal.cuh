@@ -189,6 +189,11 @@ struct EdgeArgs {                // everything in the caller's numbering
     int32_t ntiles;
     int32_t n, Kp, target;       // target: 0 residual, 1 plain
     double theta;
+    // edge stage 2 (search depth 1): x is the vector block in the sweeps' row
+    // order; xrow[i] is the vector row of caller row i (NULL: i) and xcol[p]
+    // the vector row of the column of caller slot p
+    const int32_t *xrow = nullptr, *xcol = nullptr;
+    bool compensated = false;    // mixed paths of stage 2: compensated FP32 LS sums
 };
 
 // row tiles of the edge pass: consecutive rows, at most kEdgeTileRows rows and

@@ -110,10 +110,108 @@ __device__ __forceinline__ void residual_add(C a, const C (&x)[V], const C (&y)[
 }
 
 // ---------------------------------------------------------------------------
-// Row kernel (edge shape stage 0).  G lanes own one row through all three
+// Compensated FP32 sums (mixed paths, AMGD_SUM_COMPENSATED).  Each sum is two
+// FP32 words: a running sum and the exact rounding error of every addition,
+// taken by TwoSum (six IEEE additions, no fusion) -- the Kahan-Babuska-
+// Neumaier scheme.  S_xx and S_yx travel together as one packed pair; the LS
+// terms of even and odd components as the halves of another (FP32x2
+// instructions).  Lanes combine their pairs in the shuffle butterfly with
+// TwoSum again, adding the error words; the two words are added once at the
+// end.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);     // a - b, one rounding
+}
+// s + e == a + b exactly (Knuth's TwoSum, both halves of the pair)
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = __fadd2_rn(a, b);
+    const float2 bp = sub2(s, a);
+    const float2 ap = sub2(s, bp);
+    e = __fadd2_rn(sub2(a, ap), sub2(b, bp));
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+struct Comp2 {
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float2 t)
+    {
+        float2 sn, e;
+        two_sum2(s, t, sn, e);
+        s = sn;
+        c = __fadd2_rn(c, e);
+    }
+};
+// pairs of the G lanes of a row combined (xor butterfly: every lane ends with
+// the total)
+template <int G>
+__device__ __forceinline__ void comp2_allreduce(Comp2 &v, unsigned mask)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        float2 so, co;
+        so.x = __shfl_xor_sync(mask, v.s.x, o, G);
+        so.y = __shfl_xor_sync(mask, v.s.y, o, G);
+        co.x = __shfl_xor_sync(mask, v.c.x, o, G);
+        co.y = __shfl_xor_sync(mask, v.c.y, o, G);
+        float2 sn, e;
+        two_sum2(v.s, so, sn, e);
+        v.s = sn;
+        v.c = __fadd2_rn(__fadd2_rn(v.c, co), e);
+    }
+}
+// (S_xx, S_yx) of one piece, added to a compensated pair
+template <int V, bool UW>
+__device__ __forceinline__ void comp_piece_sums(const float (&x)[V], const float (&y)[V],
+                                                const float (&w)[V], Comp2 &acc)
+{
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const float wx = UW ? x[e] : w[e] * x[e];
+        acc.add(__fmul2_rn(make_float2(wx, wx), make_float2(x[e], y[e])));
+    }
+}
+// w (y - a x)^2 of one piece, even and odd components as the pair's halves
+template <int V, bool UW>
+__device__ __forceinline__ void comp_residual(float a, const float (&x)[V], const float (&y)[V],
+                                              const float (&w)[V], Comp2 &acc)
+{
+    const float2 na = make_float2(-a, -a);
+#pragma unroll
+    for (int e = 0; e < V; e += 2) {
+        const float2 d = __ffma2_rn(na, make_float2(x[e], x[e + 1]), make_float2(y[e], y[e + 1]));
+        const float2 wd = UW ? d : make_float2(w[e] * d.x, w[e + 1] * d.y);
+        acc.add(__fmul2_rn(wd, d));
+    }
+}
+// the LS pair's two halves joined, then the lanes: one FP32 value
+template <int G>
+__device__ __forceinline__ float comp_ls_total(const Comp2 &acc, unsigned mask)
+{
+    float s, e;
+    two_sum(acc.s.x, acc.s.y, s, e);
+    Comp2 one;
+    one.s = make_float2(s, 0.f);
+    one.c = make_float2(__fadd_rn(__fadd_rn(acc.c.x, acc.c.y), e), 0.f);
+    comp2_allreduce<G>(one, mask);
+    return one.s.x + one.c.x;
+}
+
+// ---------------------------------------------------------------------------
+// Row kernel (edge shape stages 0 and 2).  G lanes own one row through all three
 // steps: the target from the row's gathers, then the fits with the row's
 // neighbours gathered again (mostly L1/L2 hits), K-component sums reduced
 // across the G lanes with shuffles, then the flags.
+// Stage 2 (PX): the vectors stay in the sweeps' row order (no caller-order
+// copy is made); row i's own vector is read at xrow[i] and the neighbour of
+// slot p at xcol[p] -- the caller CSR with every column index mapped to the
+// sweeps' numbering -- and the mixed paths may sum with compensation (COMP).
 // Per-warp output staging: a warp owns 32/G consecutive rows of the caller's
 // numbering, i.e. one contiguous run of CSR slots.  a, LS and the flags of
 // that run are collected in shared memory and written out with coalesced
@@ -141,7 +239,7 @@ constexpr int edge_smem_bytes()
 #define AMGD_EDGE_BOUNDS __launch_bounds__(kEdgeThreads)
 #endif
 
-template <class TS, int G, int NV, int U, bool UW>
+template <class TS, int G, int NV, int U, bool UW, bool PX, bool COMP>
 __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
 {
     using S = Store<TS>;
@@ -165,6 +263,7 @@ __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
     uint8_t *fl_s = esm + (size_t)(kEdgeThreads / 32) * kWarpSlots * 2 * sizeof(C) + (size_t)warp * kWarpSlots;
 
     const int32_t *__restrict__ col = A.col;
+    const int32_t *__restrict__ xcol = PX ? A.xcol : A.col;   // gather index of each slot
     const AV *__restrict__ val = (const AV *)A.val;
     const TS *__restrict__ X = (const TS *)A.x;
     const int Kp = A.Kp;
@@ -195,11 +294,12 @@ __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
         C y[NV][V];
         {
             Acc<C, V> acc[NV];
-            row_sum<TS, G, NV, U, false>(col, val, X, X, 0, Kp, lane, p0, p1, acc);
+            row_sum<TS, G, NV, U, false>(xcol, val, X, X, 0, Kp, lane, p0, p1, acc);
             const C d = C(1) / diag;
+            const int64_t xr = (PX && A.xrow) ? (int64_t)__ldg(A.xrow + r) : r;
 #pragma unroll
             for (int t = 0; t < NV; ++t) {
-                S::unpack(ldg16(X + r * Kp + (t * G + lane) * V), y[t]);      // x_i
+                S::unpack(ldg16(X + xr * Kp + (t * G + lane) * V), y[t]);     // x_i
                 if (A.target == 0) {
 #pragma unroll
                     for (int e = 0; e < V; ++e) y[t][e] = fma(-d, acc[t].get(e), y[t][e]);
@@ -233,10 +333,12 @@ __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
             uint4 raw[U][NV];
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (jj[u] >= 0 && jj[u] != r)
+                if (jj[u] >= 0 && jj[u] != r) {
+                    const int64_t xj = PX ? (int64_t)__ldg(xcol + pb + u) : (int64_t)jj[u];
 #pragma unroll
                     for (int t = 0; t < NV; ++t)
-                        raw[u][t] = ldg16(X + (int64_t)jj[u] * Kp + (t * G + lane) * V);
+                        raw[u][t] = ldg16(X + xj * Kp + (t * G + lane) * V);
+                }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (jj[u] < 0) break;
@@ -248,6 +350,26 @@ __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
                 } else if (jj[u] == j1) {
                     a_ = -v1 / diag;
                     ls_ = C(0);
+                } else if constexpr (COMP && kMixed) {
+                    Comp2 sx;
+#pragma unroll
+                    for (int t = 0; t < NV; ++t) {
+                        C xj[V];
+                        S::unpack(raw[u][t], xj);
+                        comp_piece_sums<V, UW>(xj, y[t], w[t], sx);
+                    }
+                    comp2_allreduce<G>(sx, gmask);
+                    const C sxx = sx.s.x + sx.c.x, syx = sx.s.y + sx.c.y;
+                    a_ = (sxx == C(0)) ? C(0) : divide(syx, sxx);
+                    Comp2 sl;
+#pragma unroll
+                    for (int t = 0; t < NV; ++t) {
+                        C xj[V];
+                        S::unpack(raw[u][t], xj);
+                        comp_residual<V, UW>(a_, xj, y[t], w[t], sl);
+                    }
+                    ls_ = comp_ls_total<G>(sl, gmask);
+                    defer = defer || ls_ < C(1e-4) * syy;
                 } else {
                     // x_j is unpacked from the gathered bits once per use, so only one
                     // 16-byte piece of it is live in registers at a time
@@ -542,7 +664,7 @@ __device__ __forceinline__ double elem64(const TS *p)
         return (double)*p;
 }
 
-template <class TS>
+template <class TS, bool PX>
 __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
 {
     using C = typename Store<TS>::C;
@@ -550,6 +672,9 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
     const int lane = threadIdx.x % 32;
     const TS *X = (const TS *)A.x;
     const int Kp = A.Kp;
+    // vector row of caller row i and of the neighbour of slot p (stage 2: the
+    // sweeps' row order; search depth 1, so the fit slots are A's slots)
+    auto xrow = [&](int64_t i) -> int64_t { return (PX && A.xrow) ? (int64_t)A.xrow[i] : i; };
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; q < count; q += warps) {
         const int64_t r = A.defer_list[q];
@@ -568,9 +693,10 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
             const int k = lane + 32 * h;
             w[h] = k < Kp ? A.w64[k] : 0.0;
             double acc = 0.0;
-            const double xi = k < Kp ? elem64(X + r * Kp + k) : 0.0;
+            const double xi = k < Kp ? elem64(X + xrow(r) * Kp + k) : 0.0;
             if (k < Kp)
-                for (int p = p0; p < p1; ++p) acc = fma(A.val64[p], elem64(X + (int64_t)A.col[p] * Kp + k), acc);
+                for (int p = p0; p < p1; ++p)
+                    acc = fma(A.val64[p], elem64(X + (int64_t)(PX ? A.xcol[p] : A.col[p]) * Kp + k), acc);
             y[h] = (A.target == 0) ? fma(-d, acc, xi) : xi;
         }
         double m = INFINITY;
@@ -587,9 +713,10 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
                 ls64 = 0.0;
             } else {
                 double xj[2], sxx = 0.0, syx = 0.0;
+                const int64_t xjr = PX ? (int64_t)A.xcol[p] : j;
                 for (int h = 0; h < 2; ++h) {
                     const int k = lane + 32 * h;
-                    xj[h] = k < Kp ? elem64(X + j * Kp + k) : 0.0;
+                    xj[h] = k < Kp ? elem64(X + xjr * Kp + k) : 0.0;
                     sxx = fma(w[h] * xj[h], xj[h], sxx);
                     syx = fma(w[h] * xj[h], y[h], syx);
                 }
@@ -626,13 +753,22 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
     }
 }
 
-template <class K>
-cudaError_t opt_in_smem(K kernel, int bytes, bool &opted)
+template <class TS, int G, int NV, int U, bool UW, bool PX, bool COMP>
+cudaError_t go_rows(const EdgeArgs &a, cudaStream_t s)
 {
-    if (bytes <= 48 * 1024 || opted) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) opted = true;
-    return e;
+    const int rows_per_block = kEdgeThreads / G;
+    const unsigned grid = (unsigned)(((int64_t)a.n + rows_per_block - 1) / rows_per_block);
+    constexpr int smem = edge_smem_bytes<typename Store<TS>::C, G>();
+    static PerDevice opted;                  // shared-memory opt-in made on each device
+    const int dev = current_device_index();
+    if (smem > 48 * 1024 && opted.get(dev) == 0) {
+        const cudaError_t e = cudaFuncSetAttribute(k_edge_rows<TS, G, NV, U, UW, PX, COMP>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        opted.set(dev, 1);
+    }
+    k_edge_rows<TS, G, NV, U, UW, PX, COMP><<<grid, kEdgeThreads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <class TS, int G, int NV, int U, bool UW>
@@ -643,20 +779,26 @@ cudaError_t go(int stage, const EdgeArgs &a, cudaStream_t s)
         constexpr int KP = G * NV * Store<TS>::V;
         if (a.Kp != KP || a.ntiles <= 0) return cudaErrorInvalidValue;
         constexpr int smem = EdgeTileLayout<TS, KP>::BYTES;
-        static bool opted = false;
-        const cudaError_t e = opt_in_smem(k_edge_tiles<TS, G, NV, U, UW>, smem, opted);
-        if (e != cudaSuccess) return e;
+        static PerDevice opted;              // shared-memory opt-in made on each device
+        const int dev = current_device_index();
+        if (smem > 48 * 1024 && opted.get(dev) == 0) {
+            const cudaError_t e = cudaFuncSetAttribute(k_edge_tiles<TS, G, NV, U, UW>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       smem);
+            if (e != cudaSuccess) return e;
+            opted.set(dev, 1);
+        }
         k_edge_tiles<TS, G, NV, U, UW><<<(unsigned)a.ntiles, kEdgeThreads, smem, s>>>(a);
         return cudaGetLastError();
     }
-    const int rows_per_block = kEdgeThreads / G;
-    const unsigned grid = (unsigned)(((int64_t)a.n + rows_per_block - 1) / rows_per_block);
-    constexpr int smem = edge_smem_bytes<typename Store<TS>::C, G>();
-    static bool opted = false;
-    const cudaError_t e = opt_in_smem(k_edge_rows<TS, G, NV, U, UW>, smem, opted);
-    if (e != cudaSuccess) return e;
-    k_edge_rows<TS, G, NV, U, UW><<<grid, kEdgeThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    if (stage == 2) {
+        if constexpr (std::is_same<typename Store<TS>::C, double>::value)
+            return go_rows<TS, G, NV, U, UW, true, false>(a, s);
+        else
+            return a.compensated ? go_rows<TS, G, NV, U, UW, true, true>(a, s)
+                                 : go_rows<TS, G, NV, U, UW, true, false>(a, s);
+    }
+    return go_rows<TS, G, NV, U, UW, false, false>(a, s);
 }
 
 template <class TS, int G, int NV, bool UW>

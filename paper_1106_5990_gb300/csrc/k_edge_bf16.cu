@@ -9,7 +9,8 @@ cudaError_t launch_edge_bf16(Shape sh, bool unit_w, const EdgeArgs &a, cudaStrea
     if (e != cudaSuccess) return e;
     e = edge_impl::dispatch_g<__nv_bfloat16>(sh, unit_w, a, s);
     if (e != cudaSuccess || a.n == 0) return e;
-    edge_impl::k_edge_fixup<__nv_bfloat16><<<152, 256, 0, s>>>(a);
+    if (sh.stage == 2) edge_impl::k_edge_fixup<__nv_bfloat16, true><<<152, 256, 0, s>>>(a);
+    else edge_impl::k_edge_fixup<__nv_bfloat16, false><<<152, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -175,6 +175,72 @@ def test_cancellation_uses_fp64(prec, target):
     assert rel[off].max() <= 1e-3, rel[off].max()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_cancellation_uses_fp64_colored(prec):
+    """The same cancellation-bound rows on a handle whose sweeps reorder the
+    rows (a coloring): the FP64 redo of the distance pass that reads the
+    sweeps' row order writes every output at its caller slot."""
+    n, K = 64, 16
+    rp, col, val = inputs.lap1d(n)
+    g = np.random.default_rng(8)
+    base = g.integers(-128, 128, size=K) / 128.0
+    base[0] = 0.0
+    X = np.stack([base * 2.0 ** (i % 3) * (-1) ** (i // 3) for i in range(n)])
+    X[:, 0] = 2.0 ** -20 * np.where(g.random(n) < 0.5, -1.0, 1.0)
+    Y = oracle.target(rp, col, val, X, 0)
+    a_w, ls_w = oracle.edge_ls(rp, col, val, X, Y, None, 0)
+    flag_w, _ = oracle.threshold(rp, col, ls_w, 0.5)
+    with amgd.Handle(rp, col, val, K, 0) as h:
+        h.set_precision(prec)
+        h.set_coloring(inputs.greedy_coloring(rp, col))
+        h.set_vectors(X)
+        assert np.array_equal(h.get_vectors(), X)
+        out = h.distances(0.5)
+        s_rp, s_col = h.strength()
+    rows, cols = edge_rows(rp, col)
+    off = rows != cols
+    syy, _ = ls_scales(rp, col, X, Y)
+    big = ls_w >= 1e-12 * syy
+    rel = np.abs(out["ls"] - ls_w) / np.where(big, ls_w, syy)
+    assert rel[off].max() <= 1e-3, rel[off].max()
+    flag = flags_from_strength_fast(rp, col, s_rp, s_col)
+    check_flags(flag, dict(ls=ls_w, flag=flag_w), rp, col, 0.5, 1e-3)
+
+
+def test_compensated_sums_resolve_cancellation():
+    """S_yx of a one-point fit as a cancelling sum: plain target (y_i = x_i,
+    stored exactly), K = 64 full-precision FP32 components whose products
+    with x_j = 1 sum to about 1e-7 of their magnitudes.  The compensated FP32
+    sums reproduce the oracle's a_ij = S_yx / S_xx to 1e-5 relative; plain
+    FP32 chains lose it (their error is of the size of the sum itself)."""
+    n, K = 64, 64
+    rp, col, val = inputs.lap1d(n)
+    g = np.random.default_rng(11)
+    X = np.ones((n, K))
+    for i in range(0, n, 2):
+        v = g.uniform(-1.0, 1.0, K).astype(np.float32).astype(np.float64)
+        v[-1] = np.float32(-(v[:-1].sum()) + 3e-7)          # sum of the row ~ 3e-7
+        X[i] = v
+    X = X.astype(np.float32).astype(np.float64)
+    Y = oracle.target(rp, col, val, X, 1)
+    a_w, ls_w = oracle.edge_ls(rp, col, val, X, Y, None, 1)
+    rows, cols = edge_rows(rp, col)
+    sel = (rows != cols) & (rows % 2 == 0)                   # fits of the cancelling rows
+    assert np.all(np.abs(a_w[sel]) < 1e-6)                   # the case really cancels
+    err = {}
+    for mode in ("compensated", "plain"):
+        with amgd.Handle(rp, col, val, K, 0) as h:
+            h.set_precision("fp32")
+            h.set_target(amgd.AMGD_TARGET_PLAIN)
+            h.set_summation(mode)
+            h.set_vectors(X)
+            out = h.distances(0.5)
+        err[mode] = (np.abs(out["a"][sel] - a_w[sel]) / np.abs(a_w[sel])).max()
+    print("a_ij relative error: compensated %.2e, plain %.2e" % (err["compensated"], err["plain"]))
+    assert err["compensated"] <= 1e-5
+    assert err["plain"] >= 1e-3
+
+
 def _end_to_end(prec, rp, col, val, K, seed, nu, omega, sweep, color, theta=0.5):
     want = oracle.build(rp, col, val, K, seed, nu, omega, theta,
                         oracle.SWEEP_MCGS if sweep else oracle.SWEEP_JACOBI, color)

@@ -546,6 +546,48 @@ def test_kernel_shapes_agree(prec, K):
             h.set_kernel_shape(amgd.AMGD_KERNEL_RELAX, 3, 1, 4)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("K", [5, 16, 64])
+def test_edge_stage2_shapes_agree(prec, K):
+    """The distance kernel on the sweeps' row order (edge stage 2), every
+    shape and both summation modes, against the row kernel (stage 0) on the
+    same vectors: FP64 within 1e-12 relative, mixed within 2e-5; strength
+    sets identical outside a band of 1e-4 around theta."""
+    N = 40
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
+    color = inputs.red_black(N)
+    V = {"fp64": 2, "fp32": 4, "bf16": 8}[prec]
+    P = 1
+    while P * V < K:
+        P *= 2
+
+    def run(shape, summation="compensated"):
+        with amgd.Handle(rp, col, val, K, 4) as h:
+            h.set_precision(prec)
+            h.set_coloring(color)
+            h.set_summation(summation)
+            h.set_kernel_shape(amgd.AMGD_KERNEL_EDGE, *shape)
+            h.relax(3, 1.0, amgd.AMGD_SWEEP_MCGS)
+            out = h.distances(0.5)
+            s_rp, s_col = h.strength()
+        return out, flags_from_strength(rp, col, s_rp, s_col)
+
+    ref, ref_flag = run((P, 1, 4, 0))
+    off = ~np.isnan(ref["ls"])
+    ref_w = dict(ls=ref["ls"], flag=ref_flag)
+    for nv in (1, 2, 4):
+        if P % nv:
+            continue
+        for u in (2, 4):
+            for summation in ("compensated", "plain"):
+                got, flag = run((P // nv, nv, u, 2), summation)
+                tol = 1e-12 if prec == "fp64" else 2e-5
+                rel = np.abs(got["ls"][off] - ref["ls"][off]) / np.maximum(ref["ls"][off], 1e-300)
+                assert rel.max() <= tol, (nv, u, summation, rel.max())
+                assert np.all(np.isnan(got["ls"][~off])) and np.all(got["a"][~off] == 0)
+                check_flags(flag, ref_w, rp, col, 0.5, 1e-4)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16"])
 def test_edge_batch_of_two(prec):
     """The distance pass also compiles a gather batch of 2 (both kernels):
