@@ -17,10 +17,13 @@ matrix, each with its own accuracy against the oracle.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config c1..c7]
                   [--precision bf16|fp32|fp64] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank builds its own copy of the workload on its
-own GPU (independent problems, no data exchange): weak scaling, rank 0
-prints the aggregate.  ``--impl reference`` times the FP64 CPU oracle on the
-host cores instead (rank 0 only).
+Under torchrun (N > 1) a single-matrix workload runs as an independent
+replica per rank (its own start-vector seed; weak scaling); the 64-matrix
+graph batch is split across the ranks -- every matrix keeps its key in the
+whole batch, so the union of the shards is the one-GPU build -- with no data
+exchange (strong scaling).  Rank 0 prints the aggregate.  ``--impl
+reference`` times the FP64 CPU oracle on the host cores instead (rank 0
+only).
 """
 from __future__ import annotations
 
@@ -246,8 +249,22 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+def shard_batch(nnz, world, rank):
+    """Global indices of the matrices of a batch that `rank` of `world` builds:
+    largest first, each to the rank with the fewest stored entries so far (ties:
+    the lower rank), returned ascending.  Deterministic, every matrix exactly
+    once."""
+    load = [0] * world
+    owner = [0] * len(nnz)
+    for b in sorted(range(len(nnz)), key=lambda b: (-nnz[b], b)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[b] = r
+        load[r] += nnz[b]
+    return [b for b in range(len(nnz)) if owner[b] == rank]
+
+
 def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_clocks=True,
-                tune_cache=None, summation="compensated"):
+                tune_cache=None, summation="compensated", matrix_ids=None):
     """One step = one captured build (or, for a workload with a checkpoint
     interval, one captured forward + reverse step)."""
     import torch
@@ -258,6 +275,8 @@ def run_gpu_arm(mats, color, w, precision, steps, warmup, rank, flush, want_cloc
         h = amgd.Handle(*mats[0], w["K"], w["seed"])
     else:
         h = amgd.Handle(None, None, None, w["K"], w["seed"], batch=mats)
+    if matrix_ids is not None:
+        h.set_matrix_ids(matrix_ids)      # this rank's share of a larger batch
     h.set_stream(stream)
     h.set_precision(precision)
     h.set_summation(summation)
@@ -366,7 +385,7 @@ def run_e2e(h, mats, w, sweep, steps, adjoint=None):
                 E_s=E_s)
 
 
-def oracle_step(oracle, rp, col, val, w, color, keep=None):
+def oracle_step(oracle, rp, col, val, w, color, keep=None, stream=0):
     """One step of the workload on the FP64 oracle: the strength build, or
     for a workload with a checkpoint interval the forward path and its
     reverse pass (the oracle keeps every iterate).  keep (a dict) receives
@@ -377,7 +396,7 @@ def oracle_step(oracle, rp, col, val, w, color, keep=None):
     else:
         b = oracle.build(rp, col, val, w["K"], w["seed"], w["nu"], w["omega"], w["theta"],
                          sweep=oracle.SWEEP_MCGS if w["sweep"] == "mcgs" else oracle.SWEEP_JACOBI,
-                         color=color, d=w.get("depth", 1))
+                         color=color, d=w.get("depth", 1), stream=stream)
         if keep is not None:
             keep.update(b)
         return len(b["pcol"]) - (len(rp) - 1)
@@ -511,7 +530,64 @@ def init_dist():
 # --------------------------------------------------------------------------
 # reference arm: the oracle on the host cores
 # --------------------------------------------------------------------------
+# the oracle as it stands (one build per process, single-threaded) on every
+# host core: a pool of spawned processes (never forked: the parent may hold a
+# CUDA context) each building whole samples of the workload
+_OW = None
+
+
+def _oracle_worker_init(cfg, w, scale):
+    global _OW
+    sys.path.insert(0, ROOT)
+    import oracle
+    oracle.build_lib()
+    mats, color = make_matrix(cfg, scale=scale)
+    _OW = (oracle, mats, color, w)
+
+
+def _oracle_worker_build(k):
+    oracle, mats, color, w = _OW
+    if len(mats) > 1:                       # a batch: one of its matrices per build, in turn
+        rp, col, val = mats[k % len(mats)]
+        ww = dict(w)
+        return oracle_step(oracle, rp, col, val, ww, color, stream=k % len(mats))
+    return sum(oracle_step(oracle, rp, col, val, w, color) for rp, col, val in mats)
+
+
+def reference_sample(cfg):
+    """(scale, description) of one step of the reference arm: the whole workload
+    where one oracle build takes seconds, else a stated part of it."""
+    if cfg in ("c1", "c2", "c3", "c5"):
+        return None, "full workload per step"
+    if cfg == "c6":
+        return 512, "512x512 sub-grid of the same operator per step"
+    return 8, "one matrix of the batch per step (the first 8 in turn)"
+
+
+def oracle_all_cores(cfg, w, builds, procs=None, warm=True):
+    """Throughput of `builds` oracle builds spread over `procs` spawned processes
+    (default: every host core).  Returns (edges/s, seconds, processes)."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    procs = max(1, min(procs, builds))
+    scale, _ = reference_sample(cfg)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs, initializer=_oracle_worker_init, initargs=(cfg, w, scale)) as pool:
+        if warm:
+            pool.map(_oracle_worker_build, range(procs), chunksize=1)     # untimed
+        t0 = time.perf_counter()
+        edges = sum(pool.map(_oracle_worker_build, range(builds), chunksize=1))
+        dt = time.perf_counter() - t0
+    return edges / dt, dt, procs
+
+
 def run_reference(args, cfg, w):
+    """Reference arm: the FP64 oracle (the plain CPU implementation written
+    from the paper; there is no other implementation) on the host cores.  A
+    step is one oracle build of the sample reference_sample() names -- for
+    the default 1024 x 1024 workload the whole workload, i.e. the same
+    config as the GPU arm; the steps run on every host core at once, one
+    single-threaded build per process."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -520,34 +596,17 @@ def run_reference(args, cfg, w):
     oracle.build_lib()
     if w.get("coarsen"):
         return run_reference_coarsen(args, cfg, w, ws)
-    if cfg in ("c2", "c6"):
-        mats, color = make_matrix(cfg, scale=256)
-        sample = "256x256 sub-grid of the same operator per step"
-    elif cfg == "c3":
-        mats, color = make_matrix(cfg, scale=32)
-        sample = "32^3 sub-problem of the same operator per step"
-    elif cfg == "c4":
-        mats, color = make_matrix(cfg, scale=1)
-        sample = "first matrix of the batch per step"
-    else:
-        mats, color = make_matrix(cfg)
-        sample = "full workload per step"
-    def step():
-        return sum(oracle_step(oracle, rp, col, val, w, color) for rp, col, val in mats)
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    edges = sum(step() for _ in range(args.steps))
-    dt = time.perf_counter() - t0
-    v = edges / dt
+    scale, sample = reference_sample(cfg)
+    v, dt, procs = oracle_all_cores(cfg, w, args.steps, warm=args.warmup > 0)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "config": cfg},
-            "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "config": {"workload": w["name"], "config": cfg, "same_config": scale is None},
+            "cpu_baseline": {"value": v, "unit": "edges/s", "cores": procs, "kind": "oracle",
+                             "sample": "%s; %d steps over %d single-threaded processes (one "
+                                       "per host core), warm-up build per process untimed"
+                                       % (sample, args.steps, procs)},
             "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -819,11 +878,21 @@ def main():
     import torch
     ws, rank, local = init_dist()
     torch.cuda.set_device(local)
-    w["seed"] += rank                     # independent start vectors per rank
     from paper_1106_5990_gb300 import amgd
     amgd.lib()
     precision = args.precision or w["precision"]
     mats, color = make_matrix(cfg, scale=args.scale)
+    # a batch of independent matrices is split across the ranks (each matrix keeps
+    # its key in the whole batch: the union of the shards is the one-GPU build);
+    # a single matrix runs as an independent replica per rank with its own seed
+    ids = None
+    if len(mats) > 1:
+        ids = shard_batch([len(m[1]) for m in mats], ws, rank)
+        mats = [mats[b] for b in ids]
+        scaling = "strong"
+    else:
+        w["seed"] += rank
+        scaling = "weak"
     n = sum(len(m[0]) - 1 for m in mats)
     nnz = sum(len(m[1]) for m in mats)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -831,7 +900,7 @@ def main():
         return run_coarsen(args, cfg, w, mats, color, precision, ws, rank, flush)
 
     r = run_gpu_arm(mats, color, w, precision, args.steps, args.warmup, rank, flush,
-                    tune_cache=args.tune_cache)
+                    tune_cache=args.tune_cache, matrix_ids=ids)
     depth = w.get("depth", 1)
     nnz_p = r["h"].nnz_p                       # entries of the fit pattern (A, or G_d)
     E = r["h"].E_p                             # edges whose distance the step computes
@@ -882,7 +951,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": scaling, "vs_baseline": None,
             "dtype": "f64" if precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": w["name"], "config": cfg, "n": n, "nnz": nnz, "E": E,
                        "search_depth": depth, "nnz_pattern": nnz_p,
@@ -927,7 +996,7 @@ def main():
     if not args.no_side and precision != "fp64":
         side_steps = max(3, min(args.steps, 100))
         r64 = run_gpu_arm(mats, color, w, "fp64", side_steps, 3, rank, flush, want_clocks=False,
-                          tune_cache=args.tune_cache)
+                          tune_cache=args.tune_cache, matrix_ids=ids)
         v64, t64 = whole_job(float(r64["step_ms"].sum()), E, side_steps)
         ab64 = step_bytes(r64, "fp64")
         rl = r64["phase_ms"][1] / launches_relax
@@ -945,7 +1014,8 @@ def main():
     if not args.no_side and mixed and not adj and depth == 1:
         side_steps = max(3, min(args.steps, 100))
         r_p = run_gpu_arm(mats, color, w, precision, side_steps, 3, rank, flush,
-                          want_clocks=False, tune_cache=args.tune_cache, summation="plain")
+                          want_clocks=False, tune_cache=args.tune_cache, summation="plain",
+                          matrix_ids=ids)
         v_p, t_p = whole_job(float(r_p["step_ms"].sum()), E, side_steps)
         line["plain_ls_sums"] = {"value": v_p, "unit": "edges/s", "ms_per_step": t_p,
                                  "steps": side_steps,
@@ -963,7 +1033,7 @@ def main():
     if not args.no_side and other is not None and not adj:
         side_steps = max(3, min(args.steps, 100))
         r_o = run_gpu_arm(mats, color, w, other, side_steps, 3, rank, flush, want_clocks=False,
-                          tune_cache=args.tune_cache)
+                          tune_cache=args.tune_cache, matrix_ids=ids)
         v_o, t_o = whole_job(float(r_o["step_ms"].sum()), E, side_steps)
         ab_o = step_bytes(r_o, other)
         rl_o = r_o["phase_ms"][1] / launches_relax
@@ -992,6 +1062,13 @@ def main():
     if rank == 0 and not args.no_cpu:
         ref = {}
         line["cpu_baseline"] = cpu_oracle_time(cfg, w, keep=ref)
+        # the same oracle on every host core (independent builds, one per process)
+        procs = os.cpu_count() or 1
+        v_all, dt_all, procs = oracle_all_cores(cfg, w, procs, procs)
+        line["cpu_baseline_all_cores"] = {
+            "value": v_all, "unit": "edges/s", "cores": procs, "kind": "oracle",
+            "sample": "%s; %d builds at once, one single-threaded process per host core, "
+                      "%.1f s" % (reference_sample(cfg)[1], procs, dt_all)}
         if ref and not args.scale:
             line["accuracy"] = accuracy_vs_oracle(r["h"], mats[0], ref, w["theta"])
             if r_o is not None:

@@ -113,6 +113,20 @@ int amgd_create_batch(int32_t nmat, const int64_t *const *row_ptr, const int32_t
                       const double *const *val, const int64_t *n, int32_t K, uint64_t seed,
                       int mem, amgd_handle *out);
 
+/*
+ * amgd_set_matrix_ids -- Philox key word 1 of the start vectors of each
+ *   matrix of the handle: ids[nmat] (host, each >= 0; NULL restores the
+ *   default, matrix b keyed b).  A process that builds a subset of a larger
+ *   batch (one shard of its matrices, e.g. one GPU's share) passes the
+ *   matrices' indices in the whole batch, so every matrix gets the same
+ *   start vectors -- hence the same results bit for bit -- as in a build of
+ *   the whole batch.  Takes effect at the next amgd_init_vectors or capture;
+ *   synchronises the handle's stream and drops a captured graph.  The paper
+ *   has no counterpart (it is the sharding of independent problems).
+ *   Errors: ARG, STATE, OOM, CUDA.
+ */
+int amgd_set_matrix_ids(amgd_handle h, const int64_t *ids);
+
 /* Row offsets (nmat+1) and CSR-slot offsets (nmat+1) of the matrices of a
  * batch handle, written to host arrays; a single-matrix handle has nmat 1. */
 int amgd_batch_offsets(amgd_handle h, int64_t *row_off, int64_t *slot_off);
@@ -143,11 +157,10 @@ int amgd_set_target(amgd_handle h, int target);
  *   row combine their pairs with TwoSum in the shuffle reduction, and the two
  *   words are added once at the end.  AMGD_SUM_PLAIN: FP32 fused
  *   multiply-add chains.  Either way an edge whose LS falls below 1e-4 of
- *   sum_k w_k y_k^2 makes its row be redone in FP64 (cancellation).  The
- *   compensated form is computed by the distance kernel that reads the
- *   sweeps' row order (edge stage 2, search depth 1); with a search depth
- *   d > 1 the distance pass sums plainly.  The FP64 path ignores the
- *   setting.  Drops computed distances and a captured graph.
+ *   sum_k w_k y_k^2 makes its row be redone in FP64 (cancellation).  Every
+ *   distance kernel (each edge stage, any search depth) honours the
+ *   setting; the FP64 path ignores it.  Drops computed distances and a
+ *   captured graph.
  *   Errors: ARG.
  */
 int amgd_set_summation(amgd_handle h, int mode);
@@ -310,8 +323,7 @@ int amgd_graph_launch(amgd_handle h);
  *   kernel (G lanes per row), 1 the tile kernel (one thread per stored
  *   entry) or 2 the row kernel reading the vectors in the sweeps' row
  *   order in place (search depth 1: no caller-order copy of the vectors;
- *   the only kernel with compensated sums on the mixed paths; U in {2,4};
- *   the default).  With search depth d > 1 a stage-2 shape runs
+ *   U in {2,4}; the default).  With search depth d > 1 a stage-2 shape runs
  *   as stage 0.  Shapes change speed only, never results beyond the order of
  *   the K-term LS sums.  kernel: AMGD_KERNEL_RELAX (the sweeps) or
  *   AMGD_KERNEL_EDGE (the distance pass); the shape applies to the current

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libamgd.so")
 SOURCES = ["amgd_api.cu", "k_relax.cu", "k_edge.cu", "k_edge_f64.cu", "k_edge_f32.cu",
-           "k_edge_bf16.cu", "k_init.cu", "k_compact.cu",
+           "k_edge_f32c.cu", "k_edge_bf16.cu", "k_edge_bf16c.cu", "k_init.cu", "k_compact.cu",
            "amgd_noalloc.cu", "k_adjoint.cu", "k_interp.cu", "k_cr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

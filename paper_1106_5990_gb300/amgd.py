@@ -61,6 +61,7 @@ SIGNATURES = {
     "amgd_set_precision": (_int, [_P, _int]),
     "amgd_set_target": (_int, [_P, _int]),
     "amgd_set_summation": (_int, [_P, _int]),
+    "amgd_set_matrix_ids": (_int, [_P, _P]),
     "amgd_set_weights": (_int, [_P, _P]),
     "amgd_set_coloring": (_int, [_P, _P, _i32, _int]),
     "amgd_init_vectors": (_int, [_P, _u64]),
@@ -294,6 +295,17 @@ class Handle:
 
     def set_target(self, target):
         self._ck(lib().amgd_set_target(self.h, target))
+
+    def set_matrix_ids(self, ids):
+        """Philox key word 1 of each matrix's start vectors (its index in a larger
+        batch that this handle is one shard of); None restores 0..nmat-1."""
+        if ids is None:
+            self._ck(lib().amgd_set_matrix_ids(self.h, None))
+            return
+        a = np.ascontiguousarray(ids, dtype=np.int64)
+        if a.shape != (self.nmat,):
+            raise ValueError("set_matrix_ids: need %d ids" % self.nmat)
+        self._ck(lib().amgd_set_matrix_ids(self.h, a.ctypes.data))
 
     def set_summation(self, mode):
         """AMGD_SUM_COMPENSATED (default) or AMGD_SUM_PLAIN, or "compensated" / "plain"."""

@@ -48,6 +48,7 @@ struct amgd_ctx {
     double *diag64_o = nullptr;                  // caller-order diagonal (edge pass)
     float *diag32_o = nullptr;
     void *x_caller = nullptr;                    // caller-order copy of permuted vectors
+    int64_t *mat_id = nullptr;                   // Philox key word 1 per matrix (NULL: index)
     int32_t *pinv = nullptr;                     // caller row -> permuted row
     int32_t *colx = nullptr;                     // caller CSR, columns in permuted numbering
     uint32_t *defer_count = nullptr;             // rows the mixed edge pass redoes in FP64
@@ -344,6 +345,7 @@ int run_init(amgd_ctx *h, uint64_t seed, cudaStream_t s)
     a.x = h->x[h->cur];
     a.perm = h->perm;
     a.mat_off = h->mat_off;
+    a.mat_id = h->mat_id;
     a.nmat = h->nmat;
     a.n = (int32_t)h->n;
     a.K = h->K;
@@ -902,6 +904,25 @@ int amgd_set_coloring(amgd_handle h, const int32_t *color, int32_t ncolors, int 
     return AMGD_OK;
 }
 
+int amgd_set_matrix_ids(amgd_handle h, const int64_t *ids)
+{
+    AMGD_RANGE("amgd_set_matrix_ids");
+    if (!h) return AMGD_ERR_ARG;
+    if (h->async_pending) return fail(h, AMGD_ERR_STATE, "asynchronous work pending: call amgd_sync first");
+    CK(h, cudaStreamSynchronize(h->stream));
+    drop_graph(h);                       // a captured start uses the old keys
+    if (!ids) {
+        dfree(h->mat_id);
+        h->mat_id = nullptr;
+        return AMGD_OK;
+    }
+    for (int32_t b = 0; b < h->nmat; ++b)
+        if (ids[b] < 0) return fail(h, AMGD_ERR_ARG, "matrix id < 0");
+    if (!h->mat_id) CK(h, dalloc(&h->mat_id, (size_t)h->nmat));
+    CK(h, cudaMemcpy(h->mat_id, ids, (size_t)h->nmat * sizeof(int64_t), cudaMemcpyHostToDevice));
+    return AMGD_OK;
+}
+
 int amgd_init_vectors(amgd_handle h, uint64_t seed)
 {
     AMGD_RANGE("amgd_init_vectors");
@@ -1374,17 +1395,14 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
             if (prc != AMGD_OK) { h->relax_shape[h->storage] = keep_r; return prc; }
         }
     }
-    // edge pass: stage 0 row kernel, stage 1 tile kernel, stage 2 the sweeps'
-    // row order (search depth 1).  With compensated sums on a mixed path only
-    // stage 2 is a candidate: it is the kernel that sums with compensation.
-    const bool comp_only = h->storage != ST_FP64 && h->summation == AMGD_SUM_COMPENSATED &&
-                           h->depth == 1;
+    // edge pass: stage 0 row kernel, stage 1 tile kernel, stage 2 the row
+    // kernel on the sweeps' row order (search depth 1)
     for (int stage : {0, 1, 2})
         for (int NV : {1, 2, 4})
             for (int U : {2, 4, 8}) {
                 const Shape c{P / NV, NV, U, stage};
                 if (P % NV != 0 || !shape_ok(h->storage, h->K, c) || !edge_shape_ok(c)) continue;
-                if ((stage == 2) != comp_only && (comp_only || h->depth > 1)) continue;
+                if (stage == 2 && h->depth > 1) continue;
                 float ms = 0.f;
                 h->edge_shape[h->storage] = c;
                 const int rc = time_ms(h, [&]() { return run_edge(h, 0.5, h->stream); }, 5, ms);
@@ -2099,6 +2117,7 @@ int amgd_destroy(amgd_handle h)
         dfree(h->pinv);
         dfree(h->colx);
     }
+    dfree(h->mat_id);
     if (h->depth > 1) {
         dfree(h->prp);
         dfree(h->pcol);

@@ -206,6 +206,7 @@ struct InitArgs {
     void *x;                   // n x Kp, permuted rows
     const int32_t *perm;       // permuted row -> caller row (NULL = identity)
     const int64_t *mat_off;    // nmat+1 caller-row offsets of the batch
+    const int64_t *mat_id;     // Philox key word 1 of each matrix (NULL: its index)
     int32_t nmat, n, K, Kp;
     uint64_t seed;
 };

@@ -14,18 +14,21 @@
 //        of S_yy - a S_yx; an error in a_ij enters LS only to second order)
 //      A residual-target row with one off-diagonal has y_i proportional to
 //      x_j exactly: a = -a_ij/a_ii, LS = 0.
-//      Mixed precisions (FP32 arithmetic on FP32/BF16 vectors): a row with
-//      an edge of LS < 1e-4 S_yy is recomputed in FP64 (k_edge_fixup), with
-//      y_i rebuilt from the FP64 values of A, so cancellation never decides
-//      a distance.
+//      Mixed precisions (FP32 arithmetic on FP32/BF16 vectors): the three
+//      sums are compensated (AMGD_SUM_COMPENSATED, below) or plain FMA
+//      chains; a row with an edge of LS < 1e-4 S_yy is recomputed in FP64
+//      (k_edge_fixup), with y_i rebuilt from the FP64 values of A, so
+//      cancellation never decides a distance.
 //   3. m_i = min_p LS_ip; slot p is strong iff LS_p = 0 or theta LS_p < m_i
 //      (§4.2, Eq. (4.4), r = 1/LS); per-row strong count.
-// The pass runs on the caller's numbering (a row-permuted vector block is
-// copied back first), so every output lands where the caller expects it.
-// Two kernels compute the same thing (the edge shape's stage selects one;
-// the autotuner times both): k_edge_rows, G lanes per row through all
-// steps; k_edge_tiles, rows cut into tiles with one thread per stored entry
-// for the fits.
+// The pass works in the caller's numbering, so every output lands where the
+// caller expects it.  Its kernels compute the same thing (the edge shape's
+// stage selects one; the autotuner times them): stage 0, k_edge_rows, G
+// lanes per row through all steps, on a caller-order copy of a row-permuted
+// vector block; stage 1, k_edge_tiles, rows cut into tiles with one thread
+// per stored entry for the fits, on the same copy; stage 2, k_edge_rows
+// reading the permuted block in place through renumbered column indices
+// (no copy; search depth 1).
 #pragma once
 #include <type_traits>
 
@@ -478,7 +481,7 @@ struct EdgeTileLayout {
     static constexpr int BYTES = SR + kEdgeTileSlots;
 };
 
-template <class TS, int G, int NV, int U, bool UW>
+template <class TS, int G, int NV, int U, bool UW, bool COMP>
 __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
 {
     using S = Store<TS>;
@@ -588,6 +591,44 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
         } else if (j == j1s[rl]) {
             a_ = -v1s[rl] / dg[rl];                     // y_i = -(a_ij/a_ii) x_j exactly
             ls_ = C(0);
+        } else if constexpr (COMP && kMixed) {
+            // compensated sums over all K components in this thread
+            const TS *xj = X + (int64_t)j * KP;
+            const C *yr = ys + rl * KP;
+            uint4 hold[HOLD];
+            Comp2 sx;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                const uint4 raw = ldg16(xj + c * V);
+                if constexpr (P <= 4) hold[c] = raw;
+                C x[V], y[V], w[V];
+                S::unpack(raw, x);
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    y[e] = yr[c * V + e];
+                    w[e] = UW ? C(1) : wv[c * V + e];
+                }
+                comp_piece_sums<V, UW>(x, y, w, sx);
+            }
+            const C sxx = sx.s.x + sx.c.x, syx = sx.s.y + sx.c.y;
+            a_ = (sxx == C(0)) ? C(0) : divide(syx, sxx);
+            Comp2 sl;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                uint4 raw;
+                if constexpr (P <= 4) raw = hold[c];
+                else raw = ldg16(xj + c * V);
+                C x[V], y[V], w[V];
+                S::unpack(raw, x);
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    y[e] = yr[c * V + e];
+                    w[e] = UW ? C(1) : wv[c * V + e];
+                }
+                comp_residual<V, UW>(a_, x, y, w, sl);
+            }
+            ls_ = comp_ls_total<1>(sl, 0xffffffffu);
+            if (ls_ < C(1e-4) * syy[rl]) dfr[rl] = 1;        // cancellation: redo the row in FP64
         } else {
             const TS *xj = X + (int64_t)j * KP;
             const C *yr = ys + rl * KP;
@@ -771,77 +812,76 @@ cudaError_t go_rows(const EdgeArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <class TS, int G, int NV, int U, bool UW>
+template <class TS, int G, int NV, int U, bool UW, bool COMP>
+cudaError_t go_tiles(const EdgeArgs &a, cudaStream_t s)
+{
+    constexpr int KP = G * NV * Store<TS>::V;
+    if (a.Kp != KP || a.ntiles <= 0) return cudaErrorInvalidValue;
+    constexpr int smem = EdgeTileLayout<TS, KP>::BYTES;
+    static PerDevice opted;                  // shared-memory opt-in made on each device
+    const int dev = current_device_index();
+    if (smem > 48 * 1024 && opted.get(dev) == 0) {
+        const cudaError_t e = cudaFuncSetAttribute(k_edge_tiles<TS, G, NV, U, UW, COMP>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        opted.set(dev, 1);
+    }
+    k_edge_tiles<TS, G, NV, U, UW, COMP><<<(unsigned)a.ntiles, kEdgeThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// one storage type and summation form; the plain and the compensated forms
+// are instantiated in separate translation units (parallel compilation)
+template <class TS, bool COMP, int G, int NV, int U, bool UW>
 cudaError_t go(int stage, const EdgeArgs &a, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;
-    if (stage == 1) {
-        constexpr int KP = G * NV * Store<TS>::V;
-        if (a.Kp != KP || a.ntiles <= 0) return cudaErrorInvalidValue;
-        constexpr int smem = EdgeTileLayout<TS, KP>::BYTES;
-        static PerDevice opted;              // shared-memory opt-in made on each device
-        const int dev = current_device_index();
-        if (smem > 48 * 1024 && opted.get(dev) == 0) {
-            const cudaError_t e = cudaFuncSetAttribute(k_edge_tiles<TS, G, NV, U, UW>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       smem);
-            if (e != cudaSuccess) return e;
-            opted.set(dev, 1);
-        }
-        k_edge_tiles<TS, G, NV, U, UW><<<(unsigned)a.ntiles, kEdgeThreads, smem, s>>>(a);
-        return cudaGetLastError();
-    }
-    if (stage == 2) {
-        if constexpr (std::is_same<typename Store<TS>::C, double>::value)
-            return go_rows<TS, G, NV, U, UW, true, false>(a, s);
-        else
-            return a.compensated ? go_rows<TS, G, NV, U, UW, true, true>(a, s)
-                                 : go_rows<TS, G, NV, U, UW, true, false>(a, s);
-    }
-    return go_rows<TS, G, NV, U, UW, false, false>(a, s);
+    if (stage == 1) return go_tiles<TS, G, NV, U, UW, COMP>(a, s);
+    if (stage == 2) return go_rows<TS, G, NV, U, UW, true, COMP>(a, s);
+    return go_rows<TS, G, NV, U, UW, false, COMP>(a, s);
 }
 
-template <class TS, int G, int NV, bool UW>
+template <class TS, bool COMP, int G, int NV, bool UW>
 cudaError_t dispatch_u(int stage, int U, const EdgeArgs &a, cudaStream_t s)
 {
     switch (U) {
-    case 2: return go<TS, G, NV, 2, UW>(stage, a, s);
-    case 4: return go<TS, G, NV, 4, UW>(stage, a, s);
-    case 8: return go<TS, G, NV, 8, UW>(stage, a, s);
+    case 2: return go<TS, COMP, G, NV, 2, UW>(stage, a, s);
+    case 4: return go<TS, COMP, G, NV, 4, UW>(stage, a, s);
+    case 8: return go<TS, COMP, G, NV, 8, UW>(stage, a, s);
     }
     return cudaErrorInvalidValue;
 }
 
-template <class TS, int G, int NV>
+template <class TS, bool COMP, int G, int NV>
 cudaError_t dispatch_w(int stage, int U, bool unit_w, const EdgeArgs &a, cudaStream_t s)
 {
-    return unit_w ? dispatch_u<TS, G, NV, true>(stage, U, a, s)
-                  : dispatch_u<TS, G, NV, false>(stage, U, a, s);
+    return unit_w ? dispatch_u<TS, COMP, G, NV, true>(stage, U, a, s)
+                  : dispatch_u<TS, COMP, G, NV, false>(stage, U, a, s);
 }
 
-template <class TS, int G>
+template <class TS, bool COMP, int G>
 cudaError_t dispatch_nv(int stage, int NV, int U, bool unit_w, const EdgeArgs &a, cudaStream_t s)
 {
     constexpr int V = Store<TS>::V;
     switch (NV) {
-    case 1: return dispatch_w<TS, G, 1>(stage, U, unit_w, a, s);
-    case 2: if constexpr (G * 2 * V <= 64) return dispatch_w<TS, G, 2>(stage, U, unit_w, a, s); break;
-    case 4: if constexpr (G * 4 * V <= 64) return dispatch_w<TS, G, 4>(stage, U, unit_w, a, s); break;
+    case 1: return dispatch_w<TS, COMP, G, 1>(stage, U, unit_w, a, s);
+    case 2: if constexpr (G * 2 * V <= 64) return dispatch_w<TS, COMP, G, 2>(stage, U, unit_w, a, s); break;
+    case 4: if constexpr (G * 4 * V <= 64) return dispatch_w<TS, COMP, G, 4>(stage, U, unit_w, a, s); break;
     }
     return cudaErrorInvalidValue;
 }
 
-template <class TS>
+template <class TS, bool COMP>
 cudaError_t dispatch_g(Shape sh, bool unit_w, const EdgeArgs &a, cudaStream_t s)
 {
     constexpr int V = Store<TS>::V;
     switch (sh.G) {
-    case 1: return dispatch_nv<TS, 1>(sh.stage, sh.NV, sh.U, unit_w, a, s);
-    case 2: return dispatch_nv<TS, 2>(sh.stage, sh.NV, sh.U, unit_w, a, s);
-    case 4: return dispatch_nv<TS, 4>(sh.stage, sh.NV, sh.U, unit_w, a, s);
-    case 8: if constexpr (8 * V <= 64) return dispatch_nv<TS, 8>(sh.stage, sh.NV, sh.U, unit_w, a, s); break;
-    case 16: if constexpr (16 * V <= 64) return dispatch_nv<TS, 16>(sh.stage, sh.NV, sh.U, unit_w, a, s); break;
-    case 32: if constexpr (32 * V <= 64) return dispatch_nv<TS, 32>(sh.stage, sh.NV, sh.U, unit_w, a, s); break;
+    case 1: return dispatch_nv<TS, COMP, 1>(sh.stage, sh.NV, sh.U, unit_w, a, s);
+    case 2: return dispatch_nv<TS, COMP, 2>(sh.stage, sh.NV, sh.U, unit_w, a, s);
+    case 4: return dispatch_nv<TS, COMP, 4>(sh.stage, sh.NV, sh.U, unit_w, a, s);
+    case 8: if constexpr (8 * V <= 64) return dispatch_nv<TS, COMP, 8>(sh.stage, sh.NV, sh.U, unit_w, a, s); break;
+    case 16: if constexpr (16 * V <= 64) return dispatch_nv<TS, COMP, 16>(sh.stage, sh.NV, sh.U, unit_w, a, s); break;
+    case 32: if constexpr (32 * V <= 64) return dispatch_nv<TS, COMP, 32>(sh.stage, sh.NV, sh.U, unit_w, a, s); break;
     }
     return cudaErrorInvalidValue;
 }

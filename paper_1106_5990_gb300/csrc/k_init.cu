@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(kThreads) k_tv_init(InitArgs A, int lq)
         if (A.mat_off[mid] <= o) lo = mid; else hi = mid;
     }
     const uint64_t li = (uint64_t)(o - A.mat_off[lo]);
-    const U64x4 u = philox4x64_10(li, (uint64_t)q, 0ull, 0ull, A.seed, (uint64_t)lo);
+    const uint64_t key1 = A.mat_id ? (uint64_t)A.mat_id[lo] : (uint64_t)lo;
+    const U64x4 u = philox4x64_10(li, (uint64_t)q, 0ull, 0ull, A.seed, key1);
     typename SB::Raw v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {

@@ -546,6 +546,37 @@ def test_kernel_shapes_agree(prec, K):
             h.set_kernel_shape(amgd.AMGD_KERNEL_RELAX, 3, 1, 4)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_batch_shard_keys(prec):
+    """A handle over a subset of a batch, keyed by the matrices' indices in the
+    whole batch (amgd_set_matrix_ids), reproduces the whole batch's vectors and
+    distances of those matrices bit for bit: the one-GPU share of a batch split
+    across GPUs."""
+    mats = [inputs.graph_laplacian(n, 4.0, 5, b) for b, n in enumerate([700, 2222, 99, 1500, 333])]
+    K, seed = 16, 6
+    with amgd.Handle(None, None, None, K, seed, batch=mats) as h:
+        h.set_precision(prec)
+        h.init_vectors(seed)
+        h.relax(3, 2.0 / 3.0)
+        Xa = h.get_vectors()
+        full = h.distances(0.5)
+        ro, so = h.offsets()
+    ids = [3, 1, 4]
+    with amgd.Handle(None, None, None, K, seed, batch=[mats[b] for b in ids]) as h:
+        h.set_matrix_ids(ids)
+        h.set_precision(prec)
+        h.init_vectors(seed)
+        h.relax(3, 2.0 / 3.0)
+        Xs = h.get_vectors()
+        part = h.distances(0.5)
+        ro_s, so_s = h.offsets()
+    for k, b in enumerate(ids):
+        assert np.array_equal(Xs[ro_s[k]:ro_s[k + 1]], Xa[ro[b]:ro[b + 1]]), b
+        assert np.array_equal(part["ls"][so_s[k]:so_s[k + 1]], full["ls"][so[b]:so[b + 1]],
+                              equal_nan=True), b
+        assert np.array_equal(part["a"][so_s[k]:so_s[k + 1]], full["a"][so[b]:so[b + 1]]), b
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 @pytest.mark.parametrize("K", [5, 16, 64])
 def test_edge_stage2_shapes_agree(prec, K):
