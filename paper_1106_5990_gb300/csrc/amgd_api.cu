@@ -1861,14 +1861,14 @@ namespace {
 // device buffers of the reverse pass (allocated before any capture)
 int prepare_backward(amgd_ctx *h)
 {
-    const size_t cs = h->storage == ST_FP64 ? 8 : 4;
+    const size_t cs = 8;                 // the reverse pass computes in FP64
     const size_t nk = (size_t)h->n * Kp_of(h->storage, h->K);
     const size_t xb = nk * esize(h->storage);
     const int32_t S = h->ckpt_every > 0 ? h->ckpt_every : 1;
     int rc = ensure_transpose(h);
     if (rc != AMGD_OK) return rc;
     CK(h, ensure_buf(&h->adj_vec, h->adj_vec_bytes, 4 * nk * cs));
-    CK(h, ensure_buf(&h->adj_slot, h->adj_slot_bytes, 4 * (size_t)(h->nnz ? h->nnz : 1) * cs));
+    CK(h, ensure_buf(&h->adj_slot, h->adj_slot_bytes, 6 * (size_t)(h->nnz ? h->nnz : 1) * cs));
     CK(h, ensure_buf(&h->seg, h->seg_bytes, (size_t)(S - 1) * xb));
     if (!h->lsb) CK(h, dalloc(&h->lsb, (size_t)(h->nnz ? h->nnz : 1)));
     if (!h->adj_part) CK(h, dalloc(&h->adj_part, (size_t)2 * kAdjReduceBlocks + 2));
@@ -1885,7 +1885,7 @@ int run_backward(amgd_ctx *h, const double *lsb_in, double *vb, cudaStream_t s)
     const int32_t n = (int32_t)h->n;
     const int64_t nnz = h->nnz;
     const int Kp = Kp_of(st, h->K);
-    const size_t cs = st == ST_FP64 ? 8 : 4;
+    const size_t cs = 8;                 // FP64 reverse pass
     const size_t nk = (size_t)n * Kp;
     const size_t xb = nk * esize(st);
     const int32_t S = h->ckpt_every > 0 ? h->ckpt_every : 1;
@@ -1897,27 +1897,35 @@ int run_backward(amgd_ctx *h, const double *lsb_in, double *vb, cudaStream_t s)
     char *slots = (char *)h->adj_slot;
     void *gs = slots, *gt = slots + nnz * cs, *at_b = slots + 2 * nnz * cs;
     void *bm = slots + 3 * nnz * cs;
-
-    CK(h, launch_adj_upstream(st, h->rp_o, h->col_o, h->ls, h->flag, lsb_in, h->lsb, h->adj_part,
-                              nb, n, h->target, s));
-    CK(h, launch_adj_bvals(st, h->val_o, h->diag64_o, h->at_row, h->at_slot, at_b, nnz, s));
-    if (h->mirror)   // per slot (j, i): a_ij / a_ii, the mirror entry over its row's diagonal
-        CK(h, launch_adj_bvals(st, h->val_o, h->diag64_o, h->col_o, h->mirror, bm, nnz, s));
+    double *a64 = (double *)(slots + 4 * nnz * cs), *ls64 = (double *)(slots + 5 * nnz * cs);
 
     AdjArgs a;
     a.rp = h->rp_o;
     a.col = h->col_o;
-    a.val = st == ST_FP64 ? (const void *)h->val_o : (const void *)h->val32_o;
-    a.diag = st == ST_FP64 ? (const void *)h->diag64_o : (const void *)h->diag32_o;
+    a.val = h->val_o;                    // FP64 values, diagonal and weights
+    a.diag = h->diag64_o;
     a.at_rp = h->at_rp;
     a.at_row = h->at_row;
     a.at_slot = h->at_slot;
     a.at_b = at_b;
     a.bm = h->mirror ? bm : nullptr;
     a.x = h->x[h->cur];
-    a.w = st == ST_FP64 ? (const void *)h->w64 : (const void *)h->w32;
-    a.a = h->a;
+    a.w = h->w64;
+    a.a = a64;
+    a.a_fit = a64;
+    a.ls64 = ls64;
     a.lsb = h->lsb;
+    a.n = n;
+    a.Kp = Kp;
+    a.target = h->target;
+    // the fits of X_nu in FP64 (the forward pass's own a and LS may be FP32)
+    CK(h, launch_adj_refit(st, a, s));
+    CK(h, launch_adj_upstream(st, h->rp_o, h->col_o, ls64, h->flag, lsb_in, h->lsb, h->adj_part,
+                              nb, n, h->target, s));
+    CK(h, launch_adj_bvals(st, h->val_o, h->diag64_o, h->at_row, h->at_slot, at_b, nnz, s));
+    if (h->mirror)   // per slot (j, i): a_ij / a_ii, the mirror entry over its row's diagonal
+        CK(h, launch_adj_bvals(st, h->val_o, h->diag64_o, h->col_o, h->mirror, bm, nnz, s));
+
     a.y = Y;
     a.ybar = Ybar;
     a.xbar_in = nullptr;

@@ -268,8 +268,8 @@ cudaError_t launch_strength(const int32_t *count, const int32_t *rp_orig, const 
 
 // ---------------------------------------------------------------------------
 // reverse pass (Jacobi sweeps); every array in the caller's numbering, vector
-// blocks n x Kp row-major, "C" = arithmetic type of the storage (double for
-// FP64 storage, float otherwise)
+// blocks n x Kp row-major; "C" = FP64 (the reverse pass computes in FP64 for
+// every storage of the test vectors)
 // ---------------------------------------------------------------------------
 struct AdjArgs {
     const int32_t *rp, *col;          // CSR pattern of A
@@ -280,7 +280,9 @@ struct AdjArgs {
     const void *bm;                   // symmetric pattern: per slot (j, i) a_ij / a_ii, C (else NULL)
     const void *x;                    // storage type: X_nu (edge stages) or X_k (sweeps)
     const void *w;                    // LS weights, Kp, C
-    const void *a;                    // forward fit coefficients per slot, C
+    const void *a;                    // fit coefficients per slot (FP64, from k_refit)
+    void *a_fit;                      // k_refit's output: a per slot (FP64)
+    double *ls64;                     // k_refit's output: LS per slot (FP64)
     const double *lsb;                // dL/dLS per slot (0 where no gradient flows)
     void *y, *ybar;                   // target Y and its adjoint, C
     const void *xbar_in;              // C
@@ -301,6 +303,8 @@ cudaError_t launch_adj_upstream(int storage, const int32_t *rp, const int32_t *c
 cudaError_t launch_adj_bvals(int storage, const double *val64, const double *diag64,
                              const int32_t *at_row, const int32_t *at_slot, void *at_b,
                              int64_t nnz, cudaStream_t s);
+// a and LS of every slot refitted in FP64 from the stored X_nu
+cudaError_t launch_adj_refit(int storage, const AdjArgs &a, cudaStream_t s);
 // Y, Ybar and (residual target) gt from the fits
 cudaError_t launch_adj_edge(int storage, const AdjArgs &a, cudaStream_t s);
 // Xbar_nu = direct part of the fits + the target's adjoint, per column

@@ -19,9 +19,19 @@
 // pattern whose entries are in ascending row order, so every sum has a fixed
 // order and the result is deterministic (no atomics anywhere).
 //
+// Arithmetic.  The target, the fits (a_ij and LS_ij refitted in FP64 from the
+// stored X_nu, k_refit), Y, Ybar, the last sweep's Xbar_nu and every per-slot
+// sum (gs, gt) are FP64 whatever the storage: the loss weights each fit by
+// LS^-3, so the fits must be exact to the digits the gradient needs.  The
+// backward sweeps themselves (Xbar_k = Xbar_{k+1} - omega (D^-1 A)^T Xbar_{k+1}
+// and the inner products <Xbar_{k+1,i}, X_k,j>) run in the arithmetic type of
+// the storage ("CS": FP64 for FP64 storage, FP32 otherwise), a well-conditioned
+// linear recurrence, their inner products accumulated over the sweeps in FP64.
+// The stored iterates are widened exactly.
+//
 // Lane layout as in the forward kernels: G lanes per row, one 16-byte vector
-// of the stored block per lane (V components); vectors in the arithmetic
-// type C (Y, Ybar, Xbar) use the same components per lane.
+// of the stored block per lane (V components); the FP64 vectors (Y, Ybar,
+// Xbar) use the same components per lane.
 #include "amgd_internal.cuh"
 #include "rowops.cuh"
 
@@ -84,6 +94,53 @@ __device__ __forceinline__ void stc(C *p, const C (&x)[V])
         for (int c = 0; c < V / 4; ++c)
             reinterpret_cast<float4 *>(p)[c] = make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
     }
+}
+
+// V stored components of one 16-byte vector, widened exactly to FP64
+template <class TS, int V>
+__device__ __forceinline__ void unpack64(const uint4 &raw, double (&x)[V])
+{
+    typename Store<TS>::C t[V];
+    Store<TS>::unpack(raw, t);
+#pragma unroll
+    for (int e = 0; e < V; ++e) x[e] = (double)t[e];
+}
+
+// y_i = x_i - (1/a_ii) sum_p a_ip x_col_p (one FMA per term in CSR order) or
+// y_i = x_i: this lane's V components, FP64
+template <class TS, int V>
+__device__ __forceinline__ void target64(const AdjArgs &A, int64_t r, int lane, int p0, int p1,
+                                         double (&y)[V])
+{
+    const TS *__restrict__ X = (const TS *)A.x;
+    const int Kp = A.Kp;
+    unpack64<TS, V>(ldg16(X + r * Kp + lane * V), y);
+    if (A.target != 0) return;
+    const double *__restrict__ val = (const double *)A.val;
+    double acc[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) acc[e] = 0.0;
+    for (int pb = p0; pb < p1; pb += 4) {
+        uint4 raw[4];
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (pb + u < p1) {
+                raw[u] = ldg16(X + (int64_t)__ldg(A.col + pb + u) * Kp + lane * V);
+                v[u] = __ldg(val + pb + u);
+            }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (pb + u >= p1) break;
+            double x[V];
+            unpack64<TS, V>(raw[u], x);
+#pragma unroll
+            for (int e = 0; e < V; ++e) acc[e] = fma(v[u], x[e], acc[e]);
+        }
+    }
+    const double d = 1.0 / __ldg((const double *)A.diag + r);
+#pragma unroll
+    for (int e = 0; e < V; ++e) y[e] = fma(-d, acc[e], y[e]);
 }
 
 // fixed-order block sum of one double per thread (result valid in thread 0)
@@ -150,6 +207,68 @@ k_bvals(const double *__restrict__ val, const double *__restrict__ diag,
 }
 
 // ---------------------------------------------------------------------------
+// the one-point fits of every slot of row i refitted in FP64 from the stored
+// X_nu (§4.1, Eq. (4.3)): a_p = S_yx / S_xx (0 if S_xx = 0), LS_p = sum w (y_i -
+// a_p x_j)^2 (two passes); the exact rule of a residual-target row with one
+// off-diagonal (a = -a_ij/a_ii, LS = 0); diagonal: a = 0, LS = NaN.  Written
+// to A.a and A.ls64 for the upstream gradient and the adjoint of the fits.
+// ---------------------------------------------------------------------------
+template <class TS, int G>
+__global__ void __launch_bounds__(kThreads) k_refit(AdjArgs A)
+{
+    using S = Store<TS>;
+    constexpr int V = S::V;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t r = (int64_t)blockIdx.x * (kThreads / G) + threadIdx.x / G;
+    if (r >= A.n) return;
+    const unsigned gmask = group_mask<G>();
+    const TS *__restrict__ X = (const TS *)A.x;
+    const int Kp = A.Kp;
+    const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
+    double w[V], y[V];
+    ldc<double, V>((const double *)A.w + lane * V, w);
+    target64<TS, V>(A, r, lane, p0, p1, y);
+    double *a_out = (double *)A.a_fit;
+    double *ls_out = A.ls64;
+    const bool fixed = A.target == 0 && p1 - p0 == 2;
+    const double diag = __ldg((const double *)A.diag + r);
+    for (int p = p0; p < p1; ++p) {
+        const int64_t j = __ldg(A.col + p);
+        double a_, ls_;
+        if (j == r) {
+            a_ = 0.0;
+            ls_ = NAN;
+        } else if (fixed) {
+            a_ = -__ldg((const double *)A.val + p) / diag;
+            ls_ = 0.0;
+        } else {
+            double x[V];
+            unpack64<TS, V>(ldg16(X + j * Kp + lane * V), x);
+            double xx = 0.0, yx = 0.0;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                xx = fma(w[e] * x[e], x[e], xx);
+                yx = fma(w[e] * x[e], y[e], yx);
+            }
+            xx = group_sum<G>(xx, gmask);
+            yx = group_sum<G>(yx, gmask);
+            a_ = (xx == 0.0) ? 0.0 : yx / xx;
+            double res = 0.0;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const double d = fma(-a_, x[e], y[e]);
+                res = fma(w[e] * d, d, res);
+            }
+            ls_ = group_sum<G>(res, gmask);
+        }
+        if (lane == 0) {
+            a_out[p] = a_;
+            ls_out[p] = ls_;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // row i: Y_i, Ybar_i = 2 w (y_i sum_p lsb_p - sum_p lsb_p a_p x_j), and for
 // the residual target gt_p = <Ybar_i, X_col_p> over all slots
 // ---------------------------------------------------------------------------
@@ -157,28 +276,20 @@ template <class TS, int G>
 __global__ void __launch_bounds__(kThreads) k_edge_bwd(AdjArgs A)
 {
     using S = Store<TS>;
-    using C = typename S::C;
+    using C = double;
     constexpr int V = S::V;
     const int lane = threadIdx.x & (G - 1);
     const int64_t r = (int64_t)blockIdx.x * (kThreads / G) + threadIdx.x / G;
     if (r >= A.n) return;
     const unsigned gmask = group_mask<G>();
     const TS *__restrict__ X = (const TS *)A.x;
-    const C *__restrict__ val = (const C *)A.val;
     const int Kp = A.Kp;
     const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
     const int64_t off = r * Kp + lane * V;
 
     C w[V], y[V];
     ldc<C, V>((const C *)A.w + lane * V, w);
-    S::unpack(ldg16(X + off), y);
-    if (A.target == 0) {               // same rounding as the forward edge pass
-        Acc<C, V> acc[1];
-        row_sum<TS, G, 1, 4, false>(A.col, val, X, X, 0, Kp, lane, p0, p1, acc);
-        const C d = C(1) / __ldg((const C *)A.diag + r);
-#pragma unroll
-        for (int e = 0; e < V; ++e) y[e] = fma(-d, acc[0].get(e), y[e]);
-    }
+    target64<TS, V>(A, r, lane, p0, p1, y);
     stc<C, V>((C *)A.y + off, y);
 
     C v[V];
@@ -191,7 +302,7 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd(AdjArgs A)
         const int j = __ldg(A.col + p);
         const C c = (C)(g * (double)__ldg((const C *)A.a + p));
         C xj[V];
-        S::unpack(ldg16(X + (int64_t)j * Kp + lane * V), xj);
+        unpack64<TS, V>(ldg16(X + (int64_t)j * Kp + lane * V), xj);
 #pragma unroll
         for (int e = 0; e < V; ++e) v[e] = fma(c, xj[e], v[e]);
         L += g;
@@ -207,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd(AdjArgs A)
         for (int p = p0; p < p1; ++p) {
             const int j = __ldg(A.col + p);
             C xj[V];
-            S::unpack(ldg16(X + (int64_t)j * Kp + lane * V), xj);
+            unpack64<TS, V>(ldg16(X + (int64_t)j * Kp + lane * V), xj);
             C part = C(0);
 #pragma unroll
             for (int e = 0; e < V; ++e) part = fma(yb[e], xj[e], part);
@@ -227,7 +338,7 @@ template <class TS, int G>
 __global__ void __launch_bounds__(kThreads) k_xbar_nu(AdjArgs A)
 {
     using S = Store<TS>;
-    using C = typename S::C;
+    using C = double;
     constexpr int V = S::V;
     const int lane = threadIdx.x & (G - 1);
     const int64_t jr = (int64_t)blockIdx.x * (kThreads / G) + threadIdx.x / G;
@@ -240,7 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_xbar_nu(AdjArgs A)
 
     C w[V], xj[V], acc[V];
     ldc<C, V>((const C *)A.w + lane * V, w);
-    S::unpack(ldg16(X + off), xj);
+    unpack64<TS, V>(ldg16(X + off), xj);
     if (A.target == 1) {
         ldc<C, V>(Yb + off, acc);
     } else {
@@ -262,14 +373,20 @@ __global__ void __launch_bounds__(kThreads) k_xbar_nu(AdjArgs A)
             for (int e = 0; e < V; ++e) acc[e] = fma(c * w[e], fma(-ap, xj[e], yi[e]), acc[e]);
         }
         if (A.target == 0) {
-            const C b = __ldg((const C *)A.at_b + q);
+            const C b = (C)__ldg((const typename S::C *)A.at_b + q);   // the sweeps' type
             C ybi[V];
             ldc<C, V>(Yb + (int64_t)i * Kp + lane * V, ybi);
 #pragma unroll
             for (int e = 0; e < V; ++e) acc[e] = fma(-b, ybi[e], acc[e]);
         }
     }
-    stc<C, V>((C *)A.xbar_out + off, acc);
+    {
+        using CS = typename S::C;        // the sweeps' arithmetic type
+        CS out[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) out[e] = (CS)acc[e];
+        stc<CS, V>((CS *)A.xbar_out + off, out);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -280,7 +397,7 @@ template <class TS, int G>
 __global__ void __launch_bounds__(kThreads) k_gram(AdjArgs A)
 {
     using S = Store<TS>;
-    using C = typename S::C;
+    using C = typename S::C;        // the sweeps' arithmetic type
     constexpr int V = S::V;
     constexpr int U = 4;
     const int lane = threadIdx.x & (G - 1);
@@ -288,7 +405,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(AdjArgs A)
     if (r >= A.n) return;
     const unsigned gmask = group_mask<G>();
     const TS *__restrict__ X = (const TS *)A.x;
-    C *gs = (C *)A.gs;
+    double *gs = (double *)A.gs;
     const int Kp = A.Kp;
     const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
     C xb[V];
@@ -307,7 +424,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(AdjArgs A)
 #pragma unroll
             for (int e = 0; e < V; ++e) part = fma(xb[e], xj[e], part);
             part = group_sum<G>(part, gmask);
-            if (lane == 0) gs[pb + u] = A.first ? part : gs[pb + u] + part;
+            if (lane == 0) gs[pb + u] = A.first ? (double)part : gs[pb + u] + (double)part;
         }
     }
 }
@@ -317,7 +434,7 @@ template <class TS, int G>
 __global__ void __launch_bounds__(kThreads) k_spmm_t(AdjArgs A)
 {
     using S = Store<TS>;
-    using C = typename S::C;
+    using C = typename S::C;        // the sweeps' arithmetic type
     constexpr int V = S::V;
     constexpr int U = 4;
     const int lane = threadIdx.x & (G - 1);
@@ -359,7 +476,7 @@ template <class TS, int G>
 __global__ void __launch_bounds__(kThreads) k_sweep_sym(AdjArgs A)
 {
     using S = Store<TS>;
-    using C = typename S::C;
+    using C = typename S::C;        // the sweeps' arithmetic type
     constexpr int V = S::V;
     constexpr int U = 4;
     const int lane = threadIdx.x & (G - 1);
@@ -369,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_sym(AdjArgs A)
     const TS *__restrict__ X = (const TS *)A.x;
     const C *__restrict__ Xb = (const C *)A.xbar_in;
     const C *__restrict__ bm = (const C *)A.bm;
-    C *gs = (C *)A.gs;
+    double *gs = (double *)A.gs;
     const int Kp = A.Kp;
     const C om = (C)A.omega;
     const int p0 = __ldg(A.rp + r), p1 = __ldg(A.rp + r + 1);
@@ -402,7 +519,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_sym(AdjArgs A)
                 acc[e] = fma(-c[u], xbi[u][e], acc[e]);
             }
             part = group_sum<G>(part, gmask);
-            if (lane == 0) gs[pb + u] = A.first ? part : gs[pb + u] + part;
+            if (lane == 0) gs[pb + u] = A.first ? (double)part : gs[pb + u] + (double)part;
         }
     }
     stc<C, V>((C *)A.xbar_out + r * Kp + lane * V, acc);
@@ -487,6 +604,7 @@ static int lanes(int storage, int Kp) { return Kp / (storage == ST_FP64 ? 2 : st
         return cudaGetLastError();                                                       \
     }
 
+AMGD_ADJ_LAUNCHER(launch_adj_refit, k_refit)
 AMGD_ADJ_LAUNCHER(launch_adj_edge, k_edge_bwd)
 AMGD_ADJ_LAUNCHER(launch_adj_xbar_nu, k_xbar_nu)
 AMGD_ADJ_LAUNCHER(launch_adj_gram, k_gram)
@@ -498,12 +616,9 @@ cudaError_t launch_adj_upstream(int storage, const int32_t *rp, const int32_t *c
                                 double *lsb, double *partial, int32_t nblocks, int32_t n,
                                 int32_t target, cudaStream_t s)
 {
-    if (storage == ST_FP64)
-        k_upstream<double><<<nblocks, kThreads, 0, s>>>(rp, col, (const double *)ls, flag, ls_bar,
-                                                        lsb, partial, n, target);
-    else
-        k_upstream<float><<<nblocks, kThreads, 0, s>>>(rp, col, (const float *)ls, flag, ls_bar,
-                                                       lsb, partial, n, target);
+    (void)storage;                       // LS refitted in FP64 for every storage
+    k_upstream<double><<<nblocks, kThreads, 0, s>>>(rp, col, (const double *)ls, flag, ls_bar,
+                                                    lsb, partial, n, target);
     return cudaGetLastError();
 }
 
@@ -514,7 +629,7 @@ cudaError_t launch_adj_bvals(int storage, const double *val64, const double *dia
     if (nnz == 0) return cudaSuccess;
     const int64_t want = (nnz + kThreads - 1) / kThreads;
     const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
-    if (storage == ST_FP64)
+    if (storage == ST_FP64)              // the sweeps' arithmetic type
         k_bvals<double><<<grid, kThreads, 0, s>>>(val64, diag64, at_row, at_slot, (double *)at_b, nnz);
     else
         k_bvals<float><<<grid, kThreads, 0, s>>>(val64, diag64, at_row, at_slot, (float *)at_b, nnz);
@@ -526,14 +641,10 @@ cudaError_t launch_adj_finish(int storage, const AdjArgs &a, bool have_gs, const
                               double *partial, int32_t nblocks, cudaStream_t s)
 {
     const bool have_gt = a.target == 0;
-    if (storage == ST_FP64)
-        k_finish<double><<<nblocks, kThreads, 0, s>>>(
-            a.rp, val64, diag64, diag_slot, have_gs ? (const double *)a.gs : nullptr,
-            have_gt ? (const double *)a.gt : nullptr, a.omega, a.n, val_bar, partial);
-    else
-        k_finish<float><<<nblocks, kThreads, 0, s>>>(
-            a.rp, val64, diag64, diag_slot, have_gs ? (const float *)a.gs : nullptr,
-            have_gt ? (const float *)a.gt : nullptr, a.omega, a.n, val_bar, partial);
+    (void)storage;                       // FP64 reverse pass for every storage
+    k_finish<double><<<nblocks, kThreads, 0, s>>>(
+        a.rp, val64, diag64, diag_slot, have_gs ? (const double *)a.gs : nullptr,
+        have_gt ? (const double *)a.gt : nullptr, a.omega, a.n, val_bar, partial);
     return cudaGetLastError();
 }
 
