@@ -578,29 +578,21 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
     __syncthreads();
 
     // ---- B. one-point fits, one stored entry per thread -------------------------
+    // one entry of a thread at a time (two in flight, their x_j gathered together,
+    // measured slower: the registers cost more occupancy than the overlap gains)
+    constexpr int E = 1;
     C *a_out = (C *)A.a_out;
     C *ls_out = (C *)A.ls_out;
-    for (int p = S0 + threadIdx.x; p < S1; p += kEdgeThreads) {
-        const int rl = single ? 0 : srow[p - S0];
-        const int64_t r = R0 + rl;
-        const int j = __ldg(A.pcol + p);
-        C a_, ls_;
-        if (j == r) {
-            a_ = C(0);
-            ls_ = C(NAN);
-        } else if (j == j1s[rl]) {
-            a_ = -v1s[rl] / dg[rl];                     // y_i = -(a_ij/a_ii) x_j exactly
-            ls_ = C(0);
-        } else if constexpr (COMP && kMixed) {
+    // the fit of slot p (row rl, column j) from the pieces `hold` of x_j
+    auto fit = [&](int rl, int j, const uint4 (&hold)[HOLD], C &a_, C &ls_) {
+        const TS *xj = X + (int64_t)j * KP;
+        const C *yr = ys + rl * KP;
+        if constexpr (COMP && kMixed) {
             // compensated sums over all K components in this thread
-            const TS *xj = X + (int64_t)j * KP;
-            const C *yr = ys + rl * KP;
-            uint4 hold[HOLD];
             Comp2 sx;
 #pragma unroll
             for (int c = 0; c < P; ++c) {
-                const uint4 raw = ldg16(xj + c * V);
-                if constexpr (P <= 4) hold[c] = raw;
+                const uint4 raw = (P <= 4) ? hold[c < HOLD ? c : 0] : ldg16(xj + c * V);
                 C x[V], y[V], w[V];
                 S::unpack(raw, x);
 #pragma unroll
@@ -615,9 +607,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
             Comp2 sl;
 #pragma unroll
             for (int c = 0; c < P; ++c) {
-                uint4 raw;
-                if constexpr (P <= 4) raw = hold[c];
-                else raw = ldg16(xj + c * V);
+                const uint4 raw = (P <= 4) ? hold[c < HOLD ? c : 0] : ldg16(xj + c * V);
                 C x[V], y[V], w[V];
                 S::unpack(raw, x);
 #pragma unroll
@@ -628,16 +618,11 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
                 comp_residual<V, UW>(a_, x, y, w, sl);
             }
             ls_ = comp_ls_total<1>(sl, 0xffffffffu);
-            if (ls_ < C(1e-4) * syy[rl]) dfr[rl] = 1;        // cancellation: redo the row in FP64
         } else {
-            const TS *xj = X + (int64_t)j * KP;
-            const C *yr = ys + rl * KP;
-            uint4 hold[HOLD];
             PieceSums<C, V, UW> ps;
 #pragma unroll
             for (int c = 0; c < P; ++c) {
-                const uint4 raw = ldg16(xj + c * V);
-                if constexpr (P <= 4) hold[c] = raw;
+                const uint4 raw = (P <= 4) ? hold[c < HOLD ? c : 0] : ldg16(xj + c * V);
                 C x[V], y[V], w[V];
                 S::unpack(raw, x);
 #pragma unroll
@@ -652,9 +637,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
             C res = C(0);
 #pragma unroll
             for (int c = 0; c < P; ++c) {
-                uint4 raw;
-                if constexpr (P <= 4) raw = hold[c];
-                else raw = ldg16(xj + c * V);
+                const uint4 raw = (P <= 4) ? hold[c < HOLD ? c : 0] : ldg16(xj + c * V);
                 C x[V], y[V], w[V];
                 S::unpack(raw, x);
 #pragma unroll
@@ -665,12 +648,47 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
                 residual_add<C, V, UW>(a_, x, y, w, res);
             }
             ls_ = res;
-            if constexpr (kMixed)
-                if (ls_ < C(1e-4) * syy[rl]) dfr[rl] = 1;    // cancellation: redo the row in FP64
         }
-        a_out[p] = a_;
-        ls_out[p] = ls_;
-        if (j != r) atomicMin(&rmin[rl], MB::bits(ls_));
+    };
+    for (int pb = S0 + threadIdx.x; pb < S1; pb += E * kEdgeThreads) {
+        int rls[E], js[E];
+        uint4 hold[E][HOLD];
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int p = pb + q * kEdgeThreads;
+            js[q] = -1;
+            if (p < S1) {
+                rls[q] = single ? 0 : srow[p - S0];
+                js[q] = __ldg(A.pcol + p);
+                if (P <= 4 && js[q] != R0 + rls[q] && js[q] != j1s[rls[q]]) {
+                    const TS *xj = X + (int64_t)js[q] * KP;
+#pragma unroll
+                    for (int c = 0; c < HOLD; ++c) hold[q][c] = ldg16(xj + c * V);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            if (js[q] < 0) break;
+            const int p = pb + q * kEdgeThreads;
+            const int rl = rls[q], j = js[q];
+            const int64_t r = R0 + rl;
+            C a_, ls_;
+            if (j == r) {
+                a_ = C(0);
+                ls_ = C(NAN);
+            } else if (j == j1s[rl]) {
+                a_ = -v1s[rl] / dg[rl];                 // y_i = -(a_ij/a_ii) x_j exactly
+                ls_ = C(0);
+            } else {
+                fit(rl, j, hold[q], a_, ls_);
+                if constexpr (kMixed)
+                    if (ls_ < C(1e-4) * syy[rl]) dfr[rl] = 1;    // cancellation: redo the row in FP64
+            }
+            a_out[p] = a_;
+            ls_out[p] = ls_;
+            if (j != r) atomicMin(&rmin[rl], MB::bits(ls_));
+        }
     }
     __syncthreads();
 
