@@ -164,11 +164,36 @@ def adjoint_bytes(n, nnz, K, nu, every, precision):
                 total=fwd + edge + bwd)
 
 
+def _code_only(text):
+    """C++ source with comments removed and whitespace collapsed: a note
+    edited beside a kernel does not make its recorded counters stale."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_sha(*names):
     h = hashlib.sha256()
     for nm in names:
-        with open(os.path.join(ROOT, "paper_1106_5990_gb300", "csrc", nm), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1106_5990_gb300", "csrc", nm)) as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -311,15 +311,19 @@ int amgd_graph_launch(amgd_handle h);
  *   sixteen-byte vectors (V = 2, 4, 8 elements for FP64, FP32, BF16); a
  *   shape spreads them over G lanes with NV vectors per lane (G*NV = P,
  *   NV in {1,2,4}) and gathers U nonzeros per batch (U in {4,8}; the
- *   distance pass also takes U = 2).  For the
+ *   distance pass also takes U = 2).  In these terms a warp holds 32/G
+ *   rows, a lane's tile of K is NV*V components and every vector load is 16
+ *   bytes wide; the tuner picks all three.  For the
  *   relaxation, staged selects the kernel: 0 direct; 1 persistent, each
  *   tile's CSR slice copied into shared memory with TMA bulk copies ahead of
  *   use (waits bounded to about one second; a wait that runs out makes the
  *   next synchronising call return AMGD_ERR_TIMEOUT); 2 warp-pipelined, CSR
  *   slices and neighbour rows copied with cp.async two and one row groups
- *   ahead (U must be 4); 3 persistent with L2 prefetch, each warp asking
- *   the L2 for the row pointers and CSR lines of its rows one and two tiles
- *   ahead.  For the distance pass, staged selects 0 the row
+ *   ahead (U must be 4); 3 chunked, one 1024-thread block per SM owning a
+ *   contiguous run of rows, each warp asking the L2 for the row pointers
+ *   and CSR lines of its next row groups ahead of use and loading the CSR
+ *   with an evict-first and the vectors with an evict-last cache policy.
+ *   For the distance pass, staged selects 0 the row
  *   kernel (G lanes per row), 1 the tile kernel (one thread per stored
  *   entry) or 2 the row kernel reading the vectors in the sweeps' row
  *   order in place (search depth 1: no caller-order copy of the vectors;

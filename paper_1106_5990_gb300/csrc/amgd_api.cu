@@ -173,11 +173,14 @@ bool shape_ok(int st, int K, Shape sh)
 }
 
 // the distance pass: stages 0 (rows) and 1 (tiles) take every valid shape;
-// stage 2 (the row kernel on the sweeps' row order) 2 or 4 entries per batch
+// stage 2 (the row kernel on the sweeps' row order) 2 or 4 entries per batch,
+// stage 3 (the warp-staged kernel on that order) 4 or 8
 bool edge_shape_ok(Shape sh)
 {
-    if (sh.stage < 0 || sh.stage > 2) return false;
-    return sh.stage < 2 || sh.U == 2 || sh.U == 4;
+    if (sh.stage < 0 || sh.stage > 3) return false;
+    if (sh.stage == 2) return sh.U == 2 || sh.U == 4;
+    if (sh.stage == 3) return sh.U == 4 || sh.U == 8;
+    return true;
 }
 
 // untuned default: one vector per lane, four nonzeros per batch (the
@@ -463,11 +466,11 @@ int run_relax_recorded(amgd_ctx *h, int32_t nu, double omega, cudaStream_t s)
 int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
 {
     Shape sh = h->edge_shape[h->storage];
-    if (sh.stage == 2 && h->depth > 1) sh.stage = 0;    // stage 2 covers A's own pattern
+    if (sh.stage >= 2 && h->depth > 1) sh.stage = 0;    // stages 2 and 3 cover A's own pattern
     // stages 0 and 1 run on the caller's numbering: bring a row-permuted vector
-    // block back to caller order first; stage 2 reads the sweeps' row order
+    // block back to caller order first; stages 2 and 3 read the sweeps' row order
     const void *xc = h->x[h->cur];
-    if (h->perm && sh.stage != 2) {
+    if (h->perm && sh.stage < 2) {
         if (!h->x_caller) return fail(h, AMGD_ERR_STATE, "caller-order vector buffer missing");
         CK(h, launch_unpermute(h->storage, h->x[h->cur], h->x_caller, h->perm, (int32_t)h->n,
                                Kp_of(h->storage, h->K), s));
@@ -496,7 +499,7 @@ int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
     a.Kp = Kp_of(h->storage, h->K);
     a.target = h->target;
     a.theta = theta;
-    if (sh.stage == 2) {
+    if (sh.stage >= 2) {
         a.x = h->x[h->cur];                  // the sweeps' row order, read in place
         a.xrow = h->perm ? h->pinv : nullptr;
         a.xcol = h->perm ? h->colx : h->col_o;
@@ -1396,13 +1399,14 @@ int amgd_autotune(amgd_handle h, int sweep_type, double omega, const char *cache
         }
     }
     // edge pass: stage 0 row kernel, stage 1 tile kernel, stage 2 the row
-    // kernel on the sweeps' row order (search depth 1)
-    for (int stage : {0, 1, 2})
+    // kernel and stage 3 the warp-staged kernel on the sweeps' row order
+    // (search depth 1)
+    for (int stage : {0, 1, 2, 3})
         for (int NV : {1, 2, 4})
             for (int U : {2, 4, 8}) {
                 const Shape c{P / NV, NV, U, stage};
                 if (P % NV != 0 || !shape_ok(h->storage, h->K, c) || !edge_shape_ok(c)) continue;
-                if (stage == 2 && h->depth > 1) continue;
+                if (stage >= 2 && h->depth > 1) continue;
                 float ms = 0.f;
                 h->edge_shape[h->storage] = c;
                 const int rc = time_ms(h, [&]() { return run_edge(h, 0.5, h->stream); }, 5, ms);

@@ -120,14 +120,33 @@ __device__ __forceinline__ uint4 ldg16(const void *p)
     return __ldg(reinterpret_cast<const uint4 *>(p));
 }
 
+// 32-byte read-only load of two adjacent chunks (sm_100 and later; the address
+// is 32-byte aligned)
+__device__ __forceinline__ void ldg32(const void *p, uint4 &a, uint4 &b)
+{
+    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(p));
+}
+
+// a lane that owns a whole row (G = 1) of an even number of chunks reads them
+// in pairs; the rows must then start on 32-byte boundaries, which the
+// handle's buffers do (a row is P chunks, P even).  Launchers refuse other
+// pointers instead of faulting.
+inline bool rows_aligned32(const void *x, int Kp, size_t elem)
+{
+    return ((uintptr_t)x & 31) == 0 && (Kp * elem) % 32 == 0;
+}
+
 // Kernel shape of one storage type: G lanes per row, NV 16-byte vectors per
 // lane (so a row holds P = G * NV vectors, Kp = P * V elements), U nonzeros
 // gathered per batch.  P is fixed by (storage, K); G, NV and U are free.
 struct Shape {
     int G, NV, U;
     int stage = 0;   // relaxation: 0 direct, 1 TMA-staged CSR, 2 cp.async pipelined,
-                     // 3 persistent with L2 prefetch of the CSR ahead of use;
-                     // edge pass: 0 row kernel, 1 tile kernel
+                     // 3 chunked (one block per SM, L2 prefetch of the CSR ahead of use);
+                     // edge pass: 0 row kernel, 1 tile kernel, 2 row kernel on the
+                     // sweeps' row order in place
 };
 
 // per-device record of a one-time host setting of a kernel (a shared-memory

@@ -28,7 +28,9 @@
 // vector block; stage 1, k_edge_tiles, rows cut into tiles with one thread
 // per stored entry for the fits, on the same copy; stage 2, k_edge_rows
 // reading the permuted block in place through renumbered column indices
-// (no copy; search depth 1).
+// (no copy; search depth 1); stage 3, k_edge_warp (k_edge_warp.cuh), on the
+// same in-place order, gathering every neighbour row once into a per-warp
+// shared-memory window and fitting one stored entry per lane.
 #pragma once
 #include <type_traits>
 
@@ -338,9 +340,14 @@ __global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
             for (int u = 0; u < U; ++u)
                 if (jj[u] >= 0 && jj[u] != r) {
                     const int64_t xj = PX ? (int64_t)__ldg(xcol + pb + u) : (int64_t)jj[u];
+                    if constexpr (G == 1 && NV % 2 == 0) {       // whole row per lane: 32-byte pairs
 #pragma unroll
-                    for (int t = 0; t < NV; ++t)
-                        raw[u][t] = ldg16(X + xj * Kp + (t * G + lane) * V);
+                        for (int t = 0; t < NV; t += 2) ldg32(X + xj * Kp + t * V, raw[u][t], raw[u][t + 1]);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < NV; ++t)
+                            raw[u][t] = ldg16(X + xj * Kp + (t * G + lane) * V);
+                    }
                 }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -662,8 +669,13 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
                 js[q] = __ldg(A.pcol + p);
                 if (P <= 4 && js[q] != R0 + rls[q] && js[q] != j1s[rls[q]]) {
                     const TS *xj = X + (int64_t)js[q] * KP;
+                    if constexpr (HOLD % 2 == 0) {                  // 32-byte pairs
 #pragma unroll
-                    for (int c = 0; c < HOLD; ++c) hold[q][c] = ldg16(xj + c * V);
+                        for (int c = 0; c < HOLD; c += 2) ldg32(xj + c * V, hold[q][c], hold[q][c + 1]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < HOLD; ++c) hold[q][c] = ldg16(xj + c * V);
+                    }
                 }
             }
         }
@@ -815,6 +827,8 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
 template <class TS, int G, int NV, int U, bool UW, bool PX, bool COMP>
 cudaError_t go_rows(const EdgeArgs &a, cudaStream_t s)
 {
+    if constexpr (G == 1 && NV % 2 == 0)
+        if (!rows_aligned32(a.x, a.Kp, sizeof(TS))) return cudaErrorMisalignedAddress;
     const int rows_per_block = kEdgeThreads / G;
     const unsigned grid = (unsigned)(((int64_t)a.n + rows_per_block - 1) / rows_per_block);
     constexpr int smem = edge_smem_bytes<typename Store<TS>::C, G>();
@@ -835,6 +849,8 @@ cudaError_t go_tiles(const EdgeArgs &a, cudaStream_t s)
 {
     constexpr int KP = G * NV * Store<TS>::V;
     if (a.Kp != KP || a.ntiles <= 0) return cudaErrorInvalidValue;
+    if constexpr ((G * NV) % 2 == 0)          // 32-byte row reads (row sums at G = 1, fits)
+        if (!rows_aligned32(a.x, a.Kp, sizeof(TS))) return cudaErrorMisalignedAddress;
     constexpr int smem = EdgeTileLayout<TS, KP>::BYTES;
     static PerDevice opted;                  // shared-memory opt-in made on each device
     const int dev = current_device_index();
@@ -848,6 +864,14 @@ cudaError_t go_tiles(const EdgeArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+}  // namespace edge_impl
+}  // namespace amgd
+
+#include "k_edge_warp.cuh"
+
+namespace amgd {
+namespace edge_impl {
+
 // one storage type and summation form; the plain and the compensated forms
 // are instantiated in separate translation units (parallel compilation)
 template <class TS, bool COMP, int G, int NV, int U, bool UW>
@@ -856,6 +880,10 @@ cudaError_t go(int stage, const EdgeArgs &a, cudaStream_t s)
     if (a.n <= 0) return cudaSuccess;
     if (stage == 1) return go_tiles<TS, G, NV, U, UW, COMP>(a, s);
     if (stage == 2) return go_rows<TS, G, NV, U, UW, true, COMP>(a, s);
+    if (stage == 3) {
+        if constexpr (U >= 4) return go_warp<TS, G, NV, U, UW, COMP>(a, s);
+        return cudaErrorInvalidValue;
+    }
     return go_rows<TS, G, NV, U, UW, false, COMP>(a, s);
 }
 

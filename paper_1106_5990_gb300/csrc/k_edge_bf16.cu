@@ -13,7 +13,7 @@ cudaError_t launch_edge_bf16(Shape sh, bool unit_w, const EdgeArgs &a, cudaStrea
     e = a.compensated ? launch_edge_bf16_comp(sh, unit_w, a, s)
                       : edge_impl::dispatch_g<__nv_bfloat16, false>(sh, unit_w, a, s);
     if (e != cudaSuccess || a.n == 0) return e;
-    if (sh.stage == 2) edge_impl::k_edge_fixup<__nv_bfloat16, true><<<152, 256, 0, s>>>(a);
+    if (sh.stage >= 2) edge_impl::k_edge_fixup<__nv_bfloat16, true><<<152, 256, 0, s>>>(a);
     else edge_impl::k_edge_fixup<__nv_bfloat16, false><<<152, 256, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -13,7 +13,7 @@ cudaError_t launch_edge_f32(Shape sh, bool unit_w, const EdgeArgs &a, cudaStream
     e = a.compensated ? launch_edge_f32_comp(sh, unit_w, a, s)
                       : edge_impl::dispatch_g<float, false>(sh, unit_w, a, s);
     if (e != cudaSuccess || a.n == 0) return e;
-    if (sh.stage == 2) edge_impl::k_edge_fixup<float, true><<<152, 256, 0, s>>>(a);
+    if (sh.stage >= 2) edge_impl::k_edge_fixup<float, true><<<152, 256, 0, s>>>(a);
     else edge_impl::k_edge_fixup<float, false><<<152, 256, 0, s>>>(a);
     return cudaGetLastError();
 }

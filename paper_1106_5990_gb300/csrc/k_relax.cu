@@ -519,6 +519,19 @@ __device__ __forceinline__ void st16_hint(void *p, const uint4 &v, uint64_t pol)
                  "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
                  : "memory");
 }
+// 32-byte vector load / store (sm_100 and later; the address is 32-byte aligned)
+__device__ __forceinline__ void ldg32_hint(const void *p, uint64_t pol, uint4 &a, uint4 &b)
+{
+    asm volatile("ld.global.nc.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void st32_hint(void *p, const uint4 &a, const uint4 &b, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v8.u32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8}, %9;" ::"l"(p),
+                 "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w), "l"(pol)
+                 : "memory");
+}
 __device__ __forceinline__ int32_t ld32_hint(const int32_t *p, uint64_t pol)
 {
     int32_t v;
@@ -556,6 +569,13 @@ __global__ void __launch_bounds__(kChunkThreads, 1) k_relax_chunk(RelaxArgs A, i
     const int64_t c0 = (int64_t)A.r0 + (int64_t)blockIdx.x * chunk;
     const int64_t c1 = min((int64_t)A.r1, c0 + chunk);
     const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
+    // a lane holding an even number of pieces holds them side by side and moves
+    // them two at a time (32-byte accesses: half the load instructions and
+    // cache wavefronts of a gather); otherwise the pieces interleave over the
+    // G lanes.  Every component keeps its own FMA chain, so both layouts give
+    // the same bits.
+    constexpr bool W32 = NV % 2 == 0;
+    auto piece = [&](int tt) { return W32 ? lane * NV + tt : tt * G + lane; };
 
     for (int64_t wr0 = c0 + (int64_t)warp * RW; wr0 < c1; wr0 += STEP) {
         // row pointers of this warp's group after next, into L2
@@ -587,9 +607,14 @@ __global__ void __launch_bounds__(kChunkThreads, 1) k_relax_chunk(RelaxArgs A, i
                     if (jj[u] >= 0) {
                         const TS *src = (SPLIT && jj[u] < A.split ? (const TS *)xnew : xold) +
                                         (int64_t)jj[u] * Kp;
+                        if constexpr (W32) {
 #pragma unroll
-                        for (int tt = 0; tt < NV; ++tt)
-                            raw[u][tt] = ldg16_hint(src + (tt * G + lane) * V, keep);
+                            for (int tt = 0; tt < NV; tt += 2)
+                                ldg32_hint(src + piece(tt) * V, keep, raw[u][tt], raw[u][tt + 1]);
+                        } else {
+#pragma unroll
+                            for (int tt = 0; tt < NV; ++tt) raw[u][tt] = ldg16_hint(src + piece(tt) * V, keep);
+                        }
                     }
                 }
 #pragma unroll
@@ -604,13 +629,23 @@ __global__ void __launch_bounds__(kChunkThreads, 1) k_relax_chunk(RelaxArgs A, i
                 }
             }
             const C c = (C)A.omega / ldv_hint((const AV *)A.diag + r, stream);
+            // x_i - (omega / a_ii) s_i, a pair of pieces (W32) or one piece at a time
+            constexpr int PW = W32 ? 2 : 1;
 #pragma unroll
-            for (int tt = 0; tt < NV; ++tt) {
-                C xi[V], out[V];
-                S::unpack(ldg16_hint(xold + r * Kp + (tt * G + lane) * V, keep), xi);
+            for (int t0 = 0; t0 < NV; t0 += PW) {
+                uint4 own[PW];
+                if constexpr (W32) ldg32_hint(xold + r * Kp + piece(t0) * V, keep, own[0], own[1]);
+                else own[0] = ldg16_hint(xold + r * Kp + piece(t0) * V, keep);
 #pragma unroll
-                for (int e = 0; e < V; ++e) out[e] = fma(-c, acc[tt].get(e), xi[e]);
-                st16_hint(xnew + r * Kp + (tt * G + lane) * V, S::pack(out), keep);
+                for (int h = 0; h < PW; ++h) {
+                    C xi[V], out[V];
+                    S::unpack(own[h], xi);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) out[e] = fma(-c, acc[t0 + h].get(e), xi[e]);
+                    own[h] = S::pack(out);
+                }
+                if constexpr (W32) st32_hint(xnew + r * Kp + piece(t0) * V, own[0], own[1], keep);
+                else st16_hint(xnew + r * Kp + piece(t0) * V, own[0], keep);
             }
         }
         // column-index and value lines of this warp's next group, into L2
@@ -640,6 +675,12 @@ cudaError_t go_chunk(const RelaxArgs &a, cudaStream_t s)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
         if (sms <= 0) sms = 1;
         sm_count.set(dev, sms);
+    }
+    // 32-byte accesses (NV even) need 32-byte aligned rows: always true of the
+    // handle's buffers (P even), refused rather than faulted otherwise
+    if constexpr (NV % 2 == 0) {
+        if (!rows_aligned32(a.xold, a.Kp, sizeof(TS)) || !rows_aligned32(a.xnew, a.Kp, sizeof(TS)))
+            return cudaErrorMisalignedAddress;
     }
     // one chunk per SM, a whole number of warp groups each
     int64_t chunk = (rows + sms - 1) / sms;
@@ -742,6 +783,10 @@ cudaError_t go(const RelaxArgs &a, cudaStream_t s)
 {
     const int64_t rows = (int64_t)a.r1 - a.r0;
     if (rows <= 0) return cudaSuccess;
+    if constexpr (G == 1 && NV % 2 == 0) {          // 32-byte row reads
+        if (!rows_aligned32(a.xold, a.Kp, sizeof(TS)) || !rows_aligned32(a.xnew, a.Kp, sizeof(TS)))
+            return cudaErrorMisalignedAddress;
+    }
     const int rows_per_block = kRelaxThreads / G;
     const unsigned grid = (unsigned)((rows + rows_per_block - 1) / rows_per_block);
     if (a.split > 0)

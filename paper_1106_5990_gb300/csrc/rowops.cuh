@@ -54,7 +54,8 @@ template <int V> struct Acc<float, V> {
 // s[tt][e] = sum_{p in [p0,p1)} val[p] * X[col[p]] (lane's pieces), in CSR
 // order.  SPLIT: rows j < split are read from xnew, the others from xold.
 // Nonzeros are taken U at a time: U column indices and values, then all U
-// gathers in flight before any is consumed.
+// gathers in flight before any is consumed.  A lane that owns a whole row
+// (G = 1, NV even) reads it in 32-byte pairs: the rows are 32-byte aligned.
 template <class TS, int G, int NV, int U, bool SPLIT>
 __device__ __forceinline__ void row_sum(const int32_t *__restrict__ col,
                                         const typename Store<TS>::A *__restrict__ val,
@@ -81,8 +82,13 @@ __device__ __forceinline__ void row_sum(const int32_t *__restrict__ col,
         for (int u = 0; u < U; ++u) {
             if (jj[u] >= 0) {
                 const TS *src = (SPLIT && jj[u] < split ? xnew : xold) + (int64_t)jj[u] * Kp;
+                if constexpr (G == 1 && NV % 2 == 0) {
 #pragma unroll
-                for (int tt = 0; tt < NV; ++tt) raw[u][tt] = ldg16(src + (tt * G + lane) * V);
+                    for (int tt = 0; tt < NV; tt += 2) ldg32(src + tt * V, raw[u][tt], raw[u][tt + 1]);
+                } else {
+#pragma unroll
+                    for (int tt = 0; tt < NV; ++tt) raw[u][tt] = ldg16(src + (tt * G + lane) * V);
+                }
             }
         }
 #pragma unroll

@@ -43,13 +43,13 @@ MATRICES = {
 
 
 def gpu_build(rp, col, val, K, seed, nu, omega, theta, sweep=0, color=None, w=None,
-              target=0, precision="fp64", X0=None, edge_stage=None):
+              target=0, precision="fp64", X0=None, edge_stage=None, edge_u=None):
     with amgd.Handle(rp, col, val, K, seed) as h:
         if precision != "fp64":
             h.set_precision(precision)
         if edge_stage is not None:
             G, NV, U, _ = h.kernel_shape(amgd.AMGD_KERNEL_EDGE)
-            h.set_kernel_shape(amgd.AMGD_KERNEL_EDGE, G, NV, U, edge_stage)
+            h.set_kernel_shape(amgd.AMGD_KERNEL_EDGE, G, NV, edge_u or U, edge_stage)
         if color is not None:
             h.set_coloring(color)
         if w is not None:
@@ -236,14 +236,16 @@ def test_build_fp64_parity(name, K, target):
     compare_fp64(rp, col, val, got, want, theta)
 
 
-def test_build_fp64_mcgs_weights():
+@pytest.mark.parametrize("edge_stage,edge_u", [(None, None), (3, 8)])
+def test_build_fp64_mcgs_weights(edge_stage, edge_u):
     N = 48
     rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
     color = inputs.red_black(N)
     w = np.random.default_rng(0).uniform(0.5, 2.0, 16)
     for theta in (0.25, 0.5, 0.8):
         want = oracle.build(rp, col, val, 16, 1, 8, 1.0, theta, oracle.SWEEP_MCGS, color, w=w)
-        got = gpu_build(rp, col, val, 16, 1, 8, 1.0, theta, 1, color, w=w)
+        got = gpu_build(rp, col, val, 16, 1, 8, 1.0, theta, 1, color, w=w,
+                        edge_stage=edge_stage, edge_u=edge_u)
         compare_fp64(rp, col, val, got, want, theta, w)
 
 
@@ -274,6 +276,18 @@ def test_edge_tile_kernel_matches_oracle(K, target):
     for name, (rp, col, val) in _tile_edge_matrices():
         want = oracle.build(rp, col, val, K, 3, 3, 0.6, 0.5, mode=target)
         got = gpu_build(rp, col, val, K, 3, 3, 0.6, 0.5, target=target, edge_stage=1)
+        compare_fp64(rp, col, val, got, want, 0.5)
+
+
+@pytest.mark.parametrize("K,target,U", [(16, 0, 4), (8, 1, 8), (33, 0, 8), (5, 0, 4), (64, 0, 4)])
+def test_edge_warp_kernel_matches_oracle(K, target, U):
+    """The warp-staged distance kernel (edge stage 3) against the oracle: runs
+    of rows parked in the warp's shared-memory window and, for long rows, not
+    parked (graph_2000, the 5000-entry row), ragged last warps, rows without
+    off-diagonals and one-off-diagonal rows."""
+    for name, (rp, col, val) in _tile_edge_matrices():
+        want = oracle.build(rp, col, val, K, 3, 3, 0.6, 0.5, mode=target)
+        got = gpu_build(rp, col, val, K, 3, 3, 0.6, 0.5, target=target, edge_stage=3, edge_u=U)
         compare_fp64(rp, col, val, got, want, 0.5)
 
 
@@ -579,14 +593,21 @@ def test_batch_shard_keys(prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 @pytest.mark.parametrize("K", [5, 16, 64])
-def test_edge_stage2_shapes_agree(prec, K):
-    """The distance kernel on the sweeps' row order (edge stage 2), every
-    shape and both summation modes, against the row kernel (stage 0) on the
-    same vectors: FP64 within 1e-12 relative, mixed within 2e-5; strength
-    sets identical outside a band of 1e-4 around theta."""
-    N = 40
-    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
-    color = inputs.red_black(N)
+@pytest.mark.parametrize("mat", ["aniso9_40", "graph_2000"])
+def test_edge_inplace_shapes_agree(prec, K, mat):
+    """The distance kernels on the sweeps' row order -- the row kernel (edge
+    stage 2) and the warp-staged kernel (stage 3), every shape and both
+    summation modes -- against the row kernel (stage 0) on the same vectors:
+    FP64 within 1e-12 relative, mixed within 2e-5; strength sets identical
+    outside a band of 1e-4 around theta.  graph_2000's long rows overflow the
+    warp windows of stage 3."""
+    if mat == "aniso9_40":
+        N = 40
+        rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
+        color, sweep = inputs.red_black(N), amgd.AMGD_SWEEP_MCGS
+    else:
+        rp, col, val = MATRICES[mat]()
+        color, sweep = None, amgd.AMGD_SWEEP_JACOBI
     V = {"fp64": 2, "fp32": 4, "bf16": 8}[prec]
     P = 1
     while P * V < K:
@@ -595,10 +616,11 @@ def test_edge_stage2_shapes_agree(prec, K):
     def run(shape, summation="compensated"):
         with amgd.Handle(rp, col, val, K, 4) as h:
             h.set_precision(prec)
-            h.set_coloring(color)
+            if color is not None:
+                h.set_coloring(color)
             h.set_summation(summation)
             h.set_kernel_shape(amgd.AMGD_KERNEL_EDGE, *shape)
-            h.relax(3, 1.0, amgd.AMGD_SWEEP_MCGS)
+            h.relax(3, 1.0 if color is not None else 0.7, sweep)
             out = h.distances(0.5)
             s_rp, s_col = h.strength()
         return out, flags_from_strength(rp, col, s_rp, s_col)
@@ -606,17 +628,18 @@ def test_edge_stage2_shapes_agree(prec, K):
     ref, ref_flag = run((P, 1, 4, 0))
     off = ~np.isnan(ref["ls"])
     ref_w = dict(ls=ref["ls"], flag=ref_flag)
-    for nv in (1, 2, 4):
-        if P % nv:
-            continue
-        for u in (2, 4):
-            for summation in ("compensated", "plain"):
-                got, flag = run((P // nv, nv, u, 2), summation)
-                tol = 1e-12 if prec == "fp64" else 2e-5
-                rel = np.abs(got["ls"][off] - ref["ls"][off]) / np.maximum(ref["ls"][off], 1e-300)
-                assert rel.max() <= tol, (nv, u, summation, rel.max())
-                assert np.all(np.isnan(got["ls"][~off])) and np.all(got["a"][~off] == 0)
-                check_flags(flag, ref_w, rp, col, 0.5, 1e-4)
+    for stage, us in ((2, (2, 4)), (3, (4, 8))):
+        for nv in (1, 2, 4):
+            if P % nv:
+                continue
+            for u in us:
+                for summation in ("compensated", "plain"):
+                    got, flag = run((P // nv, nv, u, stage), summation)
+                    tol = 1e-12 if prec == "fp64" else 2e-5
+                    rel = np.abs(got["ls"][off] - ref["ls"][off]) / np.maximum(ref["ls"][off], 1e-300)
+                    assert rel.max() <= tol, (stage, nv, u, summation, rel.max())
+                    assert np.all(np.isnan(got["ls"][~off])) and np.all(got["a"][~off] == 0)
+                    check_flags(flag, ref_w, rp, col, 0.5, 1e-4)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16"])
