@@ -990,7 +990,8 @@ def main():
                                   "legend": "(lanes per row G, 16-byte vectors per lane NV, "
                                             "nonzeros per gather batch U, kernel: relaxation 0 "
                                             "direct / 1 TMA-staged CSR / 2 cp.async pipelined / "
-                                            "3 chunked per SM; distances 0 rows / 1 tiles), "
+                                            "3 chunked per SM; distances 0 rows / 1 tiles / "
+                                            "2 rows in place / 3 warp-staged in place), "
                                             "autotuned"}},
             "phase_ms": phases,
             "timed_region": ("start vectors (Philox) + nu recorded sweeps + distances + reverse "

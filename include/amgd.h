@@ -325,10 +325,12 @@ int amgd_graph_launch(amgd_handle h);
  *   with an evict-first and the vectors with an evict-last cache policy.
  *   For the distance pass, staged selects 0 the row
  *   kernel (G lanes per row), 1 the tile kernel (one thread per stored
- *   entry) or 2 the row kernel reading the vectors in the sweeps' row
- *   order in place (search depth 1: no caller-order copy of the vectors;
- *   U in {2,4}; the default).  With search depth d > 1 a stage-2 shape runs
- *   as stage 0.  Shapes change speed only, never results beyond the order of
+ *   entry), 2 the row kernel reading the vectors in the sweeps' row order
+ *   in place (search depth 1: no caller-order copy of the vectors; U in
+ *   {2,4}; the default) or 3 the warp-staged kernel on that order (each
+ *   warp gathers its rows' neighbour vectors once, G lanes per row, into a
+ *   shared-memory window and fits one stored entry per lane; U in {4,8}).
+ *   With search depth d > 1 a stage-2 or stage-3 shape runs as stage 0.  Shapes change speed only, never results beyond the order of
  *   the K-term LS sums.  kernel: AMGD_KERNEL_RELAX (the sweeps) or
  *   AMGD_KERNEL_EDGE (the distance pass); the shape applies to the current
  *   storage precision.

@@ -234,18 +234,17 @@ constexpr int edge_smem_bytes()
     return (kEdgeThreads / 32) * warp_slots<G>() * (2 * (int)sizeof(C) + 1);
 }
 
-// AMGD_EDGE_MINB: minimum resident blocks per SM asked of the compiler (0: none)
-#ifndef AMGD_EDGE_MINB
-#define AMGD_EDGE_MINB 3
-#endif
-#if AMGD_EDGE_MINB > 0
-#define AMGD_EDGE_BOUNDS __launch_bounds__(kEdgeThreads, AMGD_EDGE_MINB)
-#else
-#define AMGD_EDGE_BOUNDS __launch_bounds__(kEdgeThreads)
-#endif
+// resident blocks per SM asked of the compiler: three for the plain sums
+// (occupancy hides the gathers), two for the compensated ones (their extra
+// live words would otherwise spill)
+template <bool COMP>
+constexpr int edge_rows_min_blocks()
+{
+    return COMP ? 2 : 3;
+}
 
 template <class TS, int G, int NV, int U, bool UW, bool PX, bool COMP>
-__global__ void AMGD_EDGE_BOUNDS k_edge_rows(EdgeArgs A)
+__global__ void __launch_bounds__(kEdgeThreads, edge_rows_min_blocks<COMP>()) k_edge_rows(EdgeArgs A)
 {
     using S = Store<TS>;
     using C = typename S::C;
