@@ -59,6 +59,10 @@ typedef struct amgd_ctx *amgd_handle;
 #define AMGD_ERR_TIMEOUT     -8   /* a bounded device wait gave up; reported by the
                                      next call that synchronises the stream     */
 #define AMGD_ERR_UNSUPPORTED -9   /* size or mode outside the supported range   */
+#define AMGD_ERR_CHECK       -10  /* checked build only: a gather index (column
+                                     index or row map) failed its bounds test;
+                                     reported by the next call that synchronises
+                                     the stream, the results are not valid      */
 
 /* where caller arrays live */
 #define AMGD_MEM_HOST   0
@@ -533,6 +537,12 @@ int amgd_destroy(amgd_handle h);
 
 /* Static text of a status code. */
 const char *amgd_status_string(int status);
+
+/* 1 when this library is the checked build (libamgd_checked.so: every gather
+ * index of the sweep and distance kernels is tested against the vector block
+ * before its load; a failure is reported as AMGD_ERR_CHECK), else 0.  The
+ * checked build is for tests; it is slower and computes the same results. */
+int amgd_checked_build(void);
 
 /* Message of the last error of h, or, when h is NULL, of the last failed
  * amgd_create / amgd_create_batch / amgd_strength_noalloc on this thread.

@@ -16,6 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libamgd.so")
+# the checked build: every gather index of the sweep and distance kernels is
+# bounds-tested in the kernel (AMGD_CHECKS); for tests, loaded with AMGD_CHECKED=1
+LIB_CHECKED = os.path.join(LIBDIR, "libamgd_checked.so")
 SOURCES = ["amgd_api.cu", "k_relax.cu", "k_edge.cu", "k_edge_f64.cu", "k_edge_f32.cu",
            "k_edge_f32c.cu", "k_edge_bf16.cu", "k_edge_bf16c.cu", "k_init.cu", "k_compact.cu",
            "amgd_noalloc.cu", "k_adjoint.cu", "k_interp.cu", "k_cr.cu"]
@@ -38,14 +41,16 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list | None = None,
+          checked: bool = False) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
+    lib = LIB_CHECKED if checked else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
     cc = nvcc()
-    objdir = os.path.join(LIBDIR, "obj")
+    objdir = os.path.join(LIBDIR, "obj_checked" if checked else "obj")
     os.makedirs(objdir, exist_ok=True)
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DAMGD_CHECKS=1"] if checked else [])
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
@@ -62,15 +67,15 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     if errs:
         msg = "\n".join("== %s\n%s%s" % (s, p.stdout, p.stderr) for s, p in errs)
         raise RuntimeError("nvcc failed:\n" + msg)
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [cc, *ARCH, "-shared", "-o", tmp] + [o for _, o, _ in results] + ["-cudart", "static"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError("link failed:\n" + p.stdout + p.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True,
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv,
                 extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))

@@ -19,7 +19,11 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libamgd.so")
+# AMGD_CHECKED=1 loads the checked build (every gather index bounds-tested in
+# the kernels; failures reported as AMGD_ERR_CHECK), built by
+# _build.build(checked=True)
+LIB_PATH = os.path.join(_HERE, "_lib", "libamgd_checked.so" if os.environ.get("AMGD_CHECKED") == "1"
+                        else "libamgd.so")
 
 AMGD_OK = 0
 AMGD_ERR_ARG = -1
@@ -31,6 +35,7 @@ AMGD_ERR_STATE = -6
 AMGD_ERR_CAPACITY = -7
 AMGD_ERR_TIMEOUT = -8
 AMGD_ERR_UNSUPPORTED = -9
+AMGD_ERR_CHECK = -10
 
 AMGD_MEM_HOST = 0
 AMGD_MEM_DEVICE = 1
@@ -95,6 +100,7 @@ SIGNATURES = {
     "amgd_destroy": (_int, [_P]),
     "amgd_status_string": (ctypes.c_char_p, [_int]),
     "amgd_last_error": (ctypes.c_char_p, [_P]),
+    "amgd_checked_build": (_int, []),
 }
 
 _lib = None
@@ -105,8 +111,7 @@ def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libamgd.so is not built (%s); run __graft_entry__.build()"
-                               % LIB_PATH)
+            raise RuntimeError("%s is not built; run __graft_entry__.build()" % LIB_PATH)
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             f = getattr(L, name)

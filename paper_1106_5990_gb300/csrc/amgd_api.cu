@@ -236,6 +236,10 @@ int poll_status(amgd_ctx *h)
     CK(h, cudaStreamSynchronize(h->stream));
     if (st) {
         CK(h, cudaMemsetAsync(h->status, 0, sizeof st, h->stream));
+        if (st & kStatusIndexRange)
+            return fail(h, AMGD_ERR_CHECK,
+                        "a gather index (a column index or row map of the matrix) was out of "
+                        "range; the results are not valid (checked build)");
         return fail(h, AMGD_ERR_TIMEOUT,
                     "a staged relaxation kernel gave up waiting for its shared-memory copies; "
                     "the test vectors are not valid");
@@ -374,6 +378,7 @@ int run_relax(amgd_ctx *h, int32_t nu, double omega, int sweep, cudaStream_t s)
     a.Kp = Kp_of(h->storage, h->K);
     a.omega = omega;
     a.avg_nnz = h->n ? (float)((double)h->nnz / (double)h->n) : 0.f;
+    a.nrows = (int32_t)h->n;
     for (int32_t it = 0; it < nu; ++it) {
         a.xold = h->x[h->cur];
         a.xnew = h->x[1 - h->cur];
@@ -424,6 +429,7 @@ int jacobi_step(amgd_ctx *h, const void *src, void *dst, double omega, cudaStrea
     a.Kp = Kp_of(h->storage, h->K);
     a.omega = omega;
     a.avg_nnz = h->n ? (float)((double)h->nnz / (double)h->n) : 0.f;
+    a.nrows = (int32_t)h->n;
     a.xold = src;
     a.xnew = dst;
     a.r0 = 0;
@@ -505,6 +511,7 @@ int run_edge(amgd_ctx *h, double theta, cudaStream_t s)
         a.xcol = h->perm ? h->colx : h->col_o;
     }
     a.compensated = h->summation == AMGD_SUM_COMPENSATED;
+    a.status = h->status;
     bool unit_w = true;
     for (double wk : h->h_w) unit_w = unit_w && wk == 1.0;
     CK(h, launch_edge(h->storage, sh, unit_w, a, s));
@@ -680,6 +687,19 @@ int create_impl(int32_t nmat, const int64_t *const *rp_in, const int32_t *const 
     if ((rc = upload_weights(h)) != AMGD_OK) return bail(rc);
     if ((rc = run_init(h, seed, h->stream)) != AMGD_OK) return bail(rc);
     TRY(cudaStreamSynchronize(h->stream));
+#if AMGD_CHECKS
+    // checked build only: AMGD_TEST_BAD_COLUMN=<slot> stores the out-of-range
+    // column index n + 1000 at that slot of the sweeps' pattern after every
+    // setup kernel has run, so a test can watch a gather's bounds test fire
+    // (the next synchronising call returns AMGD_ERR_CHECK)
+    if (const char *e = getenv("AMGD_TEST_BAD_COLUMN")) {
+        const long long slot = atoll(e);
+        if (slot >= 0 && slot < h->nnz) {
+            const int32_t bad = (int32_t)n + 1000;
+            TRY(cudaMemcpy(h->col_p + slot, &bad, sizeof bad, cudaMemcpyHostToDevice));
+        }
+    }
+#endif
 #undef TRY
     *out = h;
     return AMGD_OK;
@@ -2150,6 +2170,11 @@ int amgd_destroy(amgd_handle h)
     return AMGD_OK;
 }
 
+int amgd_checked_build(void)
+{
+    return AMGD_CHECKS ? 1 : 0;
+}
+
 const char *amgd_status_string(int status)
 {
     switch (status) {
@@ -2163,6 +2188,7 @@ const char *amgd_status_string(int status)
     case AMGD_ERR_CAPACITY: return "AMGD_ERR_CAPACITY: output buffer too small";
     case AMGD_ERR_TIMEOUT: return "AMGD_ERR_TIMEOUT: bounded device wait gave up";
     case AMGD_ERR_UNSUPPORTED: return "AMGD_ERR_UNSUPPORTED: size or mode not supported";
+    case AMGD_ERR_CHECK: return "AMGD_ERR_CHECK: an index failed its bounds test (checked build)";
     }
     return "unknown status";
 }

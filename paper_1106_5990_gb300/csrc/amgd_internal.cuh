@@ -166,8 +166,32 @@ inline int current_device_index()
     return d;
 }
 
-// device status bits set by bounded waits that gave up
+// device status bits: a bounded wait that gave up; an index that failed its
+// bounds test (checked build)
 constexpr uint32_t kStatusStagingTimeout = 1u;
+constexpr uint32_t kStatusIndexRange = 2u;
+
+// Checked build (compiled with -DAMGD_CHECKS=1 into libamgd_checked.so): the
+// row index of every gather the sweep and distance kernels make -- a column
+// index of the matrix, a renumbered column or a row map -- is tested against
+// the vector block before the load.  An index outside [0, rows) sets
+// kStatusIndexRange in the handle's device status word and is replaced by row
+// 0, so the load stays in bounds; the results are then invalid and the next
+// synchronising call returns AMGD_ERR_CHECK.  The normal build compiles the
+// test away.
+#ifndef AMGD_CHECKS
+#define AMGD_CHECKS 0
+#endif
+__device__ __forceinline__ int64_t checked_row(int64_t j, int64_t rows, uint32_t *status)
+{
+#if AMGD_CHECKS
+    if (j < 0 || j >= rows) {
+        if (status) atomicOr(status, kStatusIndexRange);
+        return 0;
+    }
+#endif
+    return j;
+}
 
 // ---------------------------------------------------------------------------
 // launch arguments
@@ -187,6 +211,7 @@ struct RelaxArgs {
     int32_t Kp;           // padded row stride (elements)
     double omega;
     float avg_nnz = 0.f;  // stored entries per row of the whole matrix
+    int32_t nrows = 0;    // rows of the vector block (the range of a gather index)
 };
 
 struct EdgeArgs {                // everything in the caller's numbering
@@ -213,6 +238,7 @@ struct EdgeArgs {                // everything in the caller's numbering
     // the vector row of the column of caller slot p
     const int32_t *xrow = nullptr, *xcol = nullptr;
     bool compensated = false;    // mixed paths of stage 2: compensated FP32 LS sums
+    uint32_t *status = nullptr;  // device status word (checked build: index range)
 };
 
 // row tiles of the edge pass: consecutive rows, at most kEdgeTileRows rows and

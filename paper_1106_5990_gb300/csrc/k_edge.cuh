@@ -298,9 +298,9 @@ __global__ void __launch_bounds__(kEdgeThreads, edge_rows_min_blocks<COMP>()) k_
         C y[NV][V];
         {
             Acc<C, V> acc[NV];
-            row_sum<TS, G, NV, U, false>(xcol, val, X, X, 0, Kp, lane, p0, p1, acc);
+            row_sum<TS, G, NV, U, false>(xcol, val, X, X, 0, Kp, lane, p0, p1, acc, A.n, A.status);
             const C d = C(1) / diag;
-            const int64_t xr = (PX && A.xrow) ? (int64_t)__ldg(A.xrow + r) : r;
+            const int64_t xr = (PX && A.xrow) ? checked_row(__ldg(A.xrow + r), A.n, A.status) : r;
 #pragma unroll
             for (int t = 0; t < NV; ++t) {
                 S::unpack(ldg16(X + xr * Kp + (t * G + lane) * V), y[t]);     // x_i
@@ -338,7 +338,8 @@ __global__ void __launch_bounds__(kEdgeThreads, edge_rows_min_blocks<COMP>()) k_
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (jj[u] >= 0 && jj[u] != r) {
-                    const int64_t xj = PX ? (int64_t)__ldg(xcol + pb + u) : (int64_t)jj[u];
+                    const int64_t xj = checked_row(PX ? (int64_t)__ldg(xcol + pb + u) : (int64_t)jj[u],
+                                                   A.n, A.status);
                     if constexpr (G == 1 && NV % 2 == 0) {       // whole row per lane: 32-byte pairs
 #pragma unroll
                         for (int t = 0; t < NV; t += 2) ldg32(X + xj * Kp + t * V, raw[u][t], raw[u][t + 1]);
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
             for (int t = 0; t < NV; ++t) S::unpack(ldg16(X + r * KP + (t * G + lane) * V), y[t]);
             if (A.target == 0) {
                 Acc<C, V> acc[NV];
-                row_sum<TS, G, NV, U, false>(col, val, X, X, 0, KP, lane, p0, p1, acc);
+                row_sum<TS, G, NV, U, false>(col, val, X, X, 0, KP, lane, p0, p1, acc, A.n, A.status);
                 const C d = C(1) / dg[rl];
 #pragma unroll
                 for (int t = 0; t < NV; ++t)
@@ -591,7 +592,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
     C *ls_out = (C *)A.ls_out;
     // the fit of slot p (row rl, column j) from the pieces `hold` of x_j
     auto fit = [&](int rl, int j, const uint4 (&hold)[HOLD], C &a_, C &ls_) {
-        const TS *xj = X + (int64_t)j * KP;
+        const TS *xj = X + checked_row(j, A.n, A.status) * KP;
         const C *yr = ys + rl * KP;
         if constexpr (COMP && kMixed) {
             // compensated sums over all K components in this thread
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
                 rls[q] = single ? 0 : srow[p - S0];
                 js[q] = __ldg(A.pcol + p);
                 if (P <= 4 && js[q] != R0 + rls[q] && js[q] != j1s[rls[q]]) {
-                    const TS *xj = X + (int64_t)js[q] * KP;
+                    const TS *xj = X + checked_row(js[q], A.n, A.status) * KP;
                     if constexpr (HOLD % 2 == 0) {                  // 32-byte pairs
 #pragma unroll
                         for (int c = 0; c < HOLD; c += 2) ldg32(xj + c * V, hold[q][c], hold[q][c + 1]);
@@ -744,7 +745,7 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
     const int Kp = A.Kp;
     // vector row of caller row i and of the neighbour of slot p (stage 2: the
     // sweeps' row order; search depth 1, so the fit slots are A's slots)
-    auto xrow = [&](int64_t i) -> int64_t { return (PX && A.xrow) ? (int64_t)A.xrow[i] : i; };
+    auto xrow = [&](int64_t i) -> int64_t { return (PX && A.xrow) ? checked_row(A.xrow[i], A.n, A.status) : i; };
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; q < count; q += warps) {
         const int64_t r = A.defer_list[q];
@@ -766,7 +767,7 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
             const double xi = k < Kp ? elem64(X + xrow(r) * Kp + k) : 0.0;
             if (k < Kp)
                 for (int p = p0; p < p1; ++p)
-                    acc = fma(A.val64[p], elem64(X + (int64_t)(PX ? A.xcol[p] : A.col[p]) * Kp + k), acc);
+                    acc = fma(A.val64[p], elem64(X + checked_row(PX ? A.xcol[p] : A.col[p], A.n, A.status) * Kp + k), acc);
             y[h] = (A.target == 0) ? fma(-d, acc, xi) : xi;
         }
         double m = INFINITY;
@@ -783,7 +784,7 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
                 ls64 = 0.0;
             } else {
                 double xj[2], sxx = 0.0, syx = 0.0;
-                const int64_t xjr = PX ? (int64_t)A.xcol[p] : j;
+                const int64_t xjr = checked_row(PX ? (int64_t)A.xcol[p] : j, A.n, A.status);
                 for (int h = 0; h < 2; ++h) {
                     const int k = lane + 32 * h;
                     xj[h] = k < Kp ? elem64(X + xjr * Kp + k) : 0.0;

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kWarpEdgeThreads) k_edge_warp(EdgeArgs A)
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (jj[u] >= 0) {
-                    const TS *src = X + (int64_t)jj[u] * Kp;
+                    const TS *src = X + checked_row(jj[u], A.n, A.status) * Kp;
 #pragma unroll
                     for (int t = 0; t < NV; ++t) raw[u][t] = ldg16(src + (t * G + lane) * V);
                 }
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kWarpEdgeThreads) k_edge_warp(EdgeArgs A)
             }
         }
         const C d = C(1) / diag;
-        const int64_t xr = A.xrow ? (int64_t)__ldg(A.xrow + r) : r;
+        const int64_t xr = A.xrow ? checked_row(__ldg(A.xrow + r), A.n, A.status) : r;
         C y[NV][V];
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kWarpEdgeThreads) k_edge_warp(EdgeArgs A)
                 ls_ = C(0);
             } else {
                 const C *yr = ys + rl * L::YST;
-                const TS *xg = PK ? nullptr : X + (int64_t)__ldg(xcol + p) * Kp;
+                const TS *xg = PK ? nullptr : X + checked_row(__ldg(xcol + p), A.n, A.status) * Kp;
                 auto piece = [&](int c) -> uint4 {
                     if constexpr (PK) return xs[park_index<P>(s, c)];
                     else return ldg16(xg + c * V);

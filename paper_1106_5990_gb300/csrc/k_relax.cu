@@ -55,7 +55,8 @@ __global__ void AMGD_RELAX_BOUNDS k_relax(RelaxArgs A)
 
     const int p0 = ld_csr(A.rp + r), p1 = ld_csr(A.rp + r + 1);
     Acc<C, V> acc[NV];
-    row_sum<TS, G, NV, U, SPLIT>(A.col, (const AV *)A.val, xold, xnew, A.split, Kp, lane, p0, p1, acc);
+    row_sum<TS, G, NV, U, SPLIT>(A.col, (const AV *)A.val, xold, xnew, A.split, Kp, lane, p0, p1, acc,
+                                 A.nrows, A.status);
     const C c = (C)A.omega / ld_csr((const AV *)A.diag + r);
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
@@ -198,7 +199,7 @@ k_relax_staged(RelaxArgs A)
                 uint4 *dst = land[lb] + (size_t)grp * kLandRows * (G * NV);
                 for (int p = p0; p < p1; ++p) {
                     const int j = col_s[stg][p - tl.s0a];
-                    const TS *src = (j < A.split ? (const TS *)xnew : xold) + (int64_t)j * Kp;
+                    const TS *src = (j < A.split ? (const TS *)xnew : xold) + checked_row(j, A.nrows, A.status) * Kp;
 #pragma unroll
                     for (int tt = 0; tt < NV; ++tt)
                         cp_async16(dst + (p - p0) * (G * NV) + tt * G + lane, src + (tt * G + lane) * V);
@@ -260,7 +261,7 @@ k_relax_staged(RelaxArgs A)
                 C v;
                 if (cur.staged) { j = col_s[stg][p - cur.s0a]; v = (C)val_s[stg][p - cur.s0a]; }
                 else { j = __ldg(col + p); v = (C)__ldg(val + p); }
-                const TS *src = (j < A.split ? (const TS *)xnew : xold) + (int64_t)j * Kp;
+                const TS *src = (j < A.split ? (const TS *)xnew : xold) + checked_row(j, A.nrows, A.status) * Kp;
 #pragma unroll
                 for (int tt = 0; tt < NV; ++tt) {
                     const uint4 raw = landed ? lsrc[(p - p0) * (G * NV) + tt * G + lane]
@@ -391,7 +392,7 @@ k_relax_pipe(RelaxArgs A, int64_t chunk)
         uint4 *dst = land_b[k & 1] + (size_t)rig * kPipeMaxNnz * P;
         for (int p = p0; p < p1; ++p) {
             const int j = cb[p - s0a];
-            const TS *src = (j < split ? (const TS *)xnew : xold) + (int64_t)j * Kp;
+            const TS *src = (j < split ? (const TS *)xnew : xold) + checked_row(j, A.nrows, A.status) * Kp;
 #pragma unroll
             for (int tt = 0; tt < NV; ++tt)
                 cp_async16(dst + (p - p0) * P + tt * G + lane, src + (tt * G + lane) * V);
@@ -440,7 +441,7 @@ k_relax_pipe(RelaxArgs A, int64_t chunk)
                     if (landed) {
                         raw = lsrc[(p - p0) * P + tt * G + lane];
                     } else {
-                        const TS *src = (j < split ? (const TS *)xnew : xold) + (int64_t)j * Kp;
+                        const TS *src = (j < split ? (const TS *)xnew : xold) + checked_row(j, A.nrows, A.status) * Kp;
                         raw = ldg16(src + (tt * G + lane) * V);
                     }
                     C x[V];
@@ -606,7 +607,7 @@ __global__ void __launch_bounds__(kChunkThreads, 1) k_relax_chunk(RelaxArgs A, i
                 for (int u = 0; u < U; ++u) {
                     if (jj[u] >= 0) {
                         const TS *src = (SPLIT && jj[u] < A.split ? (const TS *)xnew : xold) +
-                                        (int64_t)jj[u] * Kp;
+                                        checked_row(jj[u], A.nrows, A.status) * Kp;
                         if constexpr (W32) {
 #pragma unroll
                             for (int tt = 0; tt < NV; tt += 2)

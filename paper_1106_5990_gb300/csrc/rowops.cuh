@@ -53,6 +53,7 @@ template <int V> struct Acc<float, V> {
 
 // s[tt][e] = sum_{p in [p0,p1)} val[p] * X[col[p]] (lane's pieces), in CSR
 // order.  SPLIT: rows j < split are read from xnew, the others from xold.
+// rows, status: the gather range and status word of the checked build.
 // Nonzeros are taken U at a time: U column indices and values, then all U
 // gathers in flight before any is consumed.  A lane that owns a whole row
 // (G = 1, NV even) reads it in 32-byte pairs: the rows are 32-byte aligned.
@@ -61,7 +62,8 @@ __device__ __forceinline__ void row_sum(const int32_t *__restrict__ col,
                                         const typename Store<TS>::A *__restrict__ val,
                                         const TS *__restrict__ xold, const TS *__restrict__ xnew,
                                         int split, int Kp, int lane, int p0, int p1,
-                                        Acc<typename Store<TS>::C, Store<TS>::V> (&acc)[NV])
+                                        Acc<typename Store<TS>::C, Store<TS>::V> (&acc)[NV],
+                                        int64_t rows, uint32_t *status)
 {
     using S = Store<TS>;
     using C = typename S::C;
@@ -81,7 +83,7 @@ __device__ __forceinline__ void row_sum(const int32_t *__restrict__ col,
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (jj[u] >= 0) {
-                const TS *src = (SPLIT && jj[u] < split ? xnew : xold) + (int64_t)jj[u] * Kp;
+                const TS *src = (SPLIT && jj[u] < split ? xnew : xold) + checked_row(jj[u], rows, status) * Kp;
                 if constexpr (G == 1 && NV % 2 == 0) {
 #pragma unroll
                     for (int tt = 0; tt < NV; tt += 2) ldg32(src + tt * V, raw[u][tt], raw[u][tt + 1]);

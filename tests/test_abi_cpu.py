@@ -163,7 +163,14 @@ def test_noalloc_rejects_arguments_on_the_host(L):
 
 # entry points whose first argument is not a handle, or that accept a NULL one
 _NOT_HANDLE_FIRST = {"amgd_create", "amgd_create_batch", "amgd_destroy", "amgd_strength_noalloc",
-                     "amgd_status_string", "amgd_last_error"}
+                     "amgd_status_string", "amgd_last_error", "amgd_checked_build"}
+
+
+def test_checked_build_flag(L):
+    """The library the tests load by default is the normal build; its
+    status text covers the checked build's error code."""
+    assert L.amgd_checked_build() == 0
+    assert amgd.amgd_status_string(amgd.AMGD_ERR_CHECK).startswith("AMGD_ERR_CHECK")
 
 
 @pytest.mark.parametrize("name", sorted(set(amgd.SIGNATURES) - _NOT_HANDLE_FIRST))
