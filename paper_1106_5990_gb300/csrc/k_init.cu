@@ -52,9 +52,11 @@ template <> __device__ __forceinline__ double to_double<__nv_bfloat16>(__nv_bflo
 // The start value of a component is x = d * 2^-32 with the odd integer
 // d = 2m + 1 - 2^32, m the component's 32-bit random integer.  |d| < 2^32,
 // so the magnitude a = |d| fits 32 bits: a = 2(m - 2^31) + 1 for m >= 2^31
-// (d > 0), a = 2(2^31 - 1 - m) + 1 otherwise (d < 0).  The value is built
-// in the storage type with 32-bit integer work (the GPU's FP64 pipe is
-// narrow) and rounded to nearest even exactly once.
+// (d > 0), a = 2(2^31 - 1 - m) + 1 otherwise (d < 0).  The FP64 and BF16
+// values are built as raw bits with 32-bit integer work (the GPU's FP64 pipe
+// is narrow; an FP32 step before BF16 would round twice), the FP32 value by
+// the hardware's integer-to-FP32 conversion; either way rounded to nearest
+// even exactly once.
 __device__ __forceinline__ uint32_t start_magnitude(uint32_t m, bool &neg)
 {
     neg = (m & 0x80000000u) == 0u;
@@ -97,11 +99,13 @@ template <> struct StartBits<double> {
 };
 template <> struct StartBits<float> {
     using Raw = uint32_t;
+    // the odd integer d = 2m + 1 - 2^32 converted to FP32 by the hardware's
+    // correctly rounded (nearest-even) integer conversion, then scaled by
+    // 2^-32 exactly (|d| >= 1: every value is normal): the same single
+    // rounding as the bit assembly of the other storages, in two instructions
     __device__ __forceinline__ static Raw get(uint32_t m) {
-        bool neg;
-        uint32_t mant;
-        const uint32_t e = encode_fields<23, 127>(start_magnitude(m, neg), mant);
-        return (neg ? 0x80000000u : 0u) | (e << 23) | mant;
+        const long long d = 2ll * (long long)m + 1ll - (1ll << 32);
+        return __float_as_uint(__ll2float_rn(d) * 0x1p-32f);
     }
 };
 template <> struct StartBits<__nv_bfloat16> {
