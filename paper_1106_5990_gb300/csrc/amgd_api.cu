@@ -35,6 +35,7 @@ struct amgd_ctx {
     int32_t *diag_slot = nullptr;                // slot of each row's diagonal
     uint32_t *err_word = nullptr;                // device error bits of value checks
     uint32_t *status = nullptr;                  // device status bits of bounded waits
+    bool perm64_stale = false;                   // row-permuted FP64 values / diagonal out of date
     long long wait_limit = 2000000000LL;         // cycles (about 1 s) per staged wait
     uint32_t test_extra_tx = 0;                  // test hook, see amgd_create
     // device: row-permuted matrix (aliases of the caller arrays without coloring)
@@ -334,15 +335,35 @@ int upload_weights(amgd_ctx *h)
 // kernels read -- the caller FP64 array, the FP32 copies and, with a
 // coloring, the row-permuted arrays -- in one coalesced pass, then the
 // diagonals in caller and permuted order.
-int permute_values(amgd_ctx *h, const double *src = nullptr)
+// Every value copy from the caller-order values (src, or the handle's own
+// FP64 copy when NULL).  The row-permuted FP64 copy and diagonal feed only the
+// FP64 sweeps and the coarsening; with mixed storage they are left stale here
+// and refreshed by refresh_perm64 when one of those next runs.  err (NULL:
+// none) collects the value checks of an asynchronous update.
+int permute_values(amgd_ctx *h, const double *src = nullptr, uint32_t *err = nullptr)
 {
     const bool in_place = src == nullptr;
+    const bool mixed = h->storage != ST_FP64;
     float *v32o = (h->val32_o && h->val32_o != h->val32) ? h->val32_o : nullptr;
-    double *vp64 = h->perm ? h->val64 : nullptr;        // without a coloring val64 is val_o
+    double *vp64 = (h->perm && !mixed) ? h->val64 : nullptr;   // without a coloring val64 is val_o
     CK(h, launch_scatter_values(in_place ? h->val_o : src, h->nnz, h->perm ? h->slot_perm : nullptr,
-                                in_place ? nullptr : h->val_o, v32o, vp64, h->val32, h->stream));
+                                in_place ? nullptr : h->val_o, v32o, vp64, h->val32, h->stream, err));
     CK(h, launch_diag_values(h->val_o, h->diag_slot, h->perm, (int32_t)h->n, h->diag64_o,
-                             h->diag32_o, h->diag64, h->diag32, h->stream));
+                             h->diag32_o, mixed ? nullptr : h->diag64, h->diag32, h->stream, err));
+    h->perm64_stale = mixed;
+    return AMGD_OK;
+}
+
+// bring the row-permuted FP64 values and diagonal up to date (stream order)
+int refresh_perm64(amgd_ctx *h, cudaStream_t s)
+{
+    if (!h->perm64_stale) return AMGD_OK;
+    if (h->perm)
+        CK(h, launch_scatter_values(h->val_o, h->nnz, h->slot_perm, nullptr, nullptr, h->val64,
+                                    nullptr, s));
+    CK(h, launch_diag_values(h->val_o, h->diag_slot, h->perm, (int32_t)h->n, nullptr, nullptr,
+                             h->diag64, nullptr, s));
+    h->perm64_stale = false;
     return AMGD_OK;
 }
 
@@ -367,6 +388,10 @@ int run_init(amgd_ctx *h, uint64_t seed, cudaStream_t s)
 int run_relax(amgd_ctx *h, int32_t nu, double omega, int sweep, cudaStream_t s)
 {
     const Shape sh = h->relax_shape[h->storage];
+    if (h->storage == ST_FP64 && nu > 0) {
+        const int rc = refresh_perm64(h, s);
+        if (rc != AMGD_OK) return rc;
+    }
     RelaxArgs a;
     a.status = h->status;
     a.wait_limit = h->wait_limit;
@@ -418,6 +443,10 @@ cudaError_t ensure_buf(void **p, size_t &have, size_t bytes)
 // relaxation shape (bit-identical to the sweeps of run_relax).
 int jacobi_step(amgd_ctx *h, const void *src, void *dst, double omega, cudaStream_t s)
 {
+    if (h->storage == ST_FP64) {
+        const int rc = refresh_perm64(h, s);
+        if (rc != AMGD_OK) return rc;
+    }
     RelaxArgs a;
     a.status = h->status;
     a.wait_limit = h->wait_limit;
@@ -1060,8 +1089,9 @@ int amgd_set_values_async(amgd_handle h, const double *val, int mem)
                           h->up_stream));
     CK(h, cudaEventRecord(h->ev_up[k], h->up_stream));
     CK(h, cudaStreamWaitEvent(h->stream, h->ev_up[k], 0));
-    CK(h, launch_check_values(h->stage[k], h->nnz, h->diag_slot, (int32_t)h->n, h->async_err, h->stream));
-    rc = permute_values(h, h->stage[k]);
+    // the value checks ride on the copies (their bits land in the error word
+    // the next synchronising call reads)
+    rc = permute_values(h, h->stage[k], h->async_err);
     if (rc != AMGD_OK) return rc;
     CK(h, cudaEventRecord(h->ev_used[k], h->stream));
     h->async_pending = true;
@@ -1738,6 +1768,10 @@ int amgd_cr_coarsen(amgd_handle h, uint8_t *coarse, int coarse_mem, const double
                           coarse_mem == AMGD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     if (!h->cr_coarse_p) CK(h, dalloc(&h->cr_coarse_p, (size_t)n));
     if (!h->cr_cdiag) CK(h, dalloc(&h->cr_cdiag, (size_t)n));
+    {
+        const int rc = refresh_perm64(h, s);
+        if (rc != AMGD_OK) return rc;
+    }
     CrArgs a;
     a.rp = h->rp_p;
     a.col = h->col_p;

@@ -290,15 +290,16 @@ cudaError_t launch_permute_values(const double *v, const int32_t *rp_orig,
 
 // one coalesced pass over caller-order values src[nnz] into the caller FP64 /
 // FP32 copies and the row-permuted FP64 / FP32 copies (NULL targets skipped;
-// slot_perm NULL = identity)
+// slot_perm NULL = identity); err (NULL: none) |= 1 for a non-finite value
 cudaError_t launch_scatter_values(const double *src, int64_t nnz, const int32_t *slot_perm,
                                   double *val_o, float *val32_o, double *vp64, float *vp32,
-                                  cudaStream_t s);
+                                  cudaStream_t s, uint32_t *err = nullptr);
 // diagonals (diag_slot = caller slot of each row's diagonal) in caller order
-// and in permuted order
+// and in permuted order (NULL targets skipped); err (NULL: none) |= 2 for a
+// zero diagonal
 cudaError_t launch_diag_values(const double *v, const int32_t *diag_slot, const int32_t *perm,
                                int32_t n, double *d64_o, float *d32_o, double *d64_p, float *d32_p,
-                               cudaStream_t s);
+                               cudaStream_t s, uint32_t *err = nullptr);
 
 // value check of a staged val[nnz]: err |= 1 for a non-finite value, |= 2 for
 // a zero diagonal (diag_slot[n] = slot of each row's diagonal)

@@ -273,15 +273,18 @@ __global__ void k_check_values(const double *__restrict__ v, int64_t nnz,
 
 // one pass over the stored values in caller order (coalesced): the FP64
 // caller copy, the FP32 caller copy and the row-permuted FP64 / FP32 copies
-// (slot_perm[p] = permuted slot of caller slot p); NULL targets are skipped
+// (slot_perm[p] = permuted slot of caller slot p); NULL targets are skipped.
+// err (NULL: no check): bit 0 set when a value is not finite.
 __global__ void k_scatter_values(const double *__restrict__ src, int64_t nnz,
                                  const int32_t *__restrict__ slot_perm, double *__restrict__ val_o,
                                  float *__restrict__ val32_o, double *__restrict__ vp64,
-                                 float *__restrict__ vp32)
+                                 float *__restrict__ vp32, uint32_t *__restrict__ err)
 {
+    bool bad = false;
     for (int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x; p < nnz;
          p += (int64_t)gridDim.x * kThreads) {
         const double x = src[p];
+        bad = bad || !isfinite(x);
         const float f = (float)x;
         if (val_o) val_o[p] = x;
         if (val32_o) val32_o[p] = f;
@@ -289,22 +292,31 @@ __global__ void k_scatter_values(const double *__restrict__ src, int64_t nnz,
         if (vp64) vp64[q] = x;
         if (vp32) vp32[q] = f;
     }
+    if (err && __any_sync(0xffffffffu, bad) && (threadIdx.x % 32) == 0) atomicOr(err, 1u);
 }
 
-// diagonals in caller order and in permuted order (perm[r] = caller row of r)
+// diagonals in caller order and in permuted order (perm[r] = caller row of r);
+// NULL targets are skipped.  err (NULL: no check): bit 1 set on a zero
+// diagonal.
 __global__ void k_diag_values(const double *__restrict__ v, const int32_t *__restrict__ diag_slot,
                               const int32_t *__restrict__ perm, int32_t n, double *__restrict__ d64_o,
                               float *__restrict__ d32_o, double *__restrict__ d64_p,
-                              float *__restrict__ d32_p)
+                              float *__restrict__ d32_p, uint32_t *__restrict__ err)
 {
     const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (t >= n) return;
-    const double d = v[diag_slot[t]];
-    d64_o[t] = d;
-    d32_o[t] = (float)d;
-    const double dp = perm ? v[diag_slot[perm[t]]] : d;
-    d64_p[t] = dp;
-    d32_p[t] = (float)dp;
+    bool zero = false;
+    if (t < n) {
+        const double d = v[diag_slot[t]];
+        zero = d == 0.0;
+        if (d64_o) d64_o[t] = d;
+        if (d32_o) d32_o[t] = (float)d;
+        if (d64_p || d32_p) {
+            const double dp = perm ? v[diag_slot[perm[t]]] : d;
+            if (d64_p) d64_p[t] = dp;
+            if (d32_p) d32_p[t] = (float)dp;
+        }
+    }
+    if (err && __any_sync(0xffffffffu, zero) && (threadIdx.x % 32) == 0) atomicOr(err, 2u);
 }
 
 inline unsigned blocks(int64_t work) { return (unsigned)((work + kThreads - 1) / kThreads); }
@@ -450,21 +462,22 @@ cudaError_t launch_check_values(const double *v, int64_t nnz, const int32_t *dia
 
 cudaError_t launch_scatter_values(const double *src, int64_t nnz, const int32_t *slot_perm,
                                   double *val_o, float *val32_o, double *vp64, float *vp32,
-                                  cudaStream_t s)
+                                  cudaStream_t s, uint32_t *err)
 {
     if (nnz == 0) return cudaSuccess;
     const int64_t want = (nnz + kThreads - 1) / kThreads;
     k_scatter_values<<<(unsigned)(want < 152 * 16 ? want : 152 * 16), kThreads, 0, s>>>(
-        src, nnz, slot_perm, val_o, val32_o, vp64, vp32);
+        src, nnz, slot_perm, val_o, val32_o, vp64, vp32, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_diag_values(const double *v, const int32_t *diag_slot, const int32_t *perm,
                                int32_t n, double *d64_o, float *d32_o, double *d64_p, float *d32_p,
-                               cudaStream_t s)
+                               cudaStream_t s, uint32_t *err)
 {
     if (n == 0) return cudaSuccess;
-    k_diag_values<<<blocks(n), kThreads, 0, s>>>(v, diag_slot, perm, n, d64_o, d32_o, d64_p, d32_p);
+    k_diag_values<<<blocks(n), kThreads, 0, s>>>(v, diag_slot, perm, n, d64_o, d32_o, d64_p, d32_p,
+                                                err);
     return cudaGetLastError();
 }
 

@@ -126,3 +126,34 @@ def test_async_deferred_value_error_and_state_guard():
             with amgd.Handle(rp, col, val, 4, 1) as h2:
                 h2.strength_async(np.empty(257, np.int64), np.empty(10, np.int32))
         assert e.value.status == amgd.AMGD_ERR_STATE
+
+
+def test_fp64_copies_follow_mixed_value_updates():
+    """Value updates under mixed storage leave the row-permuted FP64 values
+    and diagonal (used only by FP64 sweeps and the coarsening) to be refreshed
+    when one of those next runs: after updates under FP32 storage, an FP64
+    build on the same handle equals one on a fresh handle bit for bit."""
+    N, K, seed = 24, 8, 3
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, 0.5)
+    color = inputs.red_black(N)
+    v1, v2 = _variants(rp, col, val, 2)
+    for coloring in (False, True):
+        with amgd.Handle(rp, col, val, K, seed) as h:
+            if coloring:
+                h.set_coloring(color)
+            h.set_precision("fp32")
+            h.set_values(v1)
+            h.set_values_async(torch.from_numpy(v2).pin_memory())
+            h.sync()
+            h.set_precision("fp64")
+            h.init_vectors(seed)
+            sweep = amgd.AMGD_SWEEP_MCGS if coloring else amgd.AMGD_SWEEP_JACOBI
+            h.relax(3, 0.9, sweep)
+            X = h.get_vectors()
+            ls = h.distances(0.5)["ls"]
+        with amgd.Handle(rp, col, v2, K, seed) as f:
+            if coloring:
+                f.set_coloring(color)
+            f.relax(3, 0.9, sweep)
+            assert np.array_equal(X, f.get_vectors()), coloring
+            assert np.array_equal(ls, f.distances(0.5)["ls"], equal_nan=True), coloring
