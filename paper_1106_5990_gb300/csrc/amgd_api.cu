@@ -1976,6 +1976,9 @@ int run_backward(amgd_ctx *h, const double *lsb_in, double *vb, cudaStream_t s)
     a.n = n;
     a.Kp = Kp;
     a.target = h->target;
+    a.unit_w = true;
+    for (double wk : h->h_w) a.unit_w = a.unit_w && wk == 1.0;
+    a.y = Y;                             // the refit leaves the FP64 target here for the adjoint
     // the fits of X_nu in FP64 (the forward pass's own a and LS may be FP32)
     CK(h, launch_adj_refit(st, a, s));
     CK(h, launch_adj_upstream(st, h->rp_o, h->col_o, ls64, h->flag, lsb_in, h->lsb, h->adj_part,

@@ -337,6 +337,7 @@ struct AdjArgs {
                                       // <Ybar_i, X_nu,j> (target), C
     int32_t n, Kp, target, first;
     double omega;
+    bool unit_w = false;              // every LS weight is 1 (the weight products are skipped)
 };
 
 // dL/dLS per slot from an upstream gradient (ls_bar) or the built-in loss

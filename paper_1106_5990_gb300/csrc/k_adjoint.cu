@@ -213,6 +213,46 @@ k_bvals(const double *__restrict__ val, const double *__restrict__ diag,
 // off-diagonal (a = -a_ij/a_ii, LS = 0); diagonal: a = 0, LS = NaN.  Written
 // to A.a and A.ls64 for the upstream gradient and the adjoint of the fits.
 // ---------------------------------------------------------------------------
+// a = yx / xx to within a few FP64 ulps: the FP32 quotient, then one FP64
+// correction with the FP32 reciprocal (its error enters only at second
+// order) -- four FP64 operations instead of a full FP64 division on the
+// narrow FP64 pipe.  Quotients whose operands fall outside the FP32 range
+// take the FP64 division.
+__device__ __forceinline__ double fit_quotient(double yx, double xx)
+{
+    const double ax = fabs(xx), ay = fabs(yx);
+    if (ax < 1e-30 || ax > 1e30 || ay > 1e30 || (ay != 0.0 && ay < 1e-30)) return yx / xx;
+    const float xf = (float)xx;
+    const double q0 = (double)((float)yx / xf);
+    const double r = fma(-q0, xx, yx);
+    return fma(r, (double)(1.0f / xf), q0);
+}
+
+// one FP64 fit of this lane's V components, with (UW) or without the weight
+// products, reduced over the G lanes of the row
+template <int G, int V, bool UW>
+__device__ __forceinline__ void fit64(const double (&x)[V], const double (&y)[V], const double (&w)[V],
+                                      unsigned gmask, double &a_, double &ls_)
+{
+    double xx = 0.0, yx = 0.0;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const double wx = UW ? x[e] : w[e] * x[e];
+        xx = fma(wx, x[e], xx);
+        yx = fma(wx, y[e], yx);
+    }
+    xx = group_sum<G>(xx, gmask);
+    yx = group_sum<G>(yx, gmask);
+    a_ = (xx == 0.0) ? 0.0 : fit_quotient(yx, xx);
+    double res = 0.0;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        const double d = fma(-a_, x[e], y[e]);
+        res = fma(UW ? d : w[e] * d, d, res);
+    }
+    ls_ = group_sum<G>(res, gmask);
+}
+
 template <class TS, int G>
 __global__ void __launch_bounds__(kThreads) k_refit(AdjArgs A)
 {
@@ -228,6 +268,7 @@ __global__ void __launch_bounds__(kThreads) k_refit(AdjArgs A)
     double w[V], y[V];
     ldc<double, V>((const double *)A.w + lane * V, w);
     target64<TS, V>(A, r, lane, p0, p1, y);
+    stc<double, V>((double *)A.y + r * Kp + lane * V, y);     // for the adjoint of the fits
     double *a_out = (double *)A.a_fit;
     double *ls_out = A.ls64;
     const bool fixed = A.target == 0 && p1 - p0 == 2;
@@ -244,22 +285,8 @@ __global__ void __launch_bounds__(kThreads) k_refit(AdjArgs A)
         } else {
             double x[V];
             unpack64<TS, V>(ldg16(X + j * Kp + lane * V), x);
-            double xx = 0.0, yx = 0.0;
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                xx = fma(w[e] * x[e], x[e], xx);
-                yx = fma(w[e] * x[e], y[e], yx);
-            }
-            xx = group_sum<G>(xx, gmask);
-            yx = group_sum<G>(yx, gmask);
-            a_ = (xx == 0.0) ? 0.0 : yx / xx;
-            double res = 0.0;
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                const double d = fma(-a_, x[e], y[e]);
-                res = fma(w[e] * d, d, res);
-            }
-            ls_ = group_sum<G>(res, gmask);
+            if (A.unit_w) fit64<G, V, true>(x, y, w, gmask, a_, ls_);
+            else fit64<G, V, false>(x, y, w, gmask, a_, ls_);
         }
         if (lane == 0) {
             a_out[p] = a_;
@@ -269,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_refit(AdjArgs A)
 }
 
 // ---------------------------------------------------------------------------
-// row i: Y_i, Ybar_i = 2 w (y_i sum_p lsb_p - sum_p lsb_p a_p x_j), and for
+// row i (Y_i as k_refit left it): Ybar_i = 2 w (y_i sum_p lsb_p - sum_p lsb_p a_p x_j), and for
 // the residual target gt_p = <Ybar_i, X_col_p> over all slots
 // ---------------------------------------------------------------------------
 template <class TS, int G>
@@ -289,8 +316,7 @@ __global__ void __launch_bounds__(kThreads) k_edge_bwd(AdjArgs A)
 
     C w[V], y[V];
     ldc<C, V>((const C *)A.w + lane * V, w);
-    target64<TS, V>(A, r, lane, p0, p1, y);
-    stc<C, V>((C *)A.y + off, y);
+    ldc<C, V>((const C *)A.y + off, y);            // the target, left by k_refit
 
     C v[V];
 #pragma unroll
