@@ -195,24 +195,6 @@ k_upstream(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-template <class C>
-__global__ void __launch_bounds__(kThreads)
-k_bvals(const double *__restrict__ val, const double *__restrict__ diag,
-        const int32_t *__restrict__ at_row, const int32_t *__restrict__ at_slot,
-        C *__restrict__ b, int64_t nnz)
-{
-    for (int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x; q < nnz;
-         q += (int64_t)gridDim.x * kThreads)
-        b[q] = (C)(__ldg(val + __ldg(at_slot + q)) / __ldg(diag + __ldg(at_row + q)));
-}
-
-// ---------------------------------------------------------------------------
-// the one-point fits of every slot of row i refitted in FP64 from the stored
-// X_nu (§4.1, Eq. (4.3)): a_p = S_yx / S_xx (0 if S_xx = 0), LS_p = sum w (y_i -
-// a_p x_j)^2 (two passes); the exact rule of a residual-target row with one
-// off-diagonal (a = -a_ij/a_ii, LS = 0); diagonal: a = 0, LS = NaN.  Written
-// to A.a and A.ls64 for the upstream gradient and the adjoint of the fits.
-// ---------------------------------------------------------------------------
 // a = yx / xx to within a few FP64 ulps: the FP32 quotient, then one FP64
 // correction with the FP32 reciprocal (its error enters only at second
 // order) -- four FP64 operations instead of a full FP64 division on the
@@ -228,6 +210,29 @@ __device__ __forceinline__ double fit_quotient(double yx, double xx)
     return fma(r, (double)(1.0f / xf), q0);
 }
 
+template <class C>
+__global__ void __launch_bounds__(kThreads)
+k_bvals(const double *__restrict__ val, const double *__restrict__ diag,
+        const int32_t *__restrict__ at_row, const int32_t *__restrict__ at_slot,
+        C *__restrict__ b, int64_t nnz)
+{
+    for (int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x; q < nnz;
+         q += (int64_t)gridDim.x * kThreads)
+    {
+        const double v = __ldg(val + __ldg(at_slot + q)), d = __ldg(diag + __ldg(at_row + q));
+        // FP32 sweeps: the quotient to a few FP64 ulps, then rounded to FP32
+        // (no FP64 division); FP64 sweeps: the FP64 quotient
+        b[q] = sizeof(C) == 4 ? (C)fit_quotient(v, d) : (C)(v / d);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the one-point fits of every slot of row i refitted in FP64 from the stored
+// X_nu (§4.1, Eq. (4.3)): a_p = S_yx / S_xx (0 if S_xx = 0), LS_p = sum w (y_i -
+// a_p x_j)^2 (two passes); the exact rule of a residual-target row with one
+// off-diagonal (a = -a_ij/a_ii, LS = 0); diagonal: a = 0, LS = NaN.  Written
+// to A.a and A.ls64 for the upstream gradient and the adjoint of the fits.
+// ---------------------------------------------------------------------------
 // one FP64 fit of this lane's V components, with (UW) or without the weight
 // products, reduced over the G lanes of the row
 template <int G, int V, bool UW>
@@ -395,8 +400,13 @@ __global__ void __launch_bounds__(kThreads) k_xbar_nu(AdjArgs A)
             const C c = (C)(-2.0 * g * (double)ap);
             C yi[V];
             ldc<C, V>(Y + (int64_t)i * Kp + lane * V, yi);
+            if (A.unit_w) {
 #pragma unroll
-            for (int e = 0; e < V; ++e) acc[e] = fma(c * w[e], fma(-ap, xj[e], yi[e]), acc[e]);
+                for (int e = 0; e < V; ++e) acc[e] = fma(c, fma(-ap, xj[e], yi[e]), acc[e]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[e] = fma(c * w[e], fma(-ap, xj[e], yi[e]), acc[e]);
+            }
         }
         if (A.target == 0) {
             const C b = (C)__ldg((const typename S::C *)A.at_b + q);   // the sweeps' type
@@ -567,19 +577,21 @@ k_finish(const int32_t *__restrict__ rp, const double *__restrict__ val,
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * kThreads) {
         const int p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-        const double aii = __ldg(diag + i);
+        // one FP64 division per row (the GB300's FP64 pipe is narrow): every
+        // quotient by a_ii below is a product with its reciprocal
+        const double inv = 1.0 / __ldg(diag + i);
         double qs = 0.0, qt = 0.0;
         for (int p = p0; p < p1; ++p) {
             const double s = gs ? (double)__ldg(gs + p) : 0.0;
             const double t = gt ? (double)__ldg(gt + p) : 0.0;
             const double v = __ldg(val + p);
-            vb[p] = -(omega * s + t) / aii;
+            vb[p] = -(omega * s + t) * inv;
             qs += v * s;
             qt += v * t;
         }
-        qs /= aii;
-        qt /= aii;
-        vb[__ldg(dslot + i)] += (qt + omega * qs) / aii;
+        qs *= inv;
+        qt *= inv;
+        vb[__ldg(dslot + i)] += (qt + omega * qs) * inv;
         acc -= qs;
     }
     const double t = block_sum(acc);
