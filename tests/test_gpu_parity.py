@@ -642,6 +642,40 @@ def test_edge_inplace_shapes_agree(prec, K, mat):
                     check_flags(flag, ref_w, rp, col, 0.5, 1e-4)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("summation", ["compensated", "plain"])
+def test_edge_warp_kernel_weighted_mixed(prec, summation):
+    """The warp-staged distance kernel (stage 3) with non-unit LS weights on
+    the mixed paths (the weights held in shared memory per block) against the
+    row kernel (stage 0) on the same vectors: within 2e-5, strength sets equal
+    outside a band of 1e-4 around theta."""
+    N = 40
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-3, math.pi / 6)
+    color = inputs.red_black(N)
+    w = np.random.default_rng(5).uniform(0.5, 2.0, 16)
+    V = {"fp32": 4, "bf16": 8}[prec]
+    P = 16 // V
+
+    def run(stage, u):
+        with amgd.Handle(rp, col, val, 16, 4) as h:
+            h.set_precision(prec)
+            h.set_coloring(color)
+            h.set_weights(w)
+            h.set_summation(summation)
+            h.set_kernel_shape(amgd.AMGD_KERNEL_EDGE, P, 1, u, stage)
+            h.relax(3, 1.0, amgd.AMGD_SWEEP_MCGS)
+            out = h.distances(0.5)
+            s_rp, s_col = h.strength()
+        return out, flags_from_strength(rp, col, s_rp, s_col)
+
+    ref, ref_flag = run(0, 4)
+    got, flag = run(3, 8)
+    off = ~np.isnan(ref["ls"])
+    rel = np.abs(got["ls"][off] - ref["ls"][off]) / np.maximum(ref["ls"][off], 1e-300)
+    assert rel.max() <= 2e-5, rel.max()
+    check_flags(flag, dict(ls=ref["ls"], flag=ref_flag), rp, col, 0.5, 1e-4)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16"])
 def test_edge_batch_of_two(prec):
     """The distance pass also compiles a gather batch of 2 (both kernels):
