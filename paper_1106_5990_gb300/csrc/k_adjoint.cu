@@ -32,6 +32,8 @@
 // Lane layout as in the forward kernels: G lanes per row, one 16-byte vector
 // of the stored block per lane (V components); the FP64 vectors (Y, Ybar,
 // Xbar) use the same components per lane.
+#include <type_traits>
+
 #include "amgd_internal.cuh"
 #include "rowops.cuh"
 
@@ -183,8 +185,10 @@ k_upstream(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                 } else if (__ldg(flag + p)) {
                     const double l = (double)__ldg(ls + p);
                     if (l > 0.0) {
-                        acc += 1.0 / (l * l);
-                        g = -2.0 / (l * l * l);
+                        // one FP64 division per slot (the FP64 pipe is narrow)
+                        const double inv = 1.0 / l, inv2 = inv * inv;
+                        acc += inv2;
+                        g = -2.0 * inv2 * inv;
                     }
                 }
             }
@@ -258,6 +262,92 @@ __device__ __forceinline__ void fit64(const double (&x)[V], const double (&y)[V]
     ls_ = group_sum<G>(res, gmask);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float fits (FP32/BF16 storage, unit weights): the same two-pass fit
+// carried in pairs of FP32 words (value = hi + lo: about 48 significant bits)
+// with error-free products (one FMA) and sums (TwoSum), on the FP32 pipe
+// instead of the GB300's narrow FP64 pipe.  The stored components x are exact
+// FP32 values; the FP64 target y enters as its two-word split.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e)
+{
+    const float t = __fadd_rn(a, b);
+    const float bp = __fsub_rn(t, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bp)), __fsub_rn(b, bp));
+    s = t;
+}
+__device__ __forceinline__ void df_two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+// (s, c) += t + t_err: s the running sum, c every rounding error (s + c the value)
+__device__ __forceinline__ void df_acc(float &s, float &c, float t, float t_err)
+{
+    float e;
+    df_two_sum(s, t, s, e);
+    c = __fadd_rn(c, __fadd_rn(e, t_err));
+}
+template <int G>
+__device__ __forceinline__ void df_allreduce(float &s, float &c, unsigned mask)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(mask, s, o, G), co = __shfl_xor_sync(mask, c, o, G);
+        float e;
+        df_two_sum(s, so, s, e);
+        c = __fadd_rn(__fadd_rn(c, co), e);
+    }
+}
+
+// one fit of this lane's V components (unit weights), reduced over the G lanes
+// of the row; a and LS as two words each (value = hi + lo)
+template <int G, int V>
+__device__ __forceinline__ void fit_df(const float (&x)[V], const float (&yh)[V], const float (&yl)[V],
+                                       unsigned gmask, float &ah, float &al, float &lh, float &ll)
+{
+    float sxx = 0.f, cxx = 0.f, syx = 0.f, cyx = 0.f;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        float p, pe;
+        df_two_prod(x[e], x[e], p, pe);
+        df_acc(sxx, cxx, p, pe);
+        df_two_prod(x[e], yh[e], p, pe);
+        df_acc(syx, cyx, p, __fmaf_rn(x[e], yl[e], pe));
+    }
+    df_allreduce<G>(sxx, cxx, gmask);
+    df_allreduce<G>(syx, cyx, gmask);
+    float xh, xl, qh, ql;
+    df_two_sum(sxx, cxx, xh, xl);
+    df_two_sum(syx, cyx, qh, ql);
+    ah = 0.f;
+    al = 0.f;
+    if (xh != 0.f) {
+        // a = yx / xx: the FP32 quotient, then the quotient of its remainder
+        ah = __fdiv_rn(qh, xh);
+        float p, pe;
+        df_two_prod(ah, xh, p, pe);
+        const float r = __fadd_rn(__fsub_rn(__fsub_rn(qh, p), pe), __fmaf_rn(-ah, xl, ql));
+        al = __fdiv_rn(r, xh);
+    }
+    float sls = 0.f, cls = 0.f;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        // d = y - a x as two words, then d^2 = dh^2 + 2 dh dl
+        float p, pe, t, te;
+        df_two_prod(ah, x[e], p, pe);
+        df_two_sum(yh[e], -p, t, te);
+        const float dl0 = __fadd_rn(__fsub_rn(te, pe), __fmaf_rn(-al, x[e], yl[e]));
+        float dh, dl;
+        df_two_sum(t, dl0, dh, dl);
+        float q, qe;
+        df_two_prod(dh, dh, q, qe);
+        df_acc(sls, cls, q, __fmaf_rn(__fmul_rn(2.f, dh), dl, qe));
+    }
+    df_allreduce<G>(sls, cls, gmask);
+    df_two_sum(sls, cls, lh, ll);
+}
+
 template <class TS, int G>
 __global__ void __launch_bounds__(kThreads) k_refit(AdjArgs A)
 {
@@ -278,6 +368,17 @@ __global__ void __launch_bounds__(kThreads) k_refit(AdjArgs A)
     double *ls_out = A.ls64;
     const bool fixed = A.target == 0 && p1 - p0 == 2;
     const double diag = __ldg((const double *)A.diag + r);
+    // mixed storage with unit weights: the fits in double-float (FP32 pipe)
+    constexpr bool kMixed = !std::is_same<TS, double>::value;
+    const bool df = kMixed && A.unit_w;
+    float yh[V], yl[V];
+    if (df) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            yh[e] = (float)y[e];
+            yl[e] = (float)(y[e] - (double)yh[e]);
+        }
+    }
     for (int p = p0; p < p1; ++p) {
         const int64_t j = __ldg(A.col + p);
         double a_, ls_;
@@ -287,6 +388,14 @@ __global__ void __launch_bounds__(kThreads) k_refit(AdjArgs A)
         } else if (fixed) {
             a_ = -__ldg((const double *)A.val + p) / diag;
             ls_ = 0.0;
+        } else if (df) {
+            if constexpr (kMixed) {
+                float xf[V], ah, al, lh, ll;
+                Store<TS>::unpack(ldg16(X + j * Kp + lane * V), xf);
+                fit_df<G, V>(xf, yh, yl, gmask, ah, al, lh, ll);
+                a_ = (double)ah + (double)al;
+                ls_ = (double)lh + (double)ll;
+            }
         } else {
             double x[V];
             unpack64<TS, V>(ldg16(X + j * Kp + lane * V), x);
