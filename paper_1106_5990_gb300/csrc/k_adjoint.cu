@@ -222,12 +222,7 @@ k_bvals(const double *__restrict__ val, const double *__restrict__ diag,
 {
     for (int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x; q < nnz;
          q += (int64_t)gridDim.x * kThreads)
-    {
-        const double v = __ldg(val + __ldg(at_slot + q)), d = __ldg(diag + __ldg(at_row + q));
-        // FP32 sweeps: the quotient to a few FP64 ulps, then rounded to FP32
-        // (no FP64 division); FP64 sweeps: the FP64 quotient
-        b[q] = sizeof(C) == 4 ? (C)fit_quotient(v, d) : (C)(v / d);
-    }
+        b[q] = (C)(__ldg(val + __ldg(at_slot + q)) / __ldg(diag + __ldg(at_row + q)));
 }
 
 // ---------------------------------------------------------------------------
