@@ -157,3 +157,28 @@ def test_fp64_copies_follow_mixed_value_updates():
             f.relax(3, 0.9, sweep)
             assert np.array_equal(X, f.get_vectors()), coloring
             assert np.array_equal(ls, f.distances(0.5)["ls"], equal_nan=True), coloring
+
+
+def test_coarsening_follows_mixed_value_updates():
+    """The coarsening reads the row-permuted FP64 values, which a value update
+    under mixed storage leaves to be refreshed: after updates under FP32
+    storage on a colored handle, the coarse set and the rates equal those of a
+    fresh handle holding the same values."""
+    N, K, seed = 32, 8, 3
+    rp, col, val = inputs.aniso2d_9pt(N, 1e-2, 0.3)
+    color = inputs.red_black(N)
+    v1, v2 = _variants(rp, col, val, 2)
+    ls = oracle.build(rp, col, v2, K, seed, 3, 1.0, 0.5)["ls"]
+    args = dict(sweep=amgd.AMGD_SWEEP_MCGS, nu=3, max_sets=6)
+    with amgd.Handle(rp, col, val, K, seed) as h:
+        h.set_coloring(color)
+        h.set_precision("fp32")
+        h.set_values(v1)
+        h.set_values_async(torch.from_numpy(v2).pin_memory())
+        h.sync()
+        C, rho = h.cr_coarsen(None, ls=ls, **args)
+    with amgd.Handle(rp, col, v2, K, seed) as f:
+        f.set_coloring(color)
+        f.set_precision("fp32")
+        Cf, rhof = f.cr_coarsen(None, ls=ls, **args)
+    assert np.array_equal(C, Cf) and np.array_equal(rho, rhof)
