@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kEdgeThreads, edge_rows_min_blocks<COMP>()) k_
 #pragma unroll
         for (int t = 0; t < NV; ++t)
 #pragma unroll
-            for (int e = 0; e < V; ++e) w[t][e] = ((const C *)A.w)[(t * G + lane) * V + e];
+            for (int e = 0; e < V; ++e) w[t][e] = ((const C *)A.w)[piece_of<G, NV>(lane, t) * V + e];
     }
 
     int q0 = 0, q1 = 0;       // the row's entries in the pattern of the fits
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kEdgeThreads, edge_rows_min_blocks<COMP>()) k_
             const int64_t xr = (PX && A.xrow) ? checked_row(__ldg(A.xrow + r), A.n, A.status) : r;
 #pragma unroll
             for (int t = 0; t < NV; ++t) {
-                S::unpack(ldg16(X + xr * Kp + (t * G + lane) * V), y[t]);     // x_i
+                S::unpack(ldg16(X + xr * Kp + piece_of<G, NV>(lane, t) * V), y[t]);     // x_i
                 if (A.target == 0) {
 #pragma unroll
                     for (int e = 0; e < V; ++e) y[t][e] = fma(-d, acc[t].get(e), y[t][e]);
@@ -340,13 +340,14 @@ __global__ void __launch_bounds__(kEdgeThreads, edge_rows_min_blocks<COMP>()) k_
                 if (jj[u] >= 0 && jj[u] != r) {
                     const int64_t xj = checked_row(PX ? (int64_t)__ldg(xcol + pb + u) : (int64_t)jj[u],
                                                    A.n, A.status);
-                    if constexpr (G == 1 && NV % 2 == 0) {       // whole row per lane: 32-byte pairs
+                    if constexpr (NV % 2 == 0) {                 // side-by-side pieces: 32-byte pairs
 #pragma unroll
-                        for (int t = 0; t < NV; t += 2) ldg32(X + xj * Kp + t * V, raw[u][t], raw[u][t + 1]);
+                        for (int t = 0; t < NV; t += 2)
+                            ldg32(X + xj * Kp + piece_of<G, NV>(lane, t) * V, raw[u][t], raw[u][t + 1]);
                     } else {
 #pragma unroll
                         for (int t = 0; t < NV; ++t)
-                            raw[u][t] = ldg16(X + xj * Kp + (t * G + lane) * V);
+                            raw[u][t] = ldg16(X + xj * Kp + piece_of<G, NV>(lane, t) * V);
                     }
                 }
 #pragma unroll
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
             }
             C y[NV][V];
 #pragma unroll
-            for (int t = 0; t < NV; ++t) S::unpack(ldg16(X + r * KP + (t * G + lane) * V), y[t]);
+            for (int t = 0; t < NV; ++t) S::unpack(ldg16(X + r * KP + piece_of<G, NV>(lane, t) * V), y[t]);
             if (A.target == 0) {
                 Acc<C, V> acc[NV];
                 row_sum<TS, G, NV, U, false>(col, val, X, X, 0, KP, lane, p0, p1, acc, A.n, A.status);
@@ -571,9 +572,9 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edge_tiles(EdgeArgs A)
             for (int t = 0; t < NV; ++t) {
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
-                    ys[rl * KP + (t * G + lane) * V + e] = y[t][e];
+                    ys[rl * KP + piece_of<G, NV>(lane, t) * V + e] = y[t][e];
                     if constexpr (kMixed)
-                        s = fma(UW ? y[t][e] : wv[(t * G + lane) * V + e] * y[t][e], y[t][e], s);
+                        s = fma(UW ? y[t][e] : wv[piece_of<G, NV>(lane, t) * V + e] * y[t][e], y[t][e], s);
                 }
             }
             if constexpr (kMixed) {
@@ -827,7 +828,7 @@ __global__ void __launch_bounds__(256) k_edge_fixup(EdgeArgs A)
 template <class TS, int G, int NV, int U, bool UW, bool PX, bool COMP>
 cudaError_t go_rows(const EdgeArgs &a, cudaStream_t s)
 {
-    if constexpr (G == 1 && NV % 2 == 0)
+    if constexpr (NV % 2 == 0)
         if (!rows_aligned32(a.x, a.Kp, sizeof(TS))) return cudaErrorMisalignedAddress;
     const int rows_per_block = kEdgeThreads / G;
     const unsigned grid = (unsigned)(((int64_t)a.n + rows_per_block - 1) / rows_per_block);

@@ -61,10 +61,10 @@ __global__ void AMGD_RELAX_BOUNDS k_relax(RelaxArgs A)
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
         C xi[V], out[V];
-        S::unpack(ldg16(xold + r * Kp + (t * G + lane) * V), xi);   // row r is never of an earlier color
+        S::unpack(ldg16(xold + r * Kp + piece_of<G, NV>(lane, t) * V), xi);   // row r is never of an earlier color
 #pragma unroll
         for (int e = 0; e < V; ++e) out[e] = fma(-c, acc[t].get(e), xi[e]);
-        S::store(xnew + r * Kp + (t * G + lane) * V, out);
+        S::store(xnew + r * Kp + piece_of<G, NV>(lane, t) * V, out);
     }
 }
 
@@ -784,7 +784,7 @@ cudaError_t go(const RelaxArgs &a, cudaStream_t s)
 {
     const int64_t rows = (int64_t)a.r1 - a.r0;
     if (rows <= 0) return cudaSuccess;
-    if constexpr (G == 1 && NV % 2 == 0) {          // 32-byte row reads
+    if constexpr (NV % 2 == 0) {                    // 32-byte row reads
         if (!rows_aligned32(a.xold, a.Kp, sizeof(TS)) || !rows_aligned32(a.xnew, a.Kp, sizeof(TS)))
             return cudaErrorMisalignedAddress;
     }

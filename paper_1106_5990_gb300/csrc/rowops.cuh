@@ -13,6 +13,17 @@
 
 namespace amgd {
 
+// The piece of a row that lane `lane` of a row's G lanes holds as its t-th
+// piece: with an even number of pieces per lane the lane holds them side by
+// side (two move in one 32-byte access), otherwise they interleave over the
+// G lanes.  Every component keeps its own FMA chain, so the layout never
+// changes a row sum.
+template <int G, int NV>
+__device__ __forceinline__ int piece_of(int lane, int t)
+{
+    return (NV % 2 == 0) ? lane * NV + t : t * G + lane;
+}
+
 // read-only load of a CSR entry
 template <class T>
 __device__ __forceinline__ T ld_csr(const T *p)
@@ -55,8 +66,9 @@ template <int V> struct Acc<float, V> {
 // order.  SPLIT: rows j < split are read from xnew, the others from xold.
 // rows, status: the gather range and status word of the checked build.
 // Nonzeros are taken U at a time: U column indices and values, then all U
-// gathers in flight before any is consumed.  A lane that owns a whole row
-// (G = 1, NV even) reads it in 32-byte pairs: the rows are 32-byte aligned.
+// gathers in flight before any is consumed.  A lane that holds an even number
+// of pieces reads them in 32-byte pairs (piece_of): the rows are 32-byte
+// aligned.
 template <class TS, int G, int NV, int U, bool SPLIT>
 __device__ __forceinline__ void row_sum(const int32_t *__restrict__ col,
                                         const typename Store<TS>::A *__restrict__ val,
@@ -84,12 +96,13 @@ __device__ __forceinline__ void row_sum(const int32_t *__restrict__ col,
         for (int u = 0; u < U; ++u) {
             if (jj[u] >= 0) {
                 const TS *src = (SPLIT && jj[u] < split ? xnew : xold) + checked_row(jj[u], rows, status) * Kp;
-                if constexpr (G == 1 && NV % 2 == 0) {
+                if constexpr (NV % 2 == 0) {
 #pragma unroll
-                    for (int tt = 0; tt < NV; tt += 2) ldg32(src + tt * V, raw[u][tt], raw[u][tt + 1]);
+                    for (int tt = 0; tt < NV; tt += 2)
+                        ldg32(src + piece_of<G, NV>(lane, tt) * V, raw[u][tt], raw[u][tt + 1]);
                 } else {
 #pragma unroll
-                    for (int tt = 0; tt < NV; ++tt) raw[u][tt] = ldg16(src + (tt * G + lane) * V);
+                    for (int tt = 0; tt < NV; ++tt) raw[u][tt] = ldg16(src + piece_of<G, NV>(lane, tt) * V);
                 }
             }
         }
