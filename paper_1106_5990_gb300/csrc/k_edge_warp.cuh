@@ -185,8 +185,14 @@ __global__ void __launch_bounds__(kWarpEdgeThreads) k_edge_warp(EdgeArgs A)
             for (int u = 0; u < U; ++u)
                 if (jj[u] >= 0) {
                     const TS *src = X + checked_row(jj[u], A.n, A.status) * Kp;
+                    if constexpr (NV % 2 == 0) {         // side-by-side pieces: 32-byte pairs
 #pragma unroll
-                    for (int t = 0; t < NV; ++t) raw[u][t] = ldg16(src + (t * G + lane) * V);
+                        for (int t = 0; t < NV; t += 2)
+                            ldg32(src + piece_of<G, NV>(lane, t) * V, raw[u][t], raw[u][t + 1]);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < NV; ++t) raw[u][t] = ldg16(src + piece_of<G, NV>(lane, t) * V);
+                    }
                 }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -197,7 +203,7 @@ __global__ void __launch_bounds__(kWarpEdgeThreads) k_edge_warp(EdgeArgs A)
                     C x[V];
                     S::unpack(raw[u][t], x);
                     acc[t].fma_piece(vv[u], x);
-                    if (parked) xs[park_index<P>(s, t * G + lane)] = raw[u][t];
+                    if (parked) xs[park_index<P>(s, piece_of<G, NV>(lane, t))] = raw[u][t];
                 }
                 if (parked && lane == 0) sr[s] = (uint8_t)rw;
             }
@@ -207,12 +213,12 @@ __global__ void __launch_bounds__(kWarpEdgeThreads) k_edge_warp(EdgeArgs A)
         C y[NV][V];
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
-            S::unpack(ldg16(X + xr * Kp + (t * G + lane) * V), y[t]);     // x_i
+            S::unpack(ldg16(X + xr * Kp + piece_of<G, NV>(lane, t) * V), y[t]);     // x_i
             if (A.target == 0) {
 #pragma unroll
                 for (int e = 0; e < V; ++e) y[t][e] = fma(-d, acc[t].get(e), y[t][e]);
             }
-            st_piece<C, V>(ys + rw * L::YST + (t * G + lane) * V, y[t]);
+            st_piece<C, V>(ys + rw * L::YST + piece_of<G, NV>(lane, t) * V, y[t]);
         }
         if constexpr (kMixed) {
             C syy = C(0);
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(kWarpEdgeThreads) k_edge_warp(EdgeArgs A)
             for (int t = 0; t < NV; ++t)
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
-                    const C wk = UW ? C(1) : wv[(t * G + lane) * V + e];
+                    const C wk = UW ? C(1) : wv[piece_of<G, NV>(lane, t) * V + e];
                     syy = fma(UW ? y[t][e] : wk * y[t][e], y[t][e], syy);
                 }
             syy = group_sum<G>(syy, gmask);
@@ -377,6 +383,8 @@ cudaError_t go_warp(const EdgeArgs &a, cudaStream_t s)
 {
     using L = WarpEdgeLayout<TS, G, NV>;
     if (a.Kp != L::KP || !a.xcol) return cudaErrorInvalidValue;
+    if constexpr (NV % 2 == 0)                    // 32-byte row reads
+        if (!rows_aligned32(a.x, a.Kp, sizeof(TS))) return cudaErrorMisalignedAddress;
     constexpr int smem = L::block_bytes(UW);
     static_assert(smem <= 227 * 1024, "warp windows exceed the shared memory of a block");
     const int64_t rows_per_block = (int64_t)kWarpEdgeWarps * L::R;
