@@ -316,8 +316,9 @@ int amgd_graph_launch(amgd_handle h);
  *   shape spreads them over G lanes with NV vectors per lane (G*NV = P,
  *   NV in {1,2,4}) and gathers U nonzeros per batch (U in {4,8}; the
  *   distance pass also takes U = 2).  In these terms a warp holds 32/G
- *   rows, a lane's tile of K is NV*V components and every vector load is 16
- *   bytes wide; the tuner picks all three.  For the
+ *   rows and a lane's tile of K is NV*V components; a lane with an even NV
+ *   holds its vectors side by side and moves two per 32-byte access, others
+ *   move one per 16-byte access; the tuner picks all three.  For the
  *   relaxation, staged selects the kernel: 0 direct; 1 persistent, each
  *   tile's CSR slice copied into shared memory with TMA bulk copies ahead of
  *   use (waits bounded to about one second; a wait that runs out makes the
