@@ -6,7 +6,9 @@
 // A warp owns R = 32/G consecutive caller rows (one contiguous run of CSR
 // slots) and walks them in three steps:
 //   1. targets, G lanes per row: every stored entry's vector row is gathered
-//      (16-byte pieces, lane-interleaved, so one warp load covers whole rows),
+//      (16-byte pieces spread over the row's G lanes -- side by side and moved
+//      two per 32-byte access when a lane holds an even number -- so one warp
+//      load covers whole rows),
 //      folded into the row sum with the sweeps' rounding, and parked in the
 //      warp's shared-memory window, slot by slot;
 //   2. fits, one lane per stored entry: x_j and y_i are read back from shared
