@@ -11,9 +11,11 @@
 // per term and the update is one fused multiply-add, so the FP64 path
 // rounds exactly like a sequential row-by-row evaluation.
 //
-// Thread mapping (Shape): G lanes own one row; lane l holds the 16-byte
-// vectors l, l+G, ..., l+(NV-1)G of every K-vector row it touches, so each
-// neighbour row is read as G*NV fully used 16-byte pieces.  Nonzeros are
+// Thread mapping (Shape): G lanes own one row; lane l holds NV of the row's
+// 16-byte vectors -- side by side (l*NV, ..., l*NV+NV-1), moved two per
+// 32-byte access, when NV is even (direct and chunked kernels; piece_of in
+// rowops.cuh), else l, l+G, ..., l+(NV-1)G (the staged kernels always) -- so
+// each neighbour row is read as fully used pieces.  Nonzeros are
 // taken U at a time: U column indices and values are loaded, then all U*NV
 // vector pieces are requested before any is consumed, which keeps U*NV loads
 // per lane in flight (the kernel is bound by HBM latency and bandwidth: CSR
