@@ -324,7 +324,7 @@ int amgd_graph_launch(amgd_handle h);
  *   use (waits bounded to about one second; a wait that runs out makes the
  *   next synchronising call return AMGD_ERR_TIMEOUT); 2 warp-pipelined, CSR
  *   slices and neighbour rows copied with cp.async two and one row groups
- *   ahead (U must be 4); 3 chunked, one 768-thread block per SM owning a
+ *   ahead (U must be 4); 3 chunked, one 896-thread block per SM owning a
  *   contiguous run of rows, each warp asking the L2 for the row pointers
  *   and CSR lines of its next row groups ahead of use and loading the CSR
  *   with an evict-first and the vectors with an evict-last cache policy.

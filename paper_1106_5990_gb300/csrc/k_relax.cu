@@ -489,11 +489,12 @@ k_relax_pipe(RelaxArgs A, int64_t chunk)
 // evict-last hint and the CSR, which streams through once per sweep, with an
 // evict-first hint, so the vectors of the next color phase and sweep tend to
 // stay in the 129 MB L2 instead of being pushed out by the matrix.  Same row
-// sums in the same order as k_relax: same bits.  768 threads (24 warps): the
-// register budget of 85 per thread holds a batch of four 64-byte rows per lane
+// sums in the same order as k_relax: same bits.  896 threads (28 warps): the
+// register budget of 72 per thread holds a batch of four 64-byte rows per lane
 // pair without spilling (at 1024 threads, 64 registers spilled and the sweep
-// was 6% slower; at 640 the direct kernel wins).
-constexpr int kChunkThreads = 768;
+// was 10% slower; 768 threads were 4% slower, and at 640 the direct kernel
+// wins).
+constexpr int kChunkThreads = 896;
 
 __device__ __forceinline__ void prefetch_l2(const void *p)
 {
