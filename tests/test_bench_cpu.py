@@ -74,3 +74,28 @@ def test_depth2_pattern_of_c2_operator():
     assert len(pcol) == s * s and len(pcol) - n == 25_104_420
     i = 500 * N + 500
     assert prp[i + 1] - prp[i] == 25
+
+
+def test_recorded_traffic_follows_code_not_comments(tmp_path, monkeypatch):
+    """The recorded DRAM bytes of a kernel stay valid through edits of its
+    comments and layout, and are dropped once its code changes."""
+    src = ("// sweep kernel\n__global__ void k(int *p) { /* one store */ p[0] = 1; }\n"
+           "const char *s = \"// not a comment\";\n")
+    assert bench._code_only(src) == bench._code_only(src.replace("// sweep kernel", "// renamed note")
+                                                     .replace("/* one store */", "")
+                                                     .replace("p[0] = 1;", "p[0]  =  1;"))
+    assert "// not a comment" in bench._code_only(src)
+    assert bench._code_only(src) != bench._code_only(src.replace("p[0] = 1", "p[0] = 2"))
+    csrc = tmp_path / "paper_1106_5990_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_text(src)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench.source_sha("k.cu")
+    table = tmp_path / "traffic.json"
+    table.write_text('{"relax/fp32/K16/c2": {"source_sha": "%s", "dram_bytes_per_launch": 123.0}}' % sha)
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(table))
+    assert bench.recorded_traffic("relax/fp32/K16/c2", sha) == 123.0
+    (csrc / "k.cu").write_text(src.replace("// sweep kernel", "// edited note"))
+    assert bench.recorded_traffic("relax/fp32/K16/c2", bench.source_sha("k.cu")) == 123.0
+    (csrc / "k.cu").write_text(src.replace("p[0] = 1", "p[0] = 3"))
+    assert bench.recorded_traffic("relax/fp32/K16/c2", bench.source_sha("k.cu")) is None
